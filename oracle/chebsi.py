@@ -1,0 +1,69 @@
+"""Subspace iteration with shrink-and-expand (arXiv:2409.05572, Algorithm 1,
+inside the framework of Algorithm 5), in plain float64.
+
+The shift-and-invert step X <- (A - zeta I)^{-1} X is replaced by a degree-m
+Chebyshev filter X <- p_m(A) X (``blocks.cheb_filter``); the theory of the
+paper's Sec. 5 is stated for a power step X <- B X, which p_m(A) is.
+
+Readings: Ritz values are sorted algebraically ascending (the Anderson
+Hamiltonian is indefinite, so "ascending magnitude" would pick interior
+eigenvalues); the filter damps [a, b] with a = the largest Ritz value of the
+active block, b = an upper bound on the spectrum supplied by the caller,
+scaled to 1 at a0 = the smallest Ritz value.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import blocks as B
+from .lobpcg import Result
+from .strategy import Strategy
+
+
+def chebsi(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none",
+           tol: float = 1e-10, max_iter: int = 1000, normA: float = 1.0,
+           degree: int = 12, upper: float | None = None,
+           keep_ritz: bool = False, **strategy_params) -> Result:
+    n, nex = X0.shape
+    assert nev <= nes < nex
+    if upper is None:
+        upper = normA
+    strat = Strategy(strategy, nes, nex, **strategy_params)
+
+    X = B.cholqr2(X0)
+    AX = B.spmm(A, X)
+    lam, Z = B.rayleigh_ritz(X, AX)
+    X, AX = X @ Z, AX @ Z
+    nnow = nex
+    Xdrop = None
+    res = Result(lam[:nev], X[:, :nev], False, 0)
+
+    for j in range(1, max_iter + 1):
+        R, rho, r = B.residual_test(X, AX, lam, normA, nev)
+        strat.record(j, r)
+        res.history.append(r)
+        res.iters = j
+        if r <= tol:
+            res.lam, res.X, res.converged, res.rho = lam[:nev].copy(), X[:, :nev].copy(), True, rho[:nev]
+            break
+        # X <- p_m(A) X replaces X <- (A - zeta I)^{-1} X.
+        X = B.cheb_filter(A, X, degree, float(lam[nnow - 1]), upper, float(lam[0]))
+        if strat.ifexpand(j, nnow):
+            X = np.hstack([X, Xdrop])
+            nnow = nex
+        X = B.cholqr2(X)
+        AX = B.spmm(A, X)
+        lam, Z = B.rayleigh_ritz(X, AX)
+        X, AX = X @ Z, AX @ Z
+        res.widths.append(nnow)
+        if keep_ritz:
+            res.ritz.append(lam.copy())
+        if strat.ifshrink(j, nnow):
+            Xdrop = X[:, nes:]
+            X, AX, lam = X[:, :nes], AX[:, :nes], lam[:nes]
+            nnow = nes
+    else:
+        res.lam, res.X = lam[:nev].copy(), X[:, :nev].copy()
+        res.rho = B.residual_test(X, AX, lam, normA, nev)[1][:nev]
+    res.events = list(strat.events)
+    return res
