@@ -1,0 +1,209 @@
+/*
+ * eig_gb300.h -- C ABI of the GB300-native shrink-and-expand block
+ * eigensolvers (Liu, Ma and Shao, "On a shrink-and-expand technique for
+ * symmetric block eigensolvers", arXiv:2409.05572).
+ *
+ * Problem (Sec. 1): for a sparse symmetric A (n x n), find the nev
+ * algebraically smallest eigenpairs A V = V Lambda.  Method: LOBPCG with
+ * soft locking (Algorithm 3) or subspace iteration with a Chebyshev filter in
+ * place of the shift-and-invert solve (Algorithm 1), inside the shrink-and-
+ * expand framework (Algorithm 5) driven by the fix / slope / slopek strategies
+ * (Algorithms 6 and 7) after a warm-up (end of Sec. 3.2).
+ *
+ * Conventions for every entry point:
+ *  - Return value: an EIG_* status; 0 is success.  eig_strerror() names it.
+ *    On EIG_EINVAL nothing was launched.  On EIG_ECUDA a CUDA call failed;
+ *    the sticky CUDA error state, if any, is left as CUDA set it.
+ *  - "device" pointers are CUDA global-memory addresses on the current
+ *    device; "host" pointers are ordinary process memory.  The library never
+ *    frees memory it did not allocate.
+ *  - Blocks are row-major: element (i, j) of an n x w block with leading
+ *    dimension ld (in elements, ld >= w) is at p[i*ld + j].
+ *  - Element formats (dtype): EIG_F64 float64; EIG_F32 float32; EIG_DF64
+ *    "double-float": each element is a pair {float hi, float lo} (8 bytes,
+ *    value hi + lo, |lo| <= ulp(hi)/2), the format the FP64 form keeps its
+ *    blocks in so that all block arithmetic runs on the FP32 pipes.
+ *  - stream: a cudaStream_t (NULL = legacy default stream).  Low-level
+ *    kernels are asynchronous on it; eig_solve() blocks until the solve ends.
+ *  - Low-level entry points allocate their temporary device memory with
+ *    cudaMallocAsync/cudaFreeAsync on the given stream.
+ */
+#ifndef EIG_GB300_H
+#define EIG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define EIG_OK 0
+#define EIG_EINVAL 1      /* bad argument (sizes, pointers, options)          */
+#define EIG_ENOMEM 2      /* device allocation failed                         */
+#define EIG_ENOTCONV 3    /* max_iter reached; partial results queryable      */
+#define EIG_EBREAKDOWN 4  /* orthogonalisation lost rank beyond recovery      */
+#define EIG_ECUDA 5       /* a CUDA runtime call failed                       */
+#define EIG_ETIMEOUT 6    /* a bounded device wait expired                    */
+#define EIG_EBUSY 7       /* serving: no free slot                            */
+#define EIG_EREJECT 8     /* serving: request can never fit                   */
+
+/* ---- element formats and arithmetic ----------------------------------- */
+#define EIG_F64 0
+#define EIG_F32 1
+#define EIG_DF64 2
+
+/* arithmetic of the block kernels (SpMM, Gram, update, residual)          */
+#define EIG_ARITH_F64 0   /* float64 blocks, native FP64 FMA                 */
+#define EIG_ARITH_DF64 1  /* double-float blocks, FP32-pipe dd arithmetic    */
+#define EIG_ARITH_F32 2   /* float32 blocks, float32 arithmetic              */
+#define EIG_ARITH_C32 3   /* float32 blocks, compensated (Dot2) accumulation */
+
+/* ---- conversions ------------------------------------------------------- */
+/* dst[i] = src[i] for i < count, converting between EIG_F64 / EIG_F32 /
+ * EIG_DF64 elements (device pointers; src and dst must not overlap). */
+int eig_convert(int64_t count, const void *src, int src_dtype, void *dst, int dst_dtype,
+                void *stream);
+
+/* ---- a7 / a13: sparse block product (Algorithms 1-3: A X, A W, A S) ----
+ * Y = alpha * A V + beta * V + gamma * U, A in CSR with int32 rowptr[n+1],
+ * colind[nnz] and values val[nnz] (all device).  V, U, Y are n x w blocks of
+ * format dtype (U may be NULL when gamma == 0); val is float64 when dtype is
+ * EIG_F64, float32 for EIG_F32 and double-float for EIG_DF64.  Y must not
+ * overlap V or U.  The three-term form is one step of the Chebyshev
+ * recurrence.  w <= 1024. */
+int eig_spmm(int64_t n, const int32_t *rowptr, const int32_t *colind, const void *val,
+             int dtype, int w, const void *V, int64_t ldv, void *Y, int64_t ldy, double alpha,
+             double beta, const void *U, int64_t ldu, double gamma, void *stream);
+
+/* ---- a4 / a5 / a8: tall-skinny Gram product (X^T A X, S^T A S, [X,P]^T W)
+ * G = U^T V (a x b, float64 row-major with leading dimension ldg, device),
+ * U: n x a, V: n x b blocks in the element format that arith implies.
+ * sym != 0 declares U^T V symmetric (U == V, or U^T A U with symmetric A):
+ * only the upper tile triangle is computed and mirrored.  The reduction over
+ * n is split across CTAs into float64 partial tiles held in temporary device
+ * memory and summed in a fixed order (deterministic).  a, b <= 4096. */
+int eig_gram(int64_t n, int a, int b, const void *U, int64_t ldu, const void *V, int64_t ldv,
+             int arith, int sym, double *G, int64_t ldg, void *stream);
+
+/* ---- a4 / a11: block update (X <- S C_X, P <- S C_P, W <- W - Q C) ------
+ * Y = U C + beta * Y.  U: n x s block, C: s x c float64 row-major (device,
+ * leading dimension ldc), Y: n x c block; U and Y use the element format of
+ * arith.  Y must not overlap U. */
+int eig_block_update(int64_t n, int s, int c, const void *U, int64_t ldu, const double *C,
+                     int64_t ldc, void *Y, int64_t ldy, double beta, int arith, void *stream);
+
+/* ---- a1 / a2: residual, norms and preconditioning (Eq. conv / rk) -------
+ * R = T (AX - X diag(lam)) for the w columns, T = diag(tdiag) (tdiag NULL:
+ * identity).  X, AX, R: n x w blocks of format dtype; lam: float64[w]
+ * (device); tdiag: n values of format dtype (device) or NULL.  Writes
+ * xnorm2[j] = ||x_j||^2 and rnorm2[j] = ||AX_j - lam_j X_j||^2 (before T),
+ * float64 device arrays of length w.  R may be NULL (norms only). */
+int eig_residual(int64_t n, int w, const void *X, int64_t ldx, const void *AX, int64_t ldax,
+                 const double *lam, const void *tdiag, void *R, int64_t ldr, double *xnorm2,
+                 double *rnorm2, int dtype, void *stream);
+
+/* ---- a5: CholeskyQR2 in place ("orthogonalize", Algorithms 1-3) --------
+ * W (n x w, format of arith) <- W R^{-1} twice, R from the float64 Cholesky
+ * factor of the Gram matrix; on breakdown the shifted form of Fukaya et al.
+ * (2020) and a third pass.  *status_out (host, may be NULL) receives 0 (plain),
+ * 1 (shift used) after the stream is synchronised.  w <= 1024. */
+int eig_cholqr2(int64_t n, int w, void *W, int64_t ldw, int arith, int *status_out,
+                void *stream);
+
+/* ---- a9: small dense symmetric eigensolver (Rayleigh-Ritz, Algorithms 1-3)
+ * A (s x s float64, device, symmetric, leading dimension lda) = Z diag(lam) Z^T
+ * with lam ascending.  lam: float64[s], Z: s x s float64 row-major (columns are
+ * eigenvectors), both device.  Householder tridiagonalisation, implicit QL
+ * with Wilkinson shifts, back-transformation; float64 throughout.  A is not
+ * modified.  s <= 4096. */
+int eig_syev(int s, const double *A, int64_t lda, double *lam, double *Z, int64_t ldz,
+             void *stream);
+
+/* ---- a10: improved Hetmaniuk-Lehoucq basis selection (Algorithm 3) -----
+ * Given all s eigenvectors Z (s x s, ascending), C_P = Z(:, nnow:s) Q with Q the
+ * orthonormal Householder factor of Z(nlock:nnow, nnow:s)^T; CP is s x
+ * (nnow - nlock) float64 row-major (device).  Requires s - nnow >= nnow - nlock. */
+int eig_hl_trick(int s, int nnow, int nlock, const double *Z, int64_t ldz, double *CP,
+                 int64_t ldcp, void *stream);
+
+/* ---- whole solves: eig_create / eig_solve / eig_query ------------------ */
+typedef struct {
+  int64_t n, nnz;
+  const int32_t *rowptr;  /* n + 1 */
+  const int32_t *colind;  /* nnz   */
+  const double *val;      /* nnz, float64 */
+  int on_device;          /* 1: the three arrays are device pointers (borrowed,
+                             must outlive the handle); 0: host (copied)     */
+} eig_csr;
+
+#define EIG_NONE 0     /* fixed block width                                  */
+#define EIG_FIX 1      /* Algorithm 6                                         */
+#define EIG_SLOPE 2    /* Algorithm 7 with Eq. ckslope                        */
+#define EIG_SLOPEK 3   /* Algorithm 7 with Eq. ckslopek                       */
+
+#define EIG_LOBPCG 0   /* Algorithm 3                                         */
+#define EIG_CHEB_SI 1  /* Algorithm 1, Chebyshev filter for the solve         */
+
+#define EIG_FORM_DF64 0   /* blocks in double-float, FP32-pipe arithmetic      */
+#define EIG_FORM_F64 1    /* blocks in float64, native FP64 arithmetic          */
+#define EIG_FORM_MIXED 2  /* float32 blocks until r <= mixed_switch, then DF64 */
+
+typedef struct {
+  int algo;            /* EIG_LOBPCG                                          */
+  int form;            /* EIG_FORM_DF64                                       */
+  double tol;          /* 1e-10: stop when r^(j) <= tol (Eq. rk)              */
+  int max_iter;        /* 1000                                                */
+  int nes;             /* nev + 5; 0 = default                                */
+  int je, js, jp;      /* 12, 2, 10                                           */
+  int j_warm;          /* 5                                                   */
+  double mu;           /* 1.1                                                 */
+  double r_warm;       /* 1e-4                                                */
+  int cheb_degree;     /* 12                                                  */
+  double cheb_upper;   /* upper bound of the spectrum (0 = normA)             */
+  int precond;         /* 0 none, 1 Jacobi T = diag(A)^{-1}                   */
+  int deflate_ones;    /* 1: keep every block orthogonal to 1/sqrt(n)         */
+  double normA;        /* ||A||_2 used by Eq. conv; must be > 0               */
+  double mixed_switch; /* 1e-5: residual at which MIXED promotes to DF64      */
+  const double *X0;    /* n x k_max float64 row-major initial block (required)*/
+  int x0_on_device;    /* 1: X0 is a device pointer                           */
+  void *stream;        /* cudaStream_t the solve runs on                      */
+} eig_options;
+
+typedef struct {
+  int status;          /* EIG_OK or EIG_ENOTCONV / error of the last solve    */
+  int iters;           /* iterations j performed                               */
+  int n_shrink, n_expand;
+  int nev;
+  const double *lambda;   /* host, nev ascending (owned by the handle)        */
+  const double *resid;    /* host, nev: ||A v - lambda v|| / normA (float64)  */
+  const double *V;        /* device, n x nev float64 row-major (owned)        */
+  const double *history;  /* host, r^(j) for j = 1..iters                     */
+  const int *widths;      /* host, active width nnow at each iteration        */
+  double time_ms;         /* wall time of eig_solve                            */
+  double normA;
+} eig_result;
+
+typedef struct eig_handle eig_handle;
+
+/* Fill *opt with the defaults listed above (X0 NULL, normA 0). */
+int eig_options_default(eig_options *opt);
+
+/* Validate and allocate a solver for the nev smallest eigenpairs with
+ * initial/expanded width k_max (nex).  Requires 1 <= nev <= nes < k_max <= n,
+ * opt->X0 != NULL and opt->normA > 0.  Device memory: about
+ * (8 + 4 k_max) n 8-byte words plus the CSR (DF64 and F64 forms). */
+int eig_create(const eig_csr *A, int nev, int k_max, int strategy, const eig_options *opt,
+               eig_handle **out);
+/* Run the solve from X0; blocks until done.  Returns EIG_OK or EIG_ENOTCONV
+ * (results of the last iteration are kept) or an error. */
+int eig_solve(eig_handle *h);
+int eig_query(const eig_handle *h, eig_result *out);
+void eig_destroy(eig_handle *h);
+const char *eig_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EIG_GB300_H */

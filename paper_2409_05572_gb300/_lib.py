@@ -1,0 +1,308 @@
+"""ctypes binding of ``libeig_gb300.so`` (C ABI in include/eig_gb300.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+Device arrays are passed as torch CUDA tensors (their ``data_ptr``); the
+double-float (DF64) element format is carried as float32 tensors whose last
+dimension holds the {hi, lo} pair.  There is no CPU fallback: a missing or
+unloadable library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libeig_gb300.so")
+
+# status codes / formats (eig_gb300.h)
+EIG_OK, EIG_EINVAL, EIG_ENOMEM, EIG_ENOTCONV, EIG_EBREAKDOWN, EIG_ECUDA, EIG_ETIMEOUT = range(7)
+EIG_F64, EIG_F32, EIG_DF64 = 0, 1, 2
+ARITH_F64, ARITH_DF64, ARITH_F32, ARITH_C32 = 0, 1, 2, 3
+STRATEGIES = {"none": 0, "fix": 1, "slope": 2, "slopek": 3}
+ALGOS = {"lobpcg": 0, "chebsi": 1}
+FORMS = {"df64": 0, "f64": 1, "mixed": 2}
+
+EXPORTS = ("eig_convert", "eig_spmm", "eig_gram", "eig_block_update", "eig_residual", "eig_cholqr2",
+           "eig_syev", "eig_hl_trick", "eig_options_default", "eig_create", "eig_solve", "eig_query",
+           "eig_destroy", "eig_strerror")
+
+
+class EigError(RuntimeError):
+    def __init__(self, fn, code, msg):
+        super().__init__(f"{fn} failed: {msg} (status {code})")
+        self.code = code
+
+
+class eig_csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("colind", C.c_void_p),
+                ("val", C.c_void_p), ("on_device", C.c_int)]
+
+
+class eig_options(C.Structure):
+    _fields_ = [("algo", C.c_int), ("form", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
+                ("nes", C.c_int), ("je", C.c_int), ("js", C.c_int), ("jp", C.c_int), ("j_warm", C.c_int),
+                ("mu", C.c_double), ("r_warm", C.c_double), ("cheb_degree", C.c_int),
+                ("cheb_upper", C.c_double), ("precond", C.c_int), ("deflate_ones", C.c_int),
+                ("normA", C.c_double), ("mixed_switch", C.c_double), ("X0", C.c_void_p),
+                ("x0_on_device", C.c_int), ("stream", C.c_void_p)]
+
+
+class eig_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("n_shrink", C.c_int), ("n_expand", C.c_int),
+                ("nev", C.c_int), ("lambda_", C.POINTER(C.c_double)), ("resid", C.POINTER(C.c_double)),
+                ("V", C.c_void_p), ("history", C.POINTER(C.c_double)), ("widths", C.POINTER(C.c_int)),
+                ("time_ms", C.c_double), ("normA", C.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                           "(the CUDA library is required; there is no CPU fallback)")
+    lib = C.CDLL(path)
+    p, i64, i32, d = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    sig = {
+        "eig_convert": [i64, p, i32, p, i32, p],
+        "eig_spmm": [i64, p, p, p, i32, i32, p, i64, p, i64, d, d, p, i64, d, p],
+        "eig_gram": [i64, i32, i32, p, i64, p, i64, i32, i32, p, i64, p],
+        "eig_block_update": [i64, i32, i32, p, i64, p, i64, p, i64, d, i32, p],
+        "eig_residual": [i64, i32, p, i64, p, i64, p, p, p, i64, p, p, i32, p],
+        "eig_cholqr2": [i64, i32, p, i64, i32, C.POINTER(C.c_int), p],
+        "eig_syev": [i32, p, i64, p, p, i64, p],
+        "eig_hl_trick": [i32, i32, i32, p, i64, p, i64, p],
+        "eig_options_default": [C.POINTER(eig_options)],
+        "eig_create": [C.POINTER(eig_csr), i32, i32, i32, C.POINTER(eig_options), C.POINTER(C.c_void_p)],
+        "eig_solve": [p],
+        "eig_query": [p, C.POINTER(eig_result)],
+        "eig_destroy": [p],
+        "eig_strerror": [i32],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.eig_destroy.restype = None
+    lib.eig_strerror.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(fn, code):
+    if code != EIG_OK:
+        raise EigError(fn, code, load().eig_strerror(code).decode())
+    return code
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _fmt(t, dtype_code=None):
+    """Element format of a tensor: float64 -> F64, float32 with trailing
+    pair dimension -> DF64 when requested, float32 -> F32."""
+    import torch
+    if dtype_code is not None:
+        return dtype_code
+    if t.dtype == torch.float64:
+        return EIG_F64
+    if t.dtype == torch.float32:
+        return EIG_F32
+    raise TypeError(t.dtype)
+
+
+# ---------------------------------------------------------------------------
+# format helpers
+# ---------------------------------------------------------------------------
+def to_df64(x, stream=None):
+    """float64 CUDA tensor -> double-float tensor (..., 2) float32."""
+    import torch
+    x = x.contiguous()
+    out = torch.empty(*x.shape, 2, dtype=torch.float32, device=x.device)
+    _check("eig_convert", load().eig_convert(x.numel(), _ptr(x), EIG_F64, _ptr(out), EIG_DF64, _stream(stream)))
+    return out
+
+
+def from_df64(x, stream=None):
+    import torch
+    x = x.contiguous()
+    out = torch.empty(*x.shape[:-1], dtype=torch.float64, device=x.device)
+    _check("eig_convert", load().eig_convert(out.numel(), _ptr(x), EIG_DF64, _ptr(out), EIG_F64, _stream(stream)))
+    return out
+
+
+def convert(src, src_dtype, dst, dst_dtype, count, stream=None):
+    return _check("eig_convert", load().eig_convert(count, _ptr(src), src_dtype, _ptr(dst), dst_dtype,
+                                                    _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# step-level entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def eig_spmm(n, rowptr, colind, val, dtype, w, V, ldv, Y, ldy, alpha=1.0, beta=0.0, U=None, ldu=0,
+             gamma=0.0, stream=None):
+    return _check("eig_spmm", load().eig_spmm(n, _ptr(rowptr), _ptr(colind), _ptr(val), dtype, w, _ptr(V), ldv,
+                                              _ptr(Y), ldy, alpha, beta, _ptr(U), ldu, gamma, _stream(stream)))
+
+
+def eig_gram(n, a, b, U, ldu, V, ldv, arith, sym, G, ldg, stream=None):
+    return _check("eig_gram", load().eig_gram(n, a, b, _ptr(U), ldu, _ptr(V), ldv, arith, int(sym), _ptr(G), ldg,
+                                              _stream(stream)))
+
+
+def eig_block_update(n, s, c, U, ldu, Cm, ldc, Y, ldy, beta, arith, stream=None):
+    return _check("eig_block_update", load().eig_block_update(n, s, c, _ptr(U), ldu, _ptr(Cm), ldc, _ptr(Y), ldy,
+                                                              beta, arith, _stream(stream)))
+
+
+def eig_residual(n, w, X, ldx, AX, ldax, lam, tdiag, R, ldr, xnorm2, rnorm2, dtype, stream=None):
+    return _check("eig_residual", load().eig_residual(n, w, _ptr(X), ldx, _ptr(AX), ldax, _ptr(lam), _ptr(tdiag),
+                                                      _ptr(R), ldr, _ptr(xnorm2), _ptr(rnorm2), dtype,
+                                                      _stream(stream)))
+
+
+def eig_cholqr2(n, w, W, ldw, arith, stream=None):
+    st = C.c_int(0)
+    _check("eig_cholqr2", load().eig_cholqr2(n, w, _ptr(W), ldw, arith, C.byref(st), _stream(stream)))
+    return st.value
+
+
+def eig_syev(s, A, lda, lam, Z, ldz, stream=None):
+    return _check("eig_syev", load().eig_syev(s, _ptr(A), lda, _ptr(lam), _ptr(Z), ldz, _stream(stream)))
+
+
+def eig_hl_trick(s, nnow, nlock, Z, ldz, CP, ldcp, stream=None):
+    return _check("eig_hl_trick", load().eig_hl_trick(s, nnow, nlock, _ptr(Z), ldz, _ptr(CP), ldcp,
+                                                      _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# whole solves: eig_create / eig_solve / eig_query
+# ---------------------------------------------------------------------------
+class Solver:
+    """Owns an eig_handle.  ``A`` is a workloads.CSR (host arrays, copied to
+    the device) or a tuple of CUDA tensors (rowptr int32, colind int32,
+    val float64) that must outlive the solver."""
+
+    def __init__(self, A, nev, k_max, strategy="fix", X0=None, normA=None, algo="lobpcg", form="df64",
+                 tol=1e-10, max_iter=1000, nes=0, stream=None, **kw):
+        lib = load()
+        self._keep = []
+        csr = eig_csr()
+        if isinstance(A, tuple):
+            rp, ci, va = A
+            csr.n, csr.nnz = rp.numel() - 1, ci.numel()
+            csr.rowptr, csr.colind, csr.val = rp.data_ptr(), ci.data_ptr(), va.data_ptr()
+            csr.on_device = 1
+            self._keep += [rp, ci, va]
+        else:
+            rp = np.ascontiguousarray(A.indptr, dtype=np.int32)
+            ci = np.ascontiguousarray(A.indices, dtype=np.int32)
+            va = np.ascontiguousarray(A.data, dtype=np.float64)
+            self._keep += [rp, ci, va]
+            csr.n, csr.nnz = A.n, ci.size
+            csr.rowptr, csr.colind, csr.val = rp.ctypes.data, ci.ctypes.data, va.ctypes.data
+            csr.on_device = 0
+        opt = eig_options()
+        lib.eig_options_default(C.byref(opt))
+        opt.algo = ALGOS[algo]
+        opt.form = FORMS[form]
+        opt.tol = tol
+        opt.max_iter = max_iter
+        opt.nes = nes
+        for k, v in kw.items():
+            if not hasattr(opt, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(opt, k, v)
+        if normA is None:
+            raise ValueError("normA is required (the matrix 2-norm of Eq. conv)")
+        opt.normA = float(normA)
+        if X0 is None:
+            raise ValueError("X0 (n x k_max float64) is required")
+        if hasattr(X0, "data_ptr"):
+            opt.X0 = X0.data_ptr()
+            opt.x0_on_device = 1
+            self._keep.append(X0)
+        else:
+            x0 = np.ascontiguousarray(X0, dtype=np.float64)
+            self._keep.append(x0)
+            opt.X0 = x0.ctypes.data
+            opt.x0_on_device = 0
+        opt.stream = _stream(stream).value if stream is not None or _torch_cuda() else None
+        self.n, self.nev = csr.n, nev
+        h = C.c_void_p()
+        _check("eig_create", lib.eig_create(C.byref(csr), nev, k_max, STRATEGIES[strategy], C.byref(opt),
+                                            C.byref(h)))
+        self._h = h
+
+    def solve(self):
+        code = load().eig_solve(self._h)
+        if code not in (EIG_OK, EIG_ENOTCONV):
+            _check("eig_solve", code)
+        return self.query()
+
+    def query(self):
+        r = eig_result()
+        _check("eig_query", load().eig_query(self._h, C.byref(r)))
+        nev, it = r.nev, r.iters
+        out = {
+            "status": r.status, "iters": it, "n_shrink": r.n_shrink, "n_expand": r.n_expand,
+            "lam": np.ctypeslib.as_array(r.lambda_, (nev,)).copy() if r.lambda_ else None,
+            "resid": np.ctypeslib.as_array(r.resid, (nev,)).copy() if r.resid else None,
+            "history": np.ctypeslib.as_array(r.history, (it,)).copy() if r.history and it else np.zeros(0),
+            "widths": (np.ctypeslib.as_array(r.widths, (max(it - (1 if r.status == EIG_OK else 0), 0),)).copy()
+                       if r.widths else np.zeros(0, dtype=np.int32)),
+            "time_ms": r.time_ms, "V_ptr": r.V,
+        }
+        return out
+
+    def V(self):
+        """n x nev float64 CUDA tensor copy of the eigenvectors."""
+        import torch
+        r = eig_result()
+        _check("eig_query", load().eig_query(self._h, C.byref(r)))
+        out = torch.empty(self.n, self.nev, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        _cuda_copy_d2d(out.data_ptr(), r.V, out.numel() * 8)
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().eig_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _torch_cuda():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def _cuda_copy_d2d(dst, src, nbytes):
+    """Device-to-device copy through the library's conversion entry point
+    (float64 -> float64)."""
+    _check("eig_convert", load().eig_convert(nbytes // 8, C.c_void_p(src), EIG_F64, C.c_void_p(dst), EIG_F64,
+                                             _stream(None)))

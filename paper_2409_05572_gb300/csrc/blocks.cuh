@@ -1,0 +1,70 @@
+// Internal (C++) interface of the n-sized block kernels: SpMM, Gram, block
+// update, residual, conversions.  Explicitly instantiated in k_blocks.cu.
+#pragma once
+#include "common.cuh"
+
+namespace eig {
+
+template <Arith A>
+struct Csr {
+  int64_t n = 0;
+  const int32_t* rowptr = nullptr;
+  const int32_t* colind = nullptr;
+  const typename Pol<A>::T* val = nullptr;
+};
+
+// Y = alpha A V + beta V + gamma U (single-segment n x w views)
+template <Arith A>
+cudaError_t spmm(const Csr<A>& M, int w, const typename Pol<A>::T* V, int64_t ldv,
+                 typename Pol<A>::T* Y, int64_t ldy, double alpha, double beta,
+                 const typename Pol<A>::T* U, int64_t ldu, double gamma, cudaStream_t st);
+
+// Scratch (float64 elements) that gram() needs for its split-K partial tiles.
+size_t gram_scratch_elems(int64_t n, int a, int b, bool sym);
+
+// G (a x b, float64, ldg) = U^T V; scratch from gram_scratch_elems().
+template <Arith A>
+cudaError_t gram(int64_t n, const Blk<typename Pol<A>::T>& U, const Blk<typename Pol<A>::T>& V,
+                 bool sym, double* G, int64_t ldg, double* scratch, cudaStream_t st,
+                 const int* gate = nullptr);
+
+// Cs[i][j] (leading dimension ldo) = staged(scale * C[i][j]) for an s x c
+// float64 matrix.
+template <Arith A>
+cudaError_t stage_coef(int s, int c, const double* C, int64_t ldc, typename Pol<A>::S* Cs,
+                       int64_t ldo, double scale, cudaStream_t st, const int* gate = nullptr);
+
+// Y = a U + b V elementwise (n x w views; Y may alias U or V).
+template <Arith A>
+cudaError_t axpby(int64_t n, int w, const typename Pol<A>::T* U, int64_t ldu, double a,
+                  const typename Pol<A>::T* V, int64_t ldv, double b, typename Pol<A>::T* Y,
+                  int64_t ldy, cudaStream_t st);
+
+// dst = src over n rows (equal widths), skipped when *gate == 0.
+template <typename T>
+cudaError_t copy_blk(int64_t n, const Blk<T>& src, const Blk<T>& dst, cudaStream_t st,
+                     const int* gate = nullptr);
+
+// Y = U Cs + beta Y, Cs staged s x c (leading dimension c); Y must not
+// overlap U.
+template <Arith A>
+cudaError_t update(int64_t n, const Blk<typename Pol<A>::T>& U, const typename Pol<A>::S* Cs,
+                   int c, const Blk<typename Pol<A>::T>& Y, double beta, cudaStream_t st,
+                   const int* gate = nullptr);
+
+// Scratch (float64 elements) for residual(): 2 * blocks * w.
+size_t residual_scratch_elems(int64_t n, int w);
+
+// R = T (AX - X diag(lam)); xnorm2, rnorm2 (float64, device, length w).
+template <Arith A>
+cudaError_t residual(int64_t n, int w, const typename Pol<A>::T* X, int64_t ldx,
+                     const typename Pol<A>::T* AX, int64_t ldax, const double* lam,
+                     const typename Pol<A>::T* tdiag, typename Pol<A>::T* R, int64_t ldr,
+                     double* xnorm2, double* rnorm2, double* scratch, cudaStream_t st);
+
+// Elementwise format conversion between float64, float32 and double-float
+// for a rows x cols block (row-major, own leading dimensions).
+cudaError_t convert2d(int64_t rows, int64_t cols, const void* src, int64_t lds, int sdt, void* dst,
+                      int64_t ldd, int ddt, cudaStream_t st);
+
+}  // namespace eig

@@ -1,0 +1,25 @@
+// Internal (C++) interface of the small dense float64 kernels (k_small.cu).
+#pragma once
+#include "common.cuh"
+
+namespace eig {
+
+// R^{-1} (w x w upper, leading dimension w) of the Cholesky factor of G;
+// *status: 0 plain, 1 shifted (Fukaya et al. 2020), 2 broken down.  work:
+// (w*w + w) doubles, used when the factor does not fit in shared memory.
+cudaError_t chol_rinv(int w, int64_t nrows, const double* G, int64_t ldg, double* Rinv, double* work,
+                      int* status, cudaStream_t st, const int* gate = nullptr);
+
+// A = Z diag(lam) Z^T, lam ascending; work of syev_work_bytes(s) bytes;
+// *status_dev: 0 ok, 1 QL did not converge, 2 rotation list overflow.
+size_t syev_work_bytes(int s);
+cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
+                 int* status_dev, cudaStream_t st);
+
+// improved Hetmaniuk-Lehoucq: CP = Z(:, nnow:s) Q, Q from Householder QR of
+// Z(nlock:nnow, nnow:s)^T; work of hl_work_bytes() bytes.
+size_t hl_work_bytes(int s, int nnow, int nlock);
+cudaError_t hl_trick(int s, int nnow, int nlock, const double* Z, int64_t ldz, double* CP, int64_t ldcp,
+                     void* work, cudaStream_t st);
+
+}  // namespace eig

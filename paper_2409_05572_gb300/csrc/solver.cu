@@ -1,0 +1,954 @@
+// Host drivers of the block eigensolvers and the C ABI (include/eig_gb300.h).
+//
+// LOBPCG with soft locking (arXiv:2409.05572, Algorithm 3) and subspace
+// iteration with a Chebyshev filter (Algorithm 1), both inside the
+// shrink-and-expand framework (Algorithm 5) driven by the fix / slope / slopek
+// strategies (Algorithms 6 and 7).  Every n-sized step runs in this library's
+// kernels on one stream; the host crosses to the device once per iteration to
+// read the residual norms of Eq. conv (a few hundred bytes) and takes the
+// strategy decision.
+//
+// Device layout: S = [X | P | W] and AS = [AX | AP | AW] live in row-major
+// n x LDS buffers (LDS = 3 k_max rounded up to 4) with X at column 0, P at
+// k_max, W at 2 k_max; two copies of each are used in turn (the block update
+// reads S and writes the next X, P).  Active columns are prefixes (plus a
+// column offset for P after soft locking), so shrinking and expanding are
+// width changes; S_drop is kept in its own n x 2(k_max - nes) buffer.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <type_traits>
+#include <vector>
+
+#include "blocks.cuh"
+#include "small.cuh"
+
+using namespace eig;
+
+// ---------------------------------------------------------------------------
+// Shrink-and-expand strategies (Algorithms 6 and 7, Eqs. ckslope/ckslopek,
+// warm-up rule).  Readings: the fix clock starts at the first shrink j0
+// (expansions when (j - j0 + js) mod je == 0 with nnow == nes, shrinks when
+// (j - j0) mod je == 0 with nnow > nes); slope/slopek shrink js iterations
+// after each expansion and expand when mu * c < c_max, c_max being the largest
+// slope since the last shrink including the current one.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct SEStrategy {
+  int kind = EIG_NONE, nes = 0, nex = 0;
+  int je = 12, js = 2, jp = 10, j_warm = 5;
+  double mu = 1.1, r_warm = 1e-4;
+  std::vector<double> r;  // r[j] for j >= 1 (r[0] unused)
+  bool warmed = false;
+  int j0 = -1, j_exp = -1;
+  bool has_cmax = false;
+  double c_max = 0.0;
+  int n_shrink = 0, n_expand = 0;
+
+  static double lg(double x) { return std::log10(std::max(x, 1e-300)); }
+  void record(int j, double rj) {
+    if ((int)r.size() <= j) r.resize(j + 1, -1.0);
+    r[j] = rj;
+  }
+  bool have(int j) const { return j >= 1 && j < (int)r.size() && r[j] >= 0.0; }
+  bool slope(int j, double* c) const {
+    if (kind == EIG_SLOPE) {
+      if (!have(j - 1)) return false;
+      *c = lg(r[j - 1]) - lg(r[j]);
+      return true;
+    }
+    if (kind == EIG_SLOPEK) {
+      if (j < jp || !have(j - jp)) return false;
+      *c = (lg(r[j - jp]) - lg(r[j])) / jp;
+      return true;
+    }
+    return false;
+  }
+  bool ifexpand(int j, int nnow) {
+    if (kind == EIG_NONE || !warmed) return false;
+    bool go = false;
+    if (kind == EIG_FIX) {
+      go = nnow == nes && ((j - j0 + js) % je) == 0;
+    } else {
+      double c;
+      if (nnow == nes && slope(j, &c)) {
+        c_max = has_cmax ? std::max(c_max, c) : c;
+        has_cmax = true;
+        go = mu * c < c_max;
+      }
+    }
+    if (go) {
+      j_exp = j;
+      ++n_expand;
+    }
+    return go;
+  }
+  bool ifshrink(int j, int nnow) {
+    if (kind == EIG_NONE || nnow <= nes) return false;
+    bool go;
+    if (!warmed) {
+      go = j >= j_warm && have(j) && r[j] <= r_warm;
+      if (go) {
+        warmed = true;
+        j0 = j;
+      }
+    } else if (kind == EIG_FIX) {
+      go = ((j - j0) % je) == 0;
+    } else {
+      go = j_exp >= 0 && (j - j_exp) == js;
+    }
+    if (go) {
+      has_cmax = false;
+      ++n_shrink;
+    }
+    return go;
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+struct eig_handle {
+  int64_t n = 0, nnz = 0;
+  int nev = 0, kmax = 0, nes = 0, strategy = 0;
+  eig_options opt{};
+  cudaStream_t st = nullptr;
+  int LDS = 0, hdrop = 0, wtw = 0;
+
+  // CSR (device)
+  int32_t *rowptr = nullptr, *colind = nullptr;
+  double* val64 = nullptr;
+  dd* valdd = nullptr;
+  float* val32 = nullptr;
+  bool own_idx = false;
+  // Jacobi diagonal and null vector, per storage format
+  double* t64 = nullptr;
+  dd* tdd = nullptr;
+  float* t32 = nullptr;
+  double* u64 = nullptr;
+  dd* udd = nullptr;
+  float* u32 = nullptr;
+  // n-sized blocks (bytes for 8-byte elements)
+  void* S[2] = {nullptr, nullptr};
+  void* AS[2] = {nullptr, nullptr};
+  void* Wt = nullptr;
+  void* Sd = nullptr;
+  // small float64 work
+  int smax = 0;
+  double *Gp = nullptr, *Rinv = nullptr, *cholw = nullptr, *Z = nullptr, *lamd = nullptr, *CP = nullptr;
+  double *gscr = nullptr, *rscr = nullptr, *xn = nullptr, *rn = nullptr;
+  void* Cs = nullptr;
+  void* syevw = nullptr;
+  void* hlw = nullptr;
+  int* flags = nullptr;  // device: [0..3] CholQR statuses, [4] syev status
+  double* hpin = nullptr;
+  // results
+  double* V = nullptr;
+  std::vector<double> lam, resid, history;
+  std::vector<int> widths;
+  int status = EIG_OK, iters = 0, n_shrink = 0, n_expand = 0;
+  double time_ms = 0.0;
+  cudaError_t cuda_err = cudaSuccess;
+};
+
+#define CK(x)                      \
+  do {                             \
+    cudaError_t e_ = (x);          \
+    if (e_ != cudaSuccess) {       \
+      h->cuda_err = e_;            \
+      return EIG_ECUDA;            \
+    }                              \
+  } while (0)
+
+namespace {
+
+constexpr int F_CHOL1 = 0, F_CHOL2 = 1, F_CHOL3 = 2, F_SYEV = 4, NFLAGS = 8;
+
+template <typename T>
+Blk<T> view(void* base, int64_t ld, int col, int w) {
+  Blk<T> b;
+  b.add(static_cast<T*>(base) + col, ld, w);
+  return b;
+}
+template <typename T>
+Blk<T> cat(const Blk<T>& a, const Blk<T>& b) {
+  Blk<T> r = a;
+  for (int t = 0; t < b.nseg; ++t) r.add(b.ptr[t], b.ld[t], b.start[t + 1] - b.start[t]);
+  return r;
+}
+
+template <Arith A> struct FormData;
+template <> struct FormData<Arith::DF64> {
+  static const dd* val(eig_handle* h) { return h->valdd; }
+  static const dd* tdiag(eig_handle* h) { return h->tdd; }
+  static dd* u0(eig_handle* h) { return h->udd; }
+};
+template <> struct FormData<Arith::F64> {
+  static const double* val(eig_handle* h) { return h->val64; }
+  static const double* tdiag(eig_handle* h) { return h->t64; }
+  static double* u0(eig_handle* h) { return h->u64; }
+};
+template <> struct FormData<Arith::F32> {
+  static const float* val(eig_handle* h) { return h->val32; }
+  static const float* tdiag(eig_handle* h) { return h->t32; }
+  static float* u0(eig_handle* h) { return h->u32; }
+};
+
+// AU: arithmetic of SpMM / update / residual; AG: arithmetic of the Gram
+// products (same storage type).
+template <Arith AU, Arith AG>
+struct Ops {
+  using T = typename Pol<AU>::T;
+  using SU = typename Pol<AU>::S;
+  eig_handle* h;
+  explicit Ops(eig_handle* hh) : h(hh) {}
+  cudaStream_t st() const { return h->st; }
+  Csr<AU> csr() const {
+    Csr<AU> c;
+    c.n = h->n;
+    c.rowptr = h->rowptr;
+    c.colind = h->colind;
+    c.val = FormData<AU>::val(h);
+    return c;
+  }
+  int64_t ld() const { return h->LDS; }
+
+  // G = U^T V into h->Gp (leading dimension b)
+  int gram(const Blk<T>& U, const Blk<T>& V, bool sym, const int* gate = nullptr) {
+    CK(eig::gram<AG>(h->n, U, V, sym, h->Gp, V.width, h->gscr, st(), gate));
+    return EIG_OK;
+  }
+  // Y = U (scale * C) + beta Y with C float64 (s x c, ldc)
+  int upd(const Blk<T>& U, const double* C, int64_t ldc, int c, double scale, const Blk<T>& Y, double beta,
+          const int* gate = nullptr) {
+    CK(stage_coef<AU>(U.width, c, C, ldc, static_cast<SU*>(h->Cs), c, scale, st(), gate));
+    CK(eig::update<AU>(h->n, U, static_cast<SU*>(h->Cs), c, Y, beta, st(), gate));
+    return EIG_OK;
+  }
+  // one CholeskyQR pass: dst = src R^{-1}; status into flags[slot]
+  int cholqr(const Blk<T>& src, const Blk<T>& dst, int slot, const int* gate = nullptr) {
+    const int w = src.width;
+    int rc = gram(src, src, true, gate);
+    if (rc) return rc;
+    CK(chol_rinv(w, h->n, h->Gp, w, h->Rinv, h->cholw, h->flags + slot, st(), gate));
+    return upd(src, h->Rinv, w, w, 1.0, dst, 0.0, gate);
+  }
+  // project D against Q (D -= Q Q^T D)
+  int project(const Blk<T>& Q, const Blk<T>& D) {
+    if (Q.width == 0) return EIG_OK;
+    int rc = gram(Q, D, false);
+    if (rc) return rc;
+    return upd(Q, h->Gp, D.width, D.width, -1.0, D, 1.0);
+  }
+  // Orthonormal basis of (I - Q Q^T) Dsrc, written to Ddst: two passes of
+  // projection + CholeskyQR (a third CholeskyQR when the first needed the
+  // shift).  Dmid is scratch; Dsrc is clobbered (Ddst may alias Dsrc).
+  int orth(const Blk<T>& Q, const Blk<T>& Dsrc, const Blk<T>& Dmid, const Blk<T>& Ddst) {
+    int rc;
+    if ((rc = project(Q, Dsrc))) return rc;
+    if ((rc = cholqr(Dsrc, Dmid, F_CHOL1))) return rc;
+    // conditional third pass (shifted CholeskyQR3): Dmid -> Dsrc -> Dmid
+    if ((rc = cholqr(Dmid, Dsrc, F_CHOL3, h->flags + F_CHOL1))) return rc;
+    CK(copy_blk<T>(h->n, Dsrc, Dmid, st(), h->flags + F_CHOL1));
+    if ((rc = project(Q, Dmid))) return rc;
+    return cholqr(Dmid, Ddst, F_CHOL2);
+  }
+  int spmm(const T* V, int64_t ldv, int w, T* Y, int64_t ldy) {
+    CK(eig::spmm<AU>(csr(), w, V, ldv, Y, ldy, 1.0, 0.0, nullptr, 0, 0.0, st()));
+    return EIG_OK;
+  }
+  int spmm_blk(const Blk<T>& V, const Blk<T>& Y) {
+    for (int t = 0; t < V.nseg; ++t) {
+      const int w = V.start[t + 1] - V.start[t];
+      // Y has the same segmentation by construction
+      CK(eig::spmm<AU>(csr(), w, V.ptr[t], V.ld[t], Y.ptr[t], Y.ld[t], 1.0, 0.0, nullptr, 0, 0.0, st()));
+    }
+    return EIG_OK;
+  }
+  // Rayleigh-Ritz: Gp = S^T AS, then Z, lamd
+  int rr(const Blk<T>& S, const Blk<T>& ASb) {
+    int rc = gram(S, ASb, true);
+    if (rc) return rc;
+    CK(syev(S.width, h->Gp, S.width, h->lamd, h->Z, S.width, h->syevw, h->flags + F_SYEV, st()));
+    return EIG_OK;
+  }
+  // residual norms (and R into Rdst when non-null); copies norms, lam and
+  // flags to the host and synchronises.
+  int resid(const T* X, const T* AX, int w, T* Rdst, bool precond) {
+    const T* td = precond ? FormData<AU>::tdiag(h) : nullptr;
+    CK(eig::residual<AU>(h->n, w, X, ld(), AX, ld(), h->lamd, td, Rdst, ld(), h->xn, h->rn, h->rscr, st()));
+    CK(cudaMemcpyAsync(h->hpin, h->xn, sizeof(double) * w, cudaMemcpyDeviceToHost, st()));
+    CK(cudaMemcpyAsync(h->hpin + h->kmax, h->rn, sizeof(double) * w, cudaMemcpyDeviceToHost, st()));
+    CK(cudaMemcpyAsync(h->hpin + 2 * h->kmax, h->lamd, sizeof(double) * w, cudaMemcpyDeviceToHost, st()));
+    CK(cudaMemcpyAsync(h->hpin + 3 * h->kmax, h->flags, sizeof(int) * NFLAGS, cudaMemcpyDeviceToHost, st()));
+    CK(cudaStreamSynchronize(st()));
+    return EIG_OK;
+  }
+};
+
+// Eq. conv / Eq. rk from the host copies of the norms
+struct ConvInfo {
+  double r = 0.0;
+  int nlock = 0;
+  bool breakdown = false;
+};
+
+ConvInfo conv_test(eig_handle* h, int w) {
+  ConvInfo ci;
+  const double* xn = h->hpin;
+  const double* rn = h->hpin + h->kmax;
+  const double* lam = h->hpin + 2 * h->kmax;
+  const int* fl = reinterpret_cast<const int*>(h->hpin + 3 * h->kmax);
+  const double nA = h->opt.normA;
+  double r = 0.0;
+  bool prefix = true;
+  for (int i = 0; i < h->nev && i < w; ++i) {
+    const double x = std::sqrt(std::max(xn[i], 0.0));
+    const double rho = std::sqrt(std::max(rn[i], 0.0)) / (nA * x + x * std::fabs(lam[i]));
+    const double rr = std::isfinite(rho) ? rho : 1e300;
+    r = std::max(r, rr);
+    if (prefix && rr <= h->opt.tol)
+      ++ci.nlock;
+    else
+      prefix = false;
+  }
+  ci.r = r;
+  ci.breakdown = fl[F_CHOL1] == 2 || fl[F_CHOL2] == 2 || fl[F_CHOL3] == 2 || fl[F_SYEV] != 0;
+  return ci;
+}
+
+int finish(eig_handle* h, int status);
+
+// ---------------------------------------------------------------------------
+// LOBPCG with soft locking and shrink-and-expand (Algorithm 3).
+// Phase state carried between precision phases of the mixed form.
+// ---------------------------------------------------------------------------
+struct LState {
+  int cur = 0;       // which S / AS buffer holds the iterate
+  int nnow = 0;      // active width of X
+  int np = 0;        // width of P
+  int poff = 0;      // column offset of P inside its slot
+  int nlock = 0;
+  bool have_drop = false;
+  int j = 0;         // last iteration done
+  SEStrategy se;
+};
+
+template <Arith AU, Arith AG>
+int lobpcg_init(eig_handle* h, LState& L) {
+  using T = typename Pol<AU>::T;
+  Ops<AU, AG> o(h);
+  const int64_t ld = h->LDS;
+  const int k = h->kmax;
+  // X0 (host or device float64) -> device staging in S[1] -> X slot of S[0]
+  // in the element format of the phase
+  CK(cudaMemcpyAsync(h->S[1], h->opt.X0, sizeof(double) * size_t(h->n) * k, cudaMemcpyDefault, h->st));
+  const int fmt = sizeof(T) == 4 ? EIG_F32 : (std::is_same<T, dd>::value ? EIG_DF64 : EIG_F64);
+  CK(convert2d(h->n, k, h->S[1], k, EIG_F64, h->S[0], ld, fmt, h->st));
+  Blk<T> X = view<T>(h->S[0], ld, 0, k);
+  Blk<T> Q;
+  if (h->opt.deflate_ones) Q.add(FormData<AU>::u0(h), 1, 1);
+  Blk<T> mid = view<T>(h->Wt, h->wtw, 0, k);
+  Blk<T> Xd = view<T>(h->S[1], ld, 0, k);
+  int rc = o.orth(Q, X, mid, Xd);  // orthonormal X0 in S[1]
+  if (rc) return rc;
+  Blk<T> AX = view<T>(h->AS[1], ld, 0, k);
+  if ((rc = o.spmm_blk(Xd, AX))) return rc;
+  if ((rc = o.rr(Xd, AX))) return rc;
+  // X <- X Z, AX <- AX Z into buffer 0
+  if ((rc = o.upd(Xd, h->Z, k, k, 1.0, view<T>(h->S[0], ld, 0, k), 0.0))) return rc;
+  if ((rc = o.upd(AX, h->Z, k, k, 1.0, view<T>(h->AS[0], ld, 0, k), 0.0))) return rc;
+  L.cur = 0;
+  L.nnow = k;
+  L.np = 0;
+  L.poff = 0;
+  L.nlock = 0;
+  L.have_drop = false;
+  L.j = 0;
+  return EIG_OK;
+}
+
+// Runs iterations until convergence, max_iter, or (when switch_r > 0) the
+// residual falls to switch_r; returns EIG_OK with *done set on convergence.
+template <Arith AU, Arith AG>
+int lobpcg_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* switched) {
+  using T = typename Pol<AU>::T;
+  Ops<AU, AG> o(h);
+  const int64_t ld = h->LDS;
+  const int k = h->kmax, nes = h->nes;
+  const bool pre = h->opt.precond != 0;
+  *done = false;
+  *switched = false;
+  int rc;
+  while (L.j < h->opt.max_iter) {
+    const int j = L.j + 1;
+    void* Sc = h->S[L.cur];
+    void* ASc = h->AS[L.cur];
+    T* X = static_cast<T*>(Sc);
+    T* AX = static_cast<T*>(ASc);
+    T* Wslot = X + 2 * k;
+    // R = T (AX - X Lambda) into the W slot, norms to the host
+    if ((rc = o.resid(X, AX, L.nnow, Wslot, pre))) return rc;
+    ConvInfo ci = conv_test(h, L.nnow);
+    if (ci.breakdown) return EIG_EBREAKDOWN;
+    h->history.push_back(ci.r);
+    L.se.record(j, ci.r);
+    L.j = j;
+    h->iters = j;
+    if (ci.r <= h->opt.tol) {
+      *done = true;
+      return EIG_OK;
+    }
+    if (switch_r > 0.0 && ci.r <= switch_r) {
+      // hand over before doing this iteration's update in the next form
+      L.j = j - 1;
+      h->history.pop_back();
+      L.se.r.resize(j);
+      *switched = true;
+      return EIG_OK;
+    }
+    // soft locking: drop the P columns of newly locked X columns
+    if (ci.nlock > L.nlock) {
+      const int d = std::min(ci.nlock - L.nlock, L.np);
+      L.poff += d;
+      L.np -= d;
+    }
+    L.nlock = ci.nlock;
+    const int nw = L.nnow - L.nlock;
+    Blk<T> Xb = view<T>(Sc, ld, 0, L.nnow);
+    Blk<T> Pb = view<T>(Sc, ld, k + L.poff, L.np);
+    Blk<T> Q;
+    if (h->opt.deflate_ones) Q.add(FormData<AU>::u0(h), 1, 1);
+    Q = cat(cat(Q, Xb), Pb);
+    Blk<T> Wb = view<T>(Sc, ld, 2 * k + L.nlock, nw);
+    Blk<T> Wmid = view<T>(h->Wt, h->wtw, 0, nw);
+    if ((rc = o.orth(Q, Wb, Wmid, Wb))) return rc;
+    // expansion: re-orthogonalise S_drop against S, append halves to X and P
+    if (L.se.ifexpand(j, L.nnow)) {
+      if (!L.have_drop) return EIG_EINVAL;
+      const int hd = h->hdrop;
+      // P must be contiguous from the slot start for the append: move it if offset
+      Blk<T> Dsrc = view<T>(h->Sd, 2 * hd, 0, 2 * hd);
+      Blk<T> Dmid = view<T>(h->Wt, h->wtw, 0, 2 * hd);
+      Blk<T> Ddst = cat(view<T>(Sc, ld, L.nnow, hd), view<T>(Sc, ld, k + L.poff + L.np, hd));
+      Blk<T> Sfull = cat(Q, Wb);
+      if ((rc = o.orth(Sfull, Dsrc, Dmid, Ddst))) return rc;
+      Blk<T> ADdst = cat(view<T>(ASc, ld, L.nnow, hd), view<T>(ASc, ld, k + L.poff + L.np, hd));
+      if ((rc = o.spmm_blk(Ddst, ADdst))) return rc;
+      L.nnow += hd;
+      L.np += hd;
+      L.have_drop = false;
+    }
+    Xb = view<T>(Sc, ld, 0, L.nnow);
+    Pb = view<T>(Sc, ld, k + L.poff, L.np);
+    // AW = A W
+    if ((rc = o.spmm(Wslot + L.nlock, ld, nw, static_cast<T*>(ASc) + 2 * k + L.nlock, ld))) return rc;
+    Blk<T> Sb = cat(cat(Xb, Pb), Wb);
+    Blk<T> ASb = cat(cat(view<T>(ASc, ld, 0, L.nnow), view<T>(ASc, ld, k + L.poff, L.np)),
+                     view<T>(ASc, ld, 2 * k + L.nlock, nw));
+    const int s = Sb.width;
+    h->widths.push_back(L.nnow);
+    if ((rc = o.rr(Sb, ASb))) return rc;
+    // improved Hetmaniuk-Lehoucq: C = [Z(:, :nnow) | C_P]
+    const int npn = L.nnow - L.nlock;
+    CK(hl_trick(s, L.nnow, L.nlock, h->Z, s, h->CP, npn, h->hlw, h->st));
+    // X, AX <- S C_X, AS C_X ; P, AP <- S C_P, AS C_P (next buffers)
+    const int nx = 1 - L.cur;
+    void* Sn = h->S[nx];
+    void* ASn = h->AS[nx];
+    {
+      using SU = typename Pol<AU>::S;
+      SU* Cs = static_cast<SU*>(h->Cs);
+      const int c = L.nnow + npn;
+      CK(stage_coef<AU>(s, L.nnow, h->Z, s, Cs, c, 1.0, h->st));
+      CK(stage_coef<AU>(s, npn, h->CP, npn, Cs + L.nnow, c, 1.0, h->st));
+      Blk<T> Yn = cat(view<T>(Sn, ld, 0, L.nnow), view<T>(Sn, ld, k, npn));
+      Blk<T> AYn = cat(view<T>(ASn, ld, 0, L.nnow), view<T>(ASn, ld, k, npn));
+      CK(eig::update<AU>(h->n, Sb, Cs, c, Yn, 0.0, h->st));
+      CK(eig::update<AU>(h->n, ASb, Cs, c, AYn, 0.0, h->st));
+    }
+    L.cur = nx;
+    L.np = npn;
+    L.poff = 0;
+    // shrink: S_drop = [X(:, nes:nnow), P(:, nes-nlock:np)]
+    if (L.se.ifshrink(j, L.nnow)) {
+      const int hd = h->hdrop;
+      const int q = nes - L.nlock;
+      CK(cudaMemcpy2DAsync(h->Sd, sizeof(T) * 2 * hd, static_cast<T*>(Sn) + nes, sizeof(T) * ld,
+                           sizeof(T) * hd, h->n, cudaMemcpyDeviceToDevice, h->st));
+      CK(cudaMemcpy2DAsync(static_cast<T*>(h->Sd) + hd, sizeof(T) * 2 * hd, static_cast<T*>(Sn) + k + q,
+                           sizeof(T) * ld, sizeof(T) * hd, h->n, cudaMemcpyDeviceToDevice, h->st));
+      L.nnow = nes;
+      L.np = q;
+      L.have_drop = true;
+    }
+  }
+  return EIG_ENOTCONV;
+}
+
+// ---------------------------------------------------------------------------
+// Subspace iteration with a Chebyshev filter (Algorithm 1, filter in place
+// of the shift-and-invert solve).
+// ---------------------------------------------------------------------------
+template <Arith AU, Arith AG>
+int chebsi_init(eig_handle* h, LState& L) {
+  return lobpcg_init<AU, AG>(h, L);  // same set-up: orthogonalise X0, Rayleigh-Ritz
+}
+
+template <Arith AU, Arith AG>
+int chebsi_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* switched) {
+  using T = typename Pol<AU>::T;
+  Ops<AU, AG> o(h);
+  const int64_t ld = h->LDS;
+  const int k = h->kmax, nes = h->nes;
+  *done = false;
+  *switched = false;
+  int rc;
+  while (L.j < h->opt.max_iter) {
+    const int j = L.j + 1;
+    void* Sc = h->S[L.cur];
+    void* ASc = h->AS[L.cur];
+    T* X = static_cast<T*>(Sc);
+    T* AX = static_cast<T*>(ASc);
+    if ((rc = o.resid(X, AX, L.nnow, nullptr, false))) return rc;
+    ConvInfo ci = conv_test(h, L.nnow);
+    if (ci.breakdown) return EIG_EBREAKDOWN;
+    h->history.push_back(ci.r);
+    L.se.record(j, ci.r);
+    L.j = j;
+    h->iters = j;
+    if (ci.r <= h->opt.tol) {
+      *done = true;
+      return EIG_OK;
+    }
+    if (switch_r > 0.0 && ci.r <= switch_r) {
+      L.j = j - 1;
+      h->history.pop_back();
+      L.se.r.resize(j);
+      *switched = true;
+      return EIG_OK;
+    }
+    // filter: Y_m = p_m(A) X, three rotating buffers X, P slot, W slot
+    const double* lamh = h->hpin + 2 * h->kmax;
+    const double a = lamh[L.nnow - 1], a0 = lamh[0];
+    const double b = h->opt.cheb_upper > 0.0 ? h->opt.cheb_upper : h->opt.normA;
+    const double e = (b - a) / 2.0, c = (b + a) / 2.0;
+    double sigma = e / (a0 - c);
+    const double tau = 2.0 / sigma;
+    T* bufs[3] = {X, X + k, X + 2 * k};
+    // Y1 = (sigma / e) (AX - c X)
+    CK(axpby<AU>(h->n, L.nnow, AX, ld, sigma / e, X, ld, -sigma * c / e, bufs[1], ld, h->st));
+    int ip = 0, iy = 1;
+    for (int d = 2; d <= h->opt.cheb_degree; ++d) {
+      const double sn = 1.0 / (tau - sigma);
+      const int inew = 3 - ip - iy;
+      CK(eig::spmm<AU>(o.csr(), L.nnow, bufs[iy], ld, bufs[inew], ld, 2.0 * sn / e, -2.0 * sn * c / e, bufs[ip], ld,
+                       -sigma * sn, h->st));
+      ip = iy;
+      iy = inew;
+      sigma = sn;
+    }
+    // expansion: X <- [Y, X_drop]
+    Blk<T> Y = view<T>(bufs[iy], ld, 0, L.nnow);
+    if (L.se.ifexpand(j, L.nnow)) {
+      if (!L.have_drop) return EIG_EINVAL;
+      Y.add(static_cast<T*>(h->Sd), h->hdrop, h->hdrop);
+      L.nnow += h->hdrop;
+      L.have_drop = false;
+    }
+    // orthogonalise into the next buffer's X slot, A X, Rayleigh-Ritz
+    const int nx = 1 - L.cur;
+    void* Sn = h->S[nx];
+    void* ASn = h->AS[nx];
+    Blk<T> Q;
+    Blk<T> Xo = view<T>(Sn, ld, 0, L.nnow);
+    Blk<T> mid = view<T>(h->Wt, h->wtw, 0, L.nnow);
+    // Y may span two buffers; orth clobbers its source
+    if ((rc = o.orth(Q, Y, mid, Xo))) return rc;
+    Blk<T> AXo = view<T>(ASn, ld, 0, L.nnow);
+    if ((rc = o.spmm_blk(Xo, AXo))) return rc;
+    h->widths.push_back(L.nnow);
+    if ((rc = o.rr(Xo, AXo))) return rc;
+    // X <- X Z, AX <- AX Z back into the current buffers
+    if ((rc = o.upd(Xo, h->Z, L.nnow, L.nnow, 1.0, view<T>(Sc, ld, 0, L.nnow), 0.0))) return rc;
+    if ((rc = o.upd(AXo, h->Z, L.nnow, L.nnow, 1.0, view<T>(ASc, ld, 0, L.nnow), 0.0))) return rc;
+    if (L.se.ifshrink(j, L.nnow)) {
+      const int hd = h->hdrop;
+      CK(cudaMemcpy2DAsync(h->Sd, sizeof(T) * hd, static_cast<T*>(Sc) + nes, sizeof(T) * ld, sizeof(T) * hd,
+                           h->n, cudaMemcpyDeviceToDevice, h->st));
+      L.nnow = nes;
+      L.have_drop = true;
+    }
+  }
+  return EIG_ENOTCONV;
+}
+
+// Convert the iterate of the float32 phase to double-float storage.
+int promote(eig_handle* h, LState& L, bool lobpcg) {
+  const int64_t ld = h->LDS;
+  const int k = h->kmax;
+  const int nx = 1 - L.cur;
+  // X, AX (and P, AP) into the other buffers, then switch to them
+  CK(convert2d(h->n, L.nnow, h->S[L.cur], ld, EIG_F32, h->S[nx], ld, EIG_DF64, h->st));
+  CK(convert2d(h->n, L.nnow, h->AS[L.cur], ld, EIG_F32, h->AS[nx], ld, EIG_DF64, h->st));
+  if (lobpcg && L.np > 0) {
+    CK(convert2d(h->n, L.np, static_cast<float*>(h->S[L.cur]) + k + L.poff, ld, EIG_F32,
+                 static_cast<dd*>(h->S[nx]) + k, ld, EIG_DF64, h->st));
+    CK(convert2d(h->n, L.np, static_cast<float*>(h->AS[L.cur]) + k + L.poff, ld, EIG_F32,
+                 static_cast<dd*>(h->AS[nx]) + k, ld, EIG_DF64, h->st));
+    L.poff = 0;
+  }
+  if (L.have_drop) {
+    const int wd = lobpcg ? 2 * h->hdrop : h->hdrop;
+    CK(convert2d(h->n, wd, h->Sd, wd, EIG_F32, h->Wt, wd, EIG_DF64, h->st));
+    std::swap(h->Sd, h->Wt);
+  }
+  L.cur = nx;
+  return EIG_OK;
+}
+
+// final float64 residual pass on V = X(:, :nev)
+int final_pass(eig_handle* h, const void* Xsrc, int src_dt) {
+  const int nev = h->nev;
+  CK(convert2d(h->n, nev, Xsrc, h->LDS, src_dt, h->V, nev, EIG_F64, h->st));
+  // A V in float64 into the Wt buffer, residual norms with the Ritz values
+  double* AV = static_cast<double*>(h->Wt);
+  Csr<Arith::F64> c;
+  c.n = h->n;
+  c.rowptr = h->rowptr;
+  c.colind = h->colind;
+  c.val = h->val64;
+  CK(eig::spmm<Arith::F64>(c, nev, h->V, nev, AV, nev, 1.0, 0.0, nullptr, 0, 0.0, h->st));
+  CK(eig::residual<Arith::F64>(h->n, nev, h->V, nev, AV, nev, h->lamd, nullptr, nullptr, 0, h->xn, h->rn, h->rscr,
+                               h->st));
+  std::vector<double> xn(nev), rn(nev), lam(nev);
+  CK(cudaMemcpyAsync(xn.data(), h->xn, sizeof(double) * nev, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(rn.data(), h->rn, sizeof(double) * nev, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(lam.data(), h->lamd, sizeof(double) * nev, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  h->lam = lam;
+  h->resid.resize(nev);
+  for (int i = 0; i < nev; ++i) h->resid[i] = std::sqrt(rn[i]) / (h->opt.normA * std::sqrt(xn[i]));
+  return EIG_OK;
+}
+
+int solve_impl(eig_handle* h) {
+  LState L;
+  L.se.kind = h->strategy;
+  L.se.nes = h->nes;
+  L.se.nex = h->kmax;
+  L.se.je = h->opt.je;
+  L.se.js = h->opt.js;
+  L.se.jp = h->opt.jp;
+  L.se.j_warm = h->opt.j_warm;
+  L.se.mu = h->opt.mu;
+  L.se.r_warm = h->opt.r_warm;
+  h->history.clear();
+  h->widths.clear();
+  h->iters = 0;
+  CK(cudaMemsetAsync(h->flags, 0, sizeof(int) * NFLAGS, h->st));
+  const bool lob = h->opt.algo == EIG_LOBPCG;
+  bool done = false, sw = false;
+  int rc;
+  const void* Xfinal = nullptr;
+  int dt = EIG_DF64;
+  if (h->opt.form == EIG_FORM_F64) {
+    rc = lob ? lobpcg_init<Arith::F64, Arith::F64>(h, L) : chebsi_init<Arith::F64, Arith::F64>(h, L);
+    if (rc) return rc;
+    rc = lob ? lobpcg_run<Arith::F64, Arith::F64>(h, L, 0.0, &done, &sw)
+             : chebsi_run<Arith::F64, Arith::F64>(h, L, 0.0, &done, &sw);
+    dt = EIG_F64;
+  } else {
+    if (h->opt.form == EIG_FORM_MIXED) {
+      rc = lob ? lobpcg_init<Arith::F32, Arith::C32>(h, L) : chebsi_init<Arith::F32, Arith::C32>(h, L);
+      if (rc) return rc;
+      rc = lob ? lobpcg_run<Arith::F32, Arith::C32>(h, L, h->opt.mixed_switch, &done, &sw)
+               : chebsi_run<Arith::F32, Arith::C32>(h, L, h->opt.mixed_switch, &done, &sw);
+      if (rc != EIG_OK && rc != EIG_ENOTCONV) return rc;
+      // promote to double-float storage in every case: the final pass and
+      // any remaining iterations read double-float blocks
+      const int rc1 = rc;
+      int prc = promote(h, L, lob);
+      if (prc) return prc;
+      if (!done && rc1 == EIG_OK) {
+        rc = lob ? lobpcg_run<Arith::DF64, Arith::DF64>(h, L, 0.0, &done, &sw)
+                 : chebsi_run<Arith::DF64, Arith::DF64>(h, L, 0.0, &done, &sw);
+      }
+    } else {
+      rc = lob ? lobpcg_init<Arith::DF64, Arith::DF64>(h, L) : chebsi_init<Arith::DF64, Arith::DF64>(h, L);
+      if (rc) return rc;
+      rc = lob ? lobpcg_run<Arith::DF64, Arith::DF64>(h, L, 0.0, &done, &sw)
+               : chebsi_run<Arith::DF64, Arith::DF64>(h, L, 0.0, &done, &sw);
+    }
+    dt = EIG_DF64;
+  }
+  if (rc != EIG_OK && rc != EIG_ENOTCONV) return rc;
+  Xfinal = h->S[L.cur];
+  h->n_shrink = L.se.n_shrink;
+  h->n_expand = L.se.n_expand;
+  int frc = final_pass(h, Xfinal, dt);
+  if (frc) return frc;
+  return finish(h, rc);
+}
+
+int finish(eig_handle* h, int status) {
+  h->status = status;
+  return status;
+}
+
+void free_all(eig_handle* h) {
+  auto F = [](void* p) {
+    if (p) cudaFree(p);
+  };
+  if (h->own_idx) {
+    F(h->rowptr);
+    F(h->colind);
+  }
+  F(h->val64);
+  F(h->valdd);
+  F(h->val32);
+  F(h->t64);
+  F(h->tdd);
+  F(h->t32);
+  F(h->u64);
+  F(h->udd);
+  F(h->u32);
+  F(h->S[0]);
+  F(h->S[1]);
+  F(h->AS[0]);
+  F(h->AS[1]);
+  F(h->Wt);
+  F(h->Sd);
+  F(h->Gp);
+  F(h->Rinv);
+  F(h->cholw);
+  F(h->Z);
+  F(h->lamd);
+  F(h->CP);
+  F(h->gscr);
+  F(h->rscr);
+  F(h->xn);
+  F(h->rn);
+  F(h->Cs);
+  F(h->syevw);
+  F(h->hlw);
+  F(h->flags);
+  F(h->V);
+  if (h->hpin) cudaFreeHost(h->hpin);
+}
+
+__global__ void diag_inv_kernel(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* val,
+                                double* t) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double d = 0.0;
+  for (int q = rowptr[i]; q < rowptr[i + 1]; ++q)
+    if (colind[q] == i) d += val[q];
+  t[i] = d != 0.0 ? 1.0 / d : 1.0;
+}
+
+__global__ void fill_kernel(int64_t n, double v, double* x) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* eig_strerror(int s) {
+  switch (s) {
+    case EIG_OK: return "ok";
+    case EIG_EINVAL: return "invalid argument";
+    case EIG_ENOMEM: return "out of device memory";
+    case EIG_ENOTCONV: return "not converged within max_iter";
+    case EIG_EBREAKDOWN: return "orthogonalisation or eigensolver breakdown";
+    case EIG_ECUDA: return "CUDA error";
+    case EIG_ETIMEOUT: return "bounded device wait expired";
+    case EIG_EBUSY: return "no free serving slot";
+    case EIG_EREJECT: return "request can never fit";
+    default: return "unknown status";
+  }
+}
+
+int eig_options_default(eig_options* o) {
+  if (!o) return EIG_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->algo = EIG_LOBPCG;
+  o->form = EIG_FORM_DF64;
+  o->tol = 1e-10;
+  o->max_iter = 1000;
+  o->nes = 0;
+  o->je = 12;
+  o->js = 2;
+  o->jp = 10;
+  o->j_warm = 5;
+  o->mu = 1.1;
+  o->r_warm = 1e-4;
+  o->cheb_degree = 12;
+  o->cheb_upper = 0.0;
+  o->precond = 0;
+  o->deflate_ones = 0;
+  o->normA = 0.0;
+  o->mixed_switch = 1e-5;
+  return EIG_OK;
+}
+
+int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_options* opt, eig_handle** out) {
+  if (!A || !out || !opt) return EIG_EINVAL;
+  *out = nullptr;
+  const int nes = opt->nes > 0 ? opt->nes : nev + 5;
+  if (A->n <= 0 || A->nnz < 0 || !A->rowptr || !A->colind || !A->val) return EIG_EINVAL;
+  if (nev < 1 || nes < nev || nes >= k_max || k_max > A->n) return EIG_EINVAL;
+  if (strategy < EIG_NONE || strategy > EIG_SLOPEK) return EIG_EINVAL;
+  if (!opt->X0 || !(opt->normA > 0.0) || opt->max_iter < 1 || !(opt->tol > 0.0)) return EIG_EINVAL;
+  if (opt->algo != EIG_LOBPCG && opt->algo != EIG_CHEB_SI) return EIG_EINVAL;
+  if (opt->form < EIG_FORM_DF64 || opt->form > EIG_FORM_MIXED) return EIG_EINVAL;
+  if (opt->algo == EIG_CHEB_SI && opt->cheb_degree < 2) return EIG_EINVAL;
+  if (opt->je < 1 || opt->js < 0 || opt->jp < 1) return EIG_EINVAL;
+  if (k_max > 1400) return EIG_EINVAL;
+  eig_handle* h = new eig_handle();
+  h->n = A->n;
+  h->nnz = A->nnz;
+  h->nev = nev;
+  h->kmax = k_max;
+  h->nes = nes;
+  h->strategy = strategy;
+  h->opt = *opt;
+  h->opt.nes = nes;
+  h->st = static_cast<cudaStream_t>(opt->stream);
+  h->LDS = ((3 * k_max) + 3) / 4 * 4;
+  h->hdrop = k_max - nes;
+  h->wtw = std::max(k_max, 2 * h->hdrop);
+  const int64_t n = A->n, nnz = A->nnz;
+  auto fail = [&](int code) {
+    free_all(h);
+    delete h;
+    return code;
+  };
+#define AL(ptr, bytes)                                                            \
+  do {                                                                            \
+    if (cudaMalloc((void**)&(ptr), (bytes) > 0 ? (bytes) : 16) != cudaSuccess) {  \
+      cudaGetLastError();                                                         \
+      return fail(EIG_ENOMEM);                                                    \
+    }                                                                             \
+  } while (0)
+  // CSR
+  if (A->on_device) {
+    h->rowptr = const_cast<int32_t*>(A->rowptr);
+    h->colind = const_cast<int32_t*>(A->colind);
+    AL(h->val64, sizeof(double) * nnz);
+    if (cudaMemcpyAsync(h->val64, A->val, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess)
+      return fail(EIG_ECUDA);
+  } else {
+    h->own_idx = true;
+    AL(h->rowptr, sizeof(int32_t) * (n + 1));
+    AL(h->colind, sizeof(int32_t) * nnz);
+    AL(h->val64, sizeof(double) * nnz);
+    if (cudaMemcpyAsync(h->rowptr, A->rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, h->st) ||
+        cudaMemcpyAsync(h->colind, A->colind, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, h->st) ||
+        cudaMemcpyAsync(h->val64, A->val, sizeof(double) * nnz, cudaMemcpyHostToDevice, h->st))
+      return fail(EIG_ECUDA);
+  }
+  AL(h->valdd, sizeof(dd) * nnz);
+  if (convert2d(1, nnz, h->val64, nnz, EIG_F64, h->valdd, nnz, EIG_DF64, h->st)) return fail(EIG_ECUDA);
+  if (opt->form == EIG_FORM_MIXED) {
+    AL(h->val32, sizeof(float) * nnz);
+    if (convert2d(1, nnz, h->val64, nnz, EIG_F64, h->val32, nnz, EIG_F32, h->st)) return fail(EIG_ECUDA);
+  }
+  if (opt->precond) {
+    AL(h->t64, sizeof(double) * n);
+    AL(h->tdd, sizeof(dd) * n);
+    AL(h->t32, sizeof(float) * n);
+    diag_inv_kernel<<<(unsigned)cdiv(n, 256), 256, 0, h->st>>>(n, h->rowptr, h->colind, h->val64, h->t64);
+    convert2d(1, n, h->t64, n, EIG_F64, h->tdd, n, EIG_DF64, h->st);
+    convert2d(1, n, h->t64, n, EIG_F64, h->t32, n, EIG_F32, h->st);
+  }
+  if (opt->deflate_ones) {
+    AL(h->u64, sizeof(double) * n);
+    AL(h->udd, sizeof(dd) * n);
+    AL(h->u32, sizeof(float) * n);
+    fill_kernel<<<(unsigned)cdiv(n, 256), 256, 0, h->st>>>(n, 1.0 / std::sqrt(double(n)), h->u64);
+    convert2d(1, n, h->u64, n, EIG_F64, h->udd, n, EIG_DF64, h->st);
+    convert2d(1, n, h->u64, n, EIG_F64, h->u32, n, EIG_F32, h->st);
+  }
+  // blocks
+  const size_t blk = sizeof(double) * size_t(n) * h->LDS;
+  AL(h->S[0], blk);
+  AL(h->S[1], blk);
+  AL(h->AS[0], blk);
+  AL(h->AS[1], blk);
+  AL(h->Wt, sizeof(double) * size_t(n) * std::max(h->wtw, nev));
+  // S_drop and Wt are swapped when the mixed form promotes; same size
+  AL(h->Sd, sizeof(double) * size_t(n) * std::max(h->wtw, nev));
+  // small
+  const int smax = 3 * k_max + 1;
+  h->smax = smax;
+  AL(h->Gp, sizeof(double) * size_t(smax) * smax);
+  AL(h->Rinv, sizeof(double) * size_t(h->wtw) * h->wtw);
+  AL(h->cholw, sizeof(double) * (size_t(h->wtw) * h->wtw + h->wtw));
+  AL(h->Z, sizeof(double) * size_t(smax) * smax);
+  AL(h->lamd, sizeof(double) * smax);
+  AL(h->CP, sizeof(double) * size_t(smax) * k_max);
+  const size_t gs = size_t(2) * num_sms() * 4 * 64 * 64 + size_t(smax) * smax + 4096;
+  AL(h->gscr, sizeof(double) * gs);
+  AL(h->rscr, sizeof(double) * residual_scratch_elems(n, k_max));
+  AL(h->xn, sizeof(double) * smax);
+  AL(h->rn, sizeof(double) * smax);
+  AL(h->Cs, sizeof(double) * size_t(smax) * (2 * k_max + 1));
+  AL(h->syevw, syev_work_bytes(smax));
+  AL(h->hlw, hl_work_bytes(smax, k_max, 0) + sizeof(double) * size_t(smax) * smax);
+  AL(h->flags, sizeof(int) * NFLAGS);
+  AL(h->V, sizeof(double) * size_t(n) * nev);
+  if (cudaMallocHost((void**)&h->hpin, sizeof(double) * (3 * size_t(k_max) + 16)) != cudaSuccess)
+    return fail(EIG_ENOMEM);
+#undef AL
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(EIG_ECUDA);
+  *out = h;
+  return EIG_OK;
+}
+
+int eig_solve(eig_handle* h) {
+  if (!h) return EIG_EINVAL;
+  auto t0 = std::chrono::steady_clock::now();
+  int rc = solve_impl(h);
+  cudaStreamSynchronize(h->st);
+  auto t1 = std::chrono::steady_clock::now();
+  h->time_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  h->status = rc;
+  return rc;
+}
+
+int eig_query(const eig_handle* h, eig_result* out) {
+  if (!h || !out) return EIG_EINVAL;
+  out->status = h->status;
+  out->iters = h->iters;
+  out->n_shrink = h->n_shrink;
+  out->n_expand = h->n_expand;
+  out->nev = h->nev;
+  out->lambda = h->lam.empty() ? nullptr : h->lam.data();
+  out->resid = h->resid.empty() ? nullptr : h->resid.data();
+  out->V = h->V;
+  out->history = h->history.empty() ? nullptr : h->history.data();
+  out->widths = h->widths.empty() ? nullptr : h->widths.data();
+  out->time_ms = h->time_ms;
+  out->normA = h->opt.normA;
+  return EIG_OK;
+}
+
+void eig_destroy(eig_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,87 @@
+"""CPU-side checks of the C ABI: the library builds, loads, and exports every
+entry point that include/*.h declares; the product never imports the oracle;
+a missing library fails loudly.  No CUDA call is made."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def libpath():
+    from paper_2409_05572_gb300 import build_lib
+    if not os.path.exists(build_lib.LIB):
+        build_lib.build()
+    return build_lib.LIB
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(eig_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("eig_create", "eig_solve", "eig_query", "eig_destroy", "eig_strerror",
+                     "eig_spmm", "eig_gram", "eig_block_update", "eig_residual", "eig_cholqr2",
+                     "eig_syev", "eig_hl_trick", "eig_convert", "eig_options_default"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in sorted(declared_functions()):
+        assert hasattr(lib, name), name
+
+
+def test_strerror_without_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.eig_strerror.restype = ctypes.c_char_p
+    assert lib.eig_strerror(0) == b"ok"
+    assert b"invalid" in lib.eig_strerror(1)
+
+
+def test_binding_exports_match_library(libpath):
+    from paper_2409_05572_gb300 import _lib
+    lib = _lib.load()
+    for name in _lib.EXPORTS:
+        assert hasattr(lib, name)
+    assert set(_lib.EXPORTS) <= declared_functions()
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2409_05572_gb300 import _lib
+    saved = _lib._lib
+    _lib._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            _lib.load(str(tmp_path / "nope.so"))
+    finally:
+        _lib._lib = saved
+
+
+def test_product_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2409_05572_gb300")
+    for path in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True) + \
+            glob.glob(os.path.join(pkg, "csrc", "*")):
+        src = open(path, errors="ignore").read()
+        assert not re.search(r"^\s*(from|import)\s+oracle\b", src, flags=re.M), path
+        assert "oracle/" not in src, path
+
+
+def test_options_default_values(libpath):
+    from paper_2409_05572_gb300 import _lib
+    lib = _lib.load()
+    o = _lib.eig_options()
+    assert lib.eig_options_default(ctypes.byref(o)) == 0
+    assert (o.tol, o.max_iter, o.je, o.js, o.jp, o.j_warm) == (1e-10, 1000, 12, 2, 10, 5)
+    assert (o.mu, o.r_warm, o.cheb_degree) == (1.1, 1e-4, 12)

@@ -1,0 +1,417 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle, step by
+step and for whole solves.  Sizes span several 64-wide tiles and a ragged
+tail; tolerances follow from the arithmetic of each form:
+
+* F64 (native float64): round-off of length-n dot products, 1e-13 relative
+  to sum |u_i v_i|.
+* DF64 (double-float, about 2^-48 per operation): 1e-12 relative to
+  sum |u_i v_i|.
+* C32 (float32 inputs, compensated Dot2 sums): 1e-9 relative to
+  sum |u_i v_i| of the float32-rounded inputs.
+* F32: 2e-5 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import blocks as B
+from oracle.chebsi import chebsi as o_chebsi
+from oracle.lobpcg import lobpcg as o_lobpcg
+from paper_2409_05572_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2409_05572_gb300 import _lib as L  # noqa: E402
+
+ARITHS = {"f64": L.ARITH_F64, "df64": L.ARITH_DF64, "f32": L.ARITH_F32, "c32": L.ARITH_C32}
+RTOL = {"f64": 1e-13, "df64": 1e-12, "c32": 1e-9, "f32": 2e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    L.load()
+    yield
+    torch.cuda.synchronize()
+
+
+def dev(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+def to_fmt(x_np, arith):
+    """Host float64 array -> device block in the element format of arith."""
+    t = dev(x_np)
+    if arith in ("f64",):
+        return t, L.EIG_F64
+    if arith == "df64":
+        return L.to_df64(t), L.EIG_DF64
+    return t.float(), L.EIG_F32
+
+
+def from_fmt(t, arith):
+    if arith == "df64":
+        return L.from_df64(t).cpu().numpy()
+    return t.double().cpu().numpy()
+
+
+def rounded(x_np, arith):
+    return x_np.astype(np.float32).astype(np.float64) if arith in ("f32", "c32") else x_np
+
+
+# ---------------------------------------------------------------------------
+# a7: SpMM
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("arith", ["f64", "df64", "f32"])
+@pytest.mark.parametrize("w", [1, 3, 8, 20, 64, 130])
+def test_spmm_parity(arith, w):
+    A = W.anderson_3d(9, seed=2)   # n = 729, 7 nnz/row, random values
+    n = A.n
+    rng = np.random.default_rng(w)
+    V = rng.standard_normal((n, w))
+    U = rng.standard_normal((n, w))
+    rp, ci = dev(A.indptr, torch.int32), dev(A.indices, torch.int32)
+    val, _ = to_fmt(A.data, arith)
+    Vd, dt = to_fmt(V, arith)
+    Ud, _ = to_fmt(U, arith)
+    Yd = torch.empty_like(Vd)
+    for (alpha, beta, gamma) in ((1.0, 0.0, 0.0), (0.37, -1.25, 0.5)):
+        L.eig_spmm(n, rp, ci, val, dt, w, Vd, w, Yd, w, alpha, beta, Ud if gamma else None, w, gamma)
+        torch.cuda.synchronize()
+        Ar, Vr, Ur = rounded(A.data, arith), rounded(V, arith), rounded(U, arith)
+        Ao = W.CSR(n, A.indptr, A.indices, Ar)
+        ref = alpha * B.spmm(Ao, Vr) + beta * Vr + gamma * Ur
+        scale = np.abs(alpha) * B.spmm(W.CSR(n, A.indptr, A.indices, np.abs(Ar)), np.abs(Vr)) + \
+            abs(beta) * np.abs(Vr) + abs(gamma) * np.abs(Ur)
+        got = from_fmt(Yd, arith)
+        assert np.all(np.abs(got - ref) <= 4 * RTOL[arith] * scale + 1e-300), (arith, w)
+
+
+def test_spmm_power_law_rows():
+    A = W.graph_laplacian(4000, seed=3)   # rows from 3 to hundreds of nonzeros
+    n, w = A.n, 37
+    V = np.random.default_rng(1).standard_normal((n, w))
+    Yd = torch.empty(n, w, dtype=torch.float64, device="cuda")
+    L.eig_spmm(n, dev(A.indptr, torch.int32), dev(A.indices, torch.int32), dev(A.data), L.EIG_F64, w,
+               dev(V), w, Yd, w)
+    ref = B.spmm(A, V)
+    scale = B.spmm(W.CSR(n, A.indptr, A.indices, np.abs(A.data)), np.abs(V))
+    assert np.all(np.abs(Yd.cpu().numpy() - ref) <= 1e-13 * scale)
+
+
+def test_spmm_empty_rows_and_zero_width():
+    n = 50
+    indptr = np.zeros(n + 1, dtype=np.int32)
+    indptr[26:] = 1
+    A = W.CSR(n, indptr, np.array([3], dtype=np.int32), np.array([2.5]))
+    V = np.arange(n * 4, dtype=np.float64).reshape(n, 4)
+    Yd = torch.full((n, 4), 7.0, dtype=torch.float64, device="cuda")
+    L.eig_spmm(n, dev(A.indptr, torch.int32), dev(A.indices, torch.int32), dev(A.data), L.EIG_F64, 4,
+               dev(V), 4, Yd, 4)
+    ref = B.spmm(A, V)
+    assert np.array_equal(Yd.cpu().numpy(), ref)
+    L.eig_spmm(n, dev(A.indptr, torch.int32), dev(A.indices, torch.int32), dev(A.data), L.EIG_F64, 0,
+               dev(V), 4, Yd, 4)
+
+
+# ---------------------------------------------------------------------------
+# a4 / a5 / a8: Gram
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("arith", ["f64", "df64", "c32", "f32"])
+@pytest.mark.parametrize("a,b,sym", [(7, 5, False), (64, 64, True), (130, 70, False), (150, 150, True)])
+def test_gram_parity(arith, a, b, sym):
+    n = 5000 + 17
+    rng = np.random.default_rng(a * 1000 + b)
+    U = rng.standard_normal((n, a))
+    V = U.copy() if sym else rng.standard_normal((n, b))
+    Ud, _ = to_fmt(U, arith)
+    Vd, _ = to_fmt(V, arith)
+    G = torch.empty(a, b + 3, dtype=torch.float64, device="cuda")
+    L.eig_gram(n, a, b, Ud, a, Vd, b, ARITHS[arith], sym, G, b + 3)
+    got = G[:, :b].cpu().numpy()
+    Ur, Vr = rounded(U, arith), rounded(V, arith)
+    ref = B.gram(Ur, Vr)
+    scale = np.abs(Ur).T @ np.abs(Vr)
+    assert np.all(np.abs(got - ref) <= RTOL[arith] * scale), np.max(np.abs(got - ref) / scale)
+    if sym:
+        assert np.array_equal(got, got.T)
+
+
+def test_gram_deterministic_and_empty():
+    n, a = 20000, 96
+    U = np.random.default_rng(3).standard_normal((n, a))
+    Ud = L.to_df64(dev(U))
+    G1 = torch.empty(a, a, dtype=torch.float64, device="cuda")
+    G2 = torch.empty_like(G1)
+    L.eig_gram(n, a, a, Ud, a, Ud, a, L.ARITH_DF64, True, G1, a)
+    L.eig_gram(n, a, a, Ud, a, Ud, a, L.ARITH_DF64, True, G2, a)
+    assert torch.equal(G1, G2)
+    G0 = torch.full((3, 3), 5.0, dtype=torch.float64, device="cuda")
+    L.eig_gram(0, 3, 3, Ud, a, Ud, a, L.ARITH_DF64, False, G0, 3)
+    assert torch.count_nonzero(G0) == 0
+
+
+# ---------------------------------------------------------------------------
+# a4 / a11: block update
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("arith", ["f64", "df64", "f32"])
+@pytest.mark.parametrize("s,c,beta", [(5, 3, 0.0), (70, 130, 0.0), (150, 64, -1.0)])
+def test_update_parity(arith, s, c, beta):
+    n = 3000 + 5
+    rng = np.random.default_rng(s + c)
+    U = rng.standard_normal((n, s))
+    Cm = rng.standard_normal((s, c))
+    Y0 = rng.standard_normal((n, c))
+    Ud, _ = to_fmt(U, arith)
+    Yd, _ = to_fmt(Y0, arith)
+    L.eig_block_update(n, s, c, Ud, s, dev(Cm), c, Yd, c, beta, ARITHS[arith])
+    got = from_fmt(Yd, arith)
+    Ur, Yr = rounded(U, arith), rounded(Y0, arith)
+    Cr = rounded(Cm, arith)
+    ref = Ur @ Cr + beta * Yr
+    scale = np.abs(Ur) @ np.abs(Cr) + abs(beta) * np.abs(Yr)
+    tol = {"f64": 1e-13, "df64": 1e-12, "f32": 2e-6}[arith]
+    assert np.all(np.abs(got - ref) <= tol * scale + 1e-300)
+
+
+# ---------------------------------------------------------------------------
+# a1 / a2: residual, norms, Jacobi preconditioning
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("arith", ["f64", "df64", "f32"])
+def test_residual_parity(arith):
+    n, w = 4000 + 3, 45
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((n, w))
+    AX = rng.standard_normal((n, w))
+    lam = rng.uniform(-3, 3, w)
+    t = rng.uniform(0.1, 2.0, n)
+    Xd, dt = to_fmt(X, arith)
+    AXd, _ = to_fmt(AX, arith)
+    td, _ = to_fmt(t, arith)
+    Rd = torch.empty_like(Xd)
+    xn = torch.empty(w, dtype=torch.float64, device="cuda")
+    rn = torch.empty_like(xn)
+    L.eig_residual(n, w, Xd, w, AXd, w, dev(lam), td, Rd, w, xn, rn, dt)
+    Xr, AXr, tr = rounded(X, arith), rounded(AX, arith), rounded(t, arith)
+    Rref, _, _ = B.residual_test(Xr, AXr, lam, 1.0, 1)
+    tol = {"f64": 1e-13, "df64": 1e-12, "f32": 1e-5}[arith]
+    scale = np.abs(AXr) + np.abs(Xr * lam)
+    assert np.all(np.abs(from_fmt(Rd, arith) - tr[:, None] * Rref) <= tol * tr[:, None] * scale)
+    assert np.allclose(xn.cpu().numpy(), np.sum(Xr * Xr, axis=0), rtol=10 * tol)
+    assert np.allclose(rn.cpu().numpy(), np.sum(Rref * Rref, axis=0), rtol=100 * tol)
+
+
+# ---------------------------------------------------------------------------
+# a5: CholeskyQR2 (unique Q with positive R diagonal -> elementwise parity)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("arith", ["f64", "df64"])
+@pytest.mark.parametrize("w", [1, 9, 64, 100])
+def test_cholqr2_parity(arith, w):
+    n = 6000 + 11
+    Wm = np.random.default_rng(w).standard_normal((n, w))
+    Wd, _ = to_fmt(Wm, arith)
+    st = L.eig_cholqr2(n, w, Wd, w, ARITHS[arith])
+    assert st == 0
+    Q = from_fmt(Wd, arith)
+    ref = B.cholqr2(Wm)
+    assert np.abs(Q - ref).max() < 1e-11
+    assert np.linalg.norm(Q.T @ Q - np.eye(w)) < 1e-12
+
+
+def test_cholqr2_shifted_path():
+    n, w = 3000, 12
+    rng = np.random.default_rng(3)
+    U, _ = np.linalg.qr(rng.standard_normal((n, w)))
+    V, _ = np.linalg.qr(rng.standard_normal((w, w)))
+    Wm = U @ np.diag(np.logspace(0, -11, w)) @ V.T
+    Wd = dev(Wm)
+    st = L.eig_cholqr2(n, w, Wd, w, L.ARITH_F64)
+    assert st == 1
+    Q = Wd.cpu().numpy()
+    assert np.linalg.norm(Q.T @ Q - np.eye(w)) < 1e-12
+    # same span as the input (the oracle's shifted CholeskyQR3 result)
+    ref = B.cholqr2(Wm)
+    assert np.linalg.norm(Q @ (Q.T @ ref) - ref) < 1e-8
+
+
+# ---------------------------------------------------------------------------
+# a9: small dense eigensolver
+# ---------------------------------------------------------------------------
+def _sym(s, seed, kind="random"):
+    rng = np.random.default_rng(seed)
+    if kind == "random":
+        M = rng.standard_normal((s, s))
+        return M + M.T
+    if kind == "clustered":
+        Q, _ = np.linalg.qr(rng.standard_normal((s, s)))
+        d = np.repeat(np.arange(1, s // 3 + 2, dtype=float), 3)[:s]
+        return Q @ np.diag(d) @ Q.T
+    if kind == "diag":
+        return np.diag(rng.uniform(-1, 1, s))
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("s,kind", [(1, "random"), (2, "random"), (3, "random"), (17, "random"),
+                                    (60, "clustered"), (64, "diag"), (200, "random"), (384, "random")])
+def test_syev_parity(s, kind):
+    A = _sym(s, s, kind)
+    lam = torch.empty(s, dtype=torch.float64, device="cuda")
+    Z = torch.empty(s, s, dtype=torch.float64, device="cuda")
+    L.eig_syev(s, dev(A), s, lam, Z, s)
+    lam_h, Z_h = lam.cpu().numpy(), Z.cpu().numpy()
+    theta, _ = B.rayleigh_ritz(np.eye(s), A)
+    nA = max(np.abs(theta).max(), 1e-300)
+    assert np.all(np.diff(lam_h) >= 0)
+    assert np.abs(lam_h - theta).max() <= 1e-13 * nA * max(1, math.sqrt(s))
+    assert np.linalg.norm(Z_h.T @ Z_h - np.eye(s)) <= 1e-13 * s
+    assert np.linalg.norm(A @ Z_h - Z_h * lam_h) <= 1e-13 * nA * s
+
+
+# ---------------------------------------------------------------------------
+# a10: improved Hetmaniuk-Lehoucq basis selection
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("s,nnow,nlock", [(30, 10, 0), (30, 10, 3), (96, 40, 0), (200, 90, 7)])
+def test_hl_trick_parity(s, nnow, nlock):
+    _, Z = np.linalg.eigh(_sym(s, s + nnow))
+    q = nnow - nlock
+    CP = torch.empty(s, q, dtype=torch.float64, device="cuda")
+    L.eig_hl_trick(s, nnow, nlock, dev(Z), s, CP, q)
+    got = CP.cpu().numpy()
+    _, ref = B.hl_trick(Z, nnow, nlock)
+    for j in range(q):
+        sg = np.sign(got[:, j] @ ref[:, j])
+        assert np.abs(sg * got[:, j] - ref[:, j]).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# invalid arguments are rejected before any launch
+# ---------------------------------------------------------------------------
+def test_invalid_arguments():
+    x = torch.zeros(10, 4, dtype=torch.float64, device="cuda")
+    with pytest.raises(L.EigError) as e:
+        L.eig_gram(10, 4, 4, x, 3, x, 4, L.ARITH_F64, False, x, 4)   # ldu < a
+    assert e.value.code == L.EIG_EINVAL
+    with pytest.raises(L.EigError):
+        L.eig_hl_trick(10, 8, 0, x, 10, x, 8)                         # s - nnow < nnow - nlock
+    with pytest.raises(L.EigError):
+        L.eig_syev(-1, x, 1, x, x, 1)
+    A = W.laplacian_2d(6)
+    with pytest.raises(L.EigError) as e:
+        L.Solver(A, nev=4, k_max=8, X0=np.zeros((36, 8)), normA=8.0, nes=8)   # nes >= k_max
+    assert e.value.code == L.EIG_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# whole solves against the oracle and the closed forms
+# ---------------------------------------------------------------------------
+def dirichlet_spectrum(dims):
+    axes = [4 * np.sin(np.arange(1, d + 1) * np.pi / (2 * (d + 1))) ** 2 for d in dims]
+    tot = axes[0]
+    for a in axes[1:]:
+        tot = np.add.outer(tot, a).ravel()
+    return np.sort(tot)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    A = W.laplacian_2d(32)
+    return A, W.dirichlet_norm((32, 32)), W.gaussian_block(A.n, 20, 0), dirichlet_spectrum((32, 32))
+
+
+@pytest.mark.parametrize("form", ["df64", "f64"])
+@pytest.mark.parametrize("strategy", ["none", "fix", "slope", "slopek"])
+def test_c1_lobpcg_parity(c1, form, strategy):
+    A, normA, X0, ex = c1
+    s = L.Solver(A, nev=10, k_max=20, strategy=strategy, X0=X0, normA=normA, tol=1e-10, form=form)
+    out = s.solve()
+    ref = o_lobpcg(A, X0, 10, 15, strategy, tol=1e-10, normA=normA)
+    assert out["status"] == 0
+    assert np.max(np.abs(out["lam"] - ref.lam) / ref.lam) <= 1e-10
+    assert np.max(np.abs(out["lam"] - ex[:10]) / ex[:10]) <= 1e-10
+    assert out["resid"].max() <= 2e-10
+    # step-by-step: the residual histories agree while rounding is negligible
+    m = min(12, len(ref.history), len(out["history"]))
+    assert np.allclose(out["history"][:m], ref.history[:m], rtol=1e-6)
+    if strategy != "none":
+        assert out["n_shrink"] >= 1 and out["n_expand"] >= 1
+    # subspace of complete clusters (10 wanted values close a pair)
+    V = s.V().cpu().numpy()
+    Qv, _ = np.linalg.qr(V)
+    Qo, _ = np.linalg.qr(ref.X)
+    assert np.linalg.norm(Qv @ Qv.T - Qo @ Qo.T, 2) < 1e-8
+    s.close()
+
+
+def test_c1_lobpcg_mixed(c1):
+    A, normA, X0, ex = c1
+    s = L.Solver(A, nev=10, k_max=20, strategy="fix", X0=X0, normA=normA, tol=1e-10, form="mixed")
+    out = s.solve()
+    assert out["status"] == 0
+    assert np.max(np.abs(out["lam"] - ex[:10]) / ex[:10]) <= 1e-8
+    assert out["resid"].max() <= 1e-8
+    s.close()
+
+
+def test_lobpcg_3d_several_tiles_closed_form():
+    A = W.laplacian_3d(20, 22, 24)   # n = 10560
+    ex = dirichlet_spectrum((20, 22, 24))
+    normA = W.dirichlet_norm((20, 22, 24))
+    X0 = W.gaussian_block(A.n, 40, 1)
+    s = L.Solver(A, nev=24, k_max=40, strategy="fix", X0=X0, normA=normA, tol=1e-10)
+    out = s.solve()
+    assert out["status"] == 0
+    assert np.max(np.abs(out["lam"] - ex[:24]) / ex[:24]) <= 1e-10
+    assert out["resid"].max() <= 2e-10
+    s.close()
+
+
+def test_lobpcg_graph_laplacian_jacobi_deflation():
+    A = W.graph_laplacian(3000, seed=3)
+    M = A.to_scipy()
+    ev = np.linalg.eigvalsh(M.toarray())
+    X0 = W.gaussian_block(A.n, 24, 3)
+    normA = float(ev[-1])
+    s = L.Solver(A, nev=12, k_max=24, strategy="fix", X0=X0, normA=normA, tol=1e-9, precond=1,
+                 deflate_ones=1, max_iter=800)
+    out = s.solve()
+    ref = o_lobpcg(A, X0, 12, 17, "fix", tol=1e-9, normA=normA, precond=1.0 / M.diagonal(),
+                   u0=np.ones(A.n) / math.sqrt(A.n), max_iter=800)
+    assert out["status"] == 0 and ref.converged
+    assert np.max(np.abs(out["lam"] - ev[1:13]) / ev[1:13]) <= 1e-9
+    assert np.max(np.abs(out["lam"] - ref.lam) / ref.lam) <= 1e-9
+    V = s.V().cpu().numpy()
+    assert np.abs(V.sum(axis=0)).max() / math.sqrt(A.n) < 1e-9
+    s.close()
+
+
+@pytest.mark.parametrize("form", ["df64", "mixed"])
+@pytest.mark.parametrize("strategy", ["none", "fix", "slopek"])
+def test_chebsi_anderson_parity(form, strategy):
+    A = W.anderson_3d(12, seed=2)    # n = 1728, indefinite
+    ev = np.linalg.eigvalsh(A.to_scipy().toarray())
+    X0 = W.gaussian_block(A.n, 32, 2)
+    ub = W.gershgorin_bound(A)
+    normA = float(np.abs(ev).max())
+    kw = dict(j_warm=2, r_warm=1e-2, je=4, js=1, jp=2)
+    s = L.Solver(A, nev=16, k_max=32, strategy=strategy, X0=X0, normA=normA, tol=1e-11, algo="chebsi",
+                 form=form, cheb_degree=10, cheb_upper=ub, max_iter=400, **kw)
+    out = s.solve()
+    ref = o_chebsi(A, X0, 16, 21, strategy, tol=1e-11, normA=normA, degree=10, upper=ub, max_iter=400, **kw)
+    assert out["status"] == 0 and ref.converged
+    tol = 1e-10 if form == "df64" else 1e-8
+    assert np.max(np.abs(out["lam"] - ev[:16]) / np.abs(ev[:16])) <= tol
+    assert np.max(np.abs(out["lam"] - ref.lam) / np.abs(ref.lam)) <= tol
+    assert out["resid"].max() <= 1e-8
+    s.close()
+
+
+def test_solver_reuse_gives_identical_results(c1):
+    A, normA, X0, _ = c1
+    s = L.Solver(A, nev=10, k_max=20, strategy="fix", X0=X0, normA=normA, tol=1e-10)
+    a = s.solve()
+    b = s.solve()
+    assert np.array_equal(a["lam"], b["lam"]) and a["iters"] == b["iters"]
+    s.close()
