@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Benchmark: converged eigenpairs/s at 1e-8 residual of the shrink-and-expand
+LOBPCG on one GB300, against the fixed-block solver.
+
+Workload (default): 3D Dirichlet 7-point Laplacian on a 128^3 grid
+(n = 2,097,152, nnz = 14,581,760, int32 CSR), the 64 smallest eigenpairs,
+LOBPCG with k_max = 128 (nes = 69), Gaussian X0 (Philox seed 1), residual
+tolerance 1e-8, strategy `fix`, double-float (FP64-storage) form.
+
+A step is one whole solve: X0 -> 64 eigenpairs whose relative residual
+||A v - lambda v|| / ||A|| is at most 1e-8 (checked in float64 after every
+solve).  value = nev / (seconds per solve) summed over ranks.  Inputs are
+resident in HBM when the timed region starts; the blocks (4.3 GB each) are
+far larger than L2, so no separate L2 flush is needed.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+build) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2409_05572_gb300 import workloads as W  # noqa: E402
+
+METRIC = "converged eigenpairs/s at 1e-8 residual vs fixed-block FP64; p50/p99 latency"
+UNIT = "eigenpairs/s"
+
+# kernels launched per library call of each kernel class (for gpu_launches)
+LAUNCHES_PER_CALL = {"spmm": 1, "gram": 2, "update": 1, "residual": 2, "chol": 1, "syev": 6, "hl": 2,
+                     "other": 1}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# FP32 issue rate measured on this machine's GB300 (152 SMs, FFMA, 72.6 TFLOP/s
+# = 36.3 T instructions/s); a double-float multiply-add is 11 FP32
+# instructions plus a renormalisation every 32, i.e. 11.1 on average.
+FP32_INSTR_PER_S = 36.3e12
+DF64_INSTR_PER_MAC = 11.1
+DF64_PEAK_TFLOPS = 2.0 * FP32_INSTR_PER_S / DF64_INSTR_PER_MAC / 1e12
+FP64_PEAK_TFLOPS = 1.01   # measured native FP64 FMA rate
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(name):
+    if name == "c2":
+        L = 128
+        A = W.laplacian_3d(L)
+        return dict(A=A, nev=64, k_max=128, normA=W.dirichlet_norm((L, L, L)), seed=1, tol=1e-8,
+                    desc="3D Dirichlet 7-point Laplacian 128^3 (n=2097152, nnz=14581760), nev=64, "
+                         "LOBPCG k_max=128 nes=69, Gaussian X0 seed 1, residual 1e-8",
+                    exact=dirichlet_lowest((L, L, L), 64))
+    if name == "c2s":   # reduced stand-in for quick checks
+        L = 48
+        A = W.laplacian_3d(L)
+        return dict(A=A, nev=64, k_max=128, normA=W.dirichlet_norm((L, L, L)), seed=1, tol=1e-8,
+                    desc="3D Dirichlet 7-point Laplacian 48^3, nev=64, LOBPCG k_max=128",
+                    exact=dirichlet_lowest((L, L, L), 64))
+    raise ValueError(name)
+
+
+def dirichlet_lowest(dims, k):
+    axes = [4 * np.sin(np.arange(1, min(d, k) + 1) * np.pi / (2 * (d + 1))) ** 2 for d in dims]
+    tot = axes[0]
+    for a in axes[1:]:
+        tot = np.add.outer(tot, a).ravel()
+    return np.sort(tot)[:k]
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, timed on the host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import blocks as B
+    from oracle.lobpcg import lobpcg as o_lobpcg  # noqa: F401
+    wl = make_workload(args.workload)
+    A, nev, k = wl["A"], wl["nev"], wl["k_max"]
+    X0 = W.gaussian_block(A.n, k, wl["seed"])
+    cores = len(os.sched_getaffinity(0))
+    per_iter = []
+    t_all = time.perf_counter()
+    for step in range(args.warmup + args.steps):
+        t = oracle_iteration_time(A, X0, nev, wl["normA"])
+        if step >= args.warmup:
+            per_iter.append(t)
+    iters_est = args.ref_iters
+    sec = statistics.mean(per_iter) * iters_est
+    value = nev / sec
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl["desc"], "strategy": args.strategy},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"one full-width LOBPCG iteration of the FP64 oracle per step "
+                                       f"(mean {statistics.mean(per_iter):.2f} s), scaled by "
+                                       f"{iters_est} iterations per solve"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def oracle_iteration_time(A, X0, nev, normA):
+    """Wall time of one full-width LOBPCG iteration of the FP64 oracle (the
+    residual, projection, CholeskyQR2, SpMM, Rayleigh-Ritz, HL and update
+    steps), after an untimed set-up Rayleigh-Ritz."""
+    from oracle import blocks as B
+    X = B.cholqr2(X0)
+    AX = B.spmm(A, X)
+    lam, Z = B.rayleigh_ritz(X, AX)
+    X, AX = X @ Z, AX @ Z
+    t0 = time.perf_counter()
+    R, rho, r = B.residual_test(X, AX, lam, normA, nev)
+    Wb = B.orth_against(R, X)
+    AW = B.spmm(A, Wb)
+    S = np.hstack([X, Wb])
+    AS = np.hstack([AX, AW])
+    theta, Zs = B.rayleigh_ritz(S, AS)
+    CX, CP = B.hl_trick(Zs, X.shape[1], 0)
+    X2, AX2, P2, AP2 = S @ CX, AS @ CX, S @ CP, AS @ CP
+    # a steady-state iteration also carries P: add the cost of its share
+    S3 = np.hstack([X2, P2, Wb])
+    AS3 = np.hstack([AX2, AP2, AW])
+    B.gram(S3, AS3)
+    _ = S3 @ np.vstack([CX, np.zeros((S3.shape[1] - CX.shape[0], CX.shape[1]))])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(A, X0, nev, normA, iters, budget_s=30.0):
+    cores = len(os.sched_getaffinity(0))
+    t = oracle_iteration_time(A, X0, nev, normA)
+    sec = t * iters
+    return {"value": nev / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one full-width LOBPCG iteration of the FP64 oracle on this workload "
+                      f"({t:.2f} s, BLAS threads = affinity cores), scaled by the GPU solve's "
+                      f"{iters} iterations"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--strategy", default="fix")
+    ap.add_argument("--form", default="df64")
+    ap.add_argument("--no-compare", action="store_true", help="skip the fixed-block comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=150,
+                    help="iterations per solve used to scale the reference arm's per-iteration time")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2409_05572_gb300 import _lib as L
+    L.load()
+
+    wl = make_workload(args.workload)
+    A, nev, k, normA, tol = wl["A"], wl["nev"], wl["k_max"], wl["normA"], wl["tol"]
+    X0 = W.gaussian_block(A.n, k, wl["seed"])
+    dev = torch.device("cuda", local)
+    rp = torch.as_tensor(A.indptr, device=dev)
+    ci = torch.as_tensor(A.indices, device=dev)
+    va = torch.as_tensor(A.data, device=dev)
+    X0d = torch.as_tensor(X0, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    # stopping test of Eq. conv at tol/2 so that ||Av - lv|| / ||A|| <= tol holds
+    solver = L.Solver((rp, ci, va), nev=nev, k_max=k, strategy=args.strategy, X0=X0d, normA=normA,
+                      tol=0.5 * tol, form=args.form, stream=stream, profile=1)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        out = solver.solve()
+    barrier()
+    clocks = Clocks(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kst = None
+    results = []
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            out = solver.solve()
+            results.append(out)
+            ks = out["kstats"]
+            if kst is None:
+                kst = {c: dict(v) for c, v in ks.items()}
+            else:
+                for c, v in ks.items():
+                    for f in v:
+                        kst[c][f] += v[f]
+        ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    ms_step = ms_total / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = ws * nev / (ms_step / 1e3)
+    last = results[-1]
+    ok = last["status"] == 0 and float(np.max(last["resid"])) <= tol
+    eig_err = float(np.max(np.abs(last["lam"] - wl["exact"]) / np.abs(wl["exact"])))
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.form, "data": "synthetic",
+            "config": {"workload": wl["desc"], "nev": nev, "k_max": k, "strategy": args.strategy,
+                       "form": args.form, "tol": tol, "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (each n x k block is 4.3 GB); no flush"},
+            "converged": bool(ok), "iters": last["iters"], "n_shrink": last["n_shrink"],
+            "n_expand": last["n_expand"], "max_resid": float(np.max(last["resid"])),
+            "max_rel_eig_err_vs_closed_form": eig_err, "clocks": clk}
+
+    # per-kernel-class time shares and the roofline of the dominant kernel
+    tot_ms = sum(v["ms"] for v in kst.values())
+    line["kernel_share"] = {c: round(v["ms"] / tot_ms, 4) for c, v in kst.items() if v["launches"]}
+    line["gpu_launches"] = int(sum(LAUNCHES_PER_CALL[c] * v["launches"] for c, v in kst.items())
+                               / args.steps)
+    hbm, _, src = peaks()
+    dom = max(kst, key=lambda c: kst[c]["ms"])
+    v = kst[dom]
+    if dom == "spmm":
+        ach = v["bytes"] / (v["ms"] / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "peak_source": src}
+    else:
+        ach = v["flops"] / (v["ms"] / 1e3) / 1e12
+        pk = FP64_PEAK_TFLOPS if args.form == "f64" else DF64_PEAK_TFLOPS
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk,
+                "peak_source": "derived: FP32 issue rate measured on GB300 (36.3e12 FFMA/s) / "
+                               "11.1 FP32 instructions per double-float multiply-add x 2"
+                if args.form != "f64" else "measured native FP64 FMA rate"}
+    roof["avg_launch_ms"] = v["ms"] / max(v["launches"], 1)
+    roof["traffic"] = None
+    line["roofline"] = roof
+    sp = kst.get("spmm")
+    if sp and sp["launches"]:
+        a = sp["bytes"] / (sp["ms"] / 1e3) / 1e9
+        line["spmm_hbm"] = {"achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm}
+
+    if rank == 0 and not args.no_compare:
+        fixed = L.Solver((rp, ci, va), nev=nev, k_max=k, strategy="none", X0=X0d, normA=normA, tol=0.5 * tol,
+                         form=args.form, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fo = fixed.solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fms = e0.elapsed_time(e1)
+        line["fixed_block"] = {"value": nev / (fms / 1e3), "unit": UNIT, "ms": fms, "iters": fo["iters"],
+                               "converged": bool(fo["status"] == 0 and np.max(fo["resid"]) <= tol),
+                               "speedup_of_shrink_expand": fms / ms_step}
+        fixed.close()
+
+    if rank == 0 and not args.no_e2e:
+        # end to end through the public API: host CSR + pinned host X0 in,
+        # eigenvalues and eigenvectors back to the host
+        X0h = torch.as_tensor(X0).pin_memory()
+        Vh = torch.empty(A.n, nev, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = L.Solver(A, nev=nev, k_max=k, strategy=args.strategy, X0=X0h.numpy(), normA=normA, tol=0.5 * tol,
+                      form=args.form, stream=stream)
+        o2 = s2.solve()
+        Vd = s2.V()
+        Vh.copy_(Vd)
+        torch.cuda.synchronize()
+        s2.close()
+        t_e2e = time.perf_counter() - t0
+        h2d = A.indptr.nbytes + A.indices.nbytes + A.data.nbytes + X0.nbytes
+        line["e2e"] = {"value": nev / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(Vh.numel() * 8 + nev * 8), "seconds": t_e2e}
+
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(A, X0, nev, normA, last["iters"])
+
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -169,7 +169,19 @@ typedef struct {
   const double *X0;    /* n x k_max float64 row-major initial block (required)*/
   int x0_on_device;    /* 1: X0 is a device pointer                           */
   void *stream;        /* cudaStream_t the solve runs on                      */
+  int profile;         /* 1: time every kernel class with CUDA events          */
 } eig_options;
+
+/* kernel classes of the per-class statistics (eig_result.kstats) */
+#define EIG_K_SPMM 0
+#define EIG_K_GRAM 1
+#define EIG_K_UPDATE 2
+#define EIG_K_RESIDUAL 3
+#define EIG_K_CHOL 4
+#define EIG_K_SYEV 5
+#define EIG_K_HL 6
+#define EIG_K_OTHER 7
+#define EIG_NKCLASS 8
 
 typedef struct {
   int status;          /* EIG_OK or EIG_ENOTCONV / error of the last solve    */
@@ -183,6 +195,11 @@ typedef struct {
   const int *widths;      /* host, active width nnow at each iteration        */
   double time_ms;         /* wall time of eig_solve                            */
   double normA;
+  /* host, EIG_NKCLASS x 4 (launches, device ms, algorithmic flops,
+   * algorithmic DRAM bytes) per kernel class; all zero unless opt.profile.
+   * Flops count 2 per multiply-add in the arithmetic of the form; bytes
+   * count each n-sized operand read once and each result written once. */
+  const double *kstats;
 } eig_result;
 
 typedef struct eig_handle eig_handle;

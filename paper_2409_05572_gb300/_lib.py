@@ -46,14 +46,16 @@ class eig_options(C.Structure):
                 ("mu", C.c_double), ("r_warm", C.c_double), ("cheb_degree", C.c_int),
                 ("cheb_upper", C.c_double), ("precond", C.c_int), ("deflate_ones", C.c_int),
                 ("normA", C.c_double), ("mixed_switch", C.c_double), ("X0", C.c_void_p),
-                ("x0_on_device", C.c_int), ("stream", C.c_void_p)]
+                ("x0_on_device", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int)]
 
 
 class eig_result(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("n_shrink", C.c_int), ("n_expand", C.c_int),
                 ("nev", C.c_int), ("lambda_", C.POINTER(C.c_double)), ("resid", C.POINTER(C.c_double)),
                 ("V", C.c_void_p), ("history", C.POINTER(C.c_double)), ("widths", C.POINTER(C.c_int)),
-                ("time_ms", C.c_double), ("normA", C.c_double)]
+                ("time_ms", C.c_double), ("normA", C.c_double), ("kstats", C.POINTER(C.c_double))]
+
+KCLASSES = ("spmm", "gram", "update", "residual", "chol", "syev", "hl", "other")
 
 
 _lib = None
@@ -269,6 +271,10 @@ class Solver:
                        if r.widths else np.zeros(0, dtype=np.int32)),
             "time_ms": r.time_ms, "V_ptr": r.V,
         }
+        if r.kstats:
+            ks = np.ctypeslib.as_array(r.kstats, (len(KCLASSES), 4)).copy()
+            out["kstats"] = {name: {"launches": int(ks[i, 0]), "ms": ks[i, 1], "flops": ks[i, 2],
+                                    "bytes": ks[i, 3]} for i, name in enumerate(KCLASSES)}
         return out
 
     def V(self):

@@ -350,7 +350,7 @@ __global__ void gram_reduce_kernel(int a, int b, int nsplit, bool sym, const dou
   if (idx >= int64_t(a) * b) return;
   int i = int(idx / b), j = int(idx % b);
   int si = i, sj = j;
-  if (sym && (i / GT) > (j / GT)) {
+  if (sym && i > j) {  // mirror the upper triangle: exact symmetry
     si = j;
     sj = i;
   }

@@ -154,6 +154,15 @@ struct eig_handle {
   int status = EIG_OK, iters = 0, n_shrink = 0, n_expand = 0;
   double time_ms = 0.0;
   cudaError_t cuda_err = cudaSuccess;
+  // per-kernel-class statistics (opt.profile)
+  struct Rec {
+    cudaEvent_t a, b;
+    int cls;
+    double flops, bytes;
+  };
+  std::vector<Rec> pend;
+  std::vector<cudaEvent_t> evpool;
+  double kst[EIG_NKCLASS][4] = {};
 };
 
 #define CK(x)                      \
@@ -168,6 +177,51 @@ struct eig_handle {
 namespace {
 
 constexpr int F_CHOL1 = 0, F_CHOL2 = 1, F_CHOL3 = 2, F_SYEV = 4, NFLAGS = 8;
+
+// CUDA-event bracket of one kernel class when profiling is on
+cudaEvent_t ev_get(eig_handle* h) {
+  if (!h->evpool.empty()) {
+    cudaEvent_t e = h->evpool.back();
+    h->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+struct Prof {
+  eig_handle* h;
+  int cls;
+  double fl, by;
+  cudaEvent_t a = nullptr;
+  Prof(eig_handle* hh, int c, double flops, double bytes) : h(hh), cls(c), fl(flops), by(bytes) {
+    if (h->opt.profile) {
+      a = ev_get(h);
+      cudaEventRecord(a, h->st);
+    }
+  }
+  ~Prof() {
+    if (a) {
+      cudaEvent_t b = ev_get(h);
+      cudaEventRecord(b, h->st);
+      h->pend.push_back({a, b, cls, fl, by});
+    }
+  }
+};
+// resolve recorded brackets (stream already synchronised)
+void prof_flush(eig_handle* h) {
+  for (auto& r : h->pend) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    h->kst[r.cls][0] += 1.0;
+    h->kst[r.cls][1] += ms;
+    h->kst[r.cls][2] += r.flops;
+    h->kst[r.cls][3] += r.bytes;
+    h->evpool.push_back(r.a);
+    h->evpool.push_back(r.b);
+  }
+  h->pend.clear();
+}
 
 template <typename T>
 Blk<T> view(void* base, int64_t ld, int col, int w) {
@@ -218,15 +272,24 @@ struct Ops {
   }
   int64_t ld() const { return h->LDS; }
 
+  static constexpr double E = sizeof(T);
   // G = U^T V into h->Gp (leading dimension b)
   int gram(const Blk<T>& U, const Blk<T>& V, bool sym, const int* gate = nullptr) {
+    const double nn = double(h->n), a = U.width, b = V.width;
+    const bool same = U.ptr[0] == V.ptr[0];
+    Prof p(h, EIG_K_GRAM, sym ? nn * a * (b + 1) : 2.0 * nn * a * b, E * nn * (same ? a : a + b));
     CK(eig::gram<AG>(h->n, U, V, sym, h->Gp, V.width, h->gscr, st(), gate));
     return EIG_OK;
   }
   // Y = U (scale * C) + beta Y with C float64 (s x c, ldc)
   int upd(const Blk<T>& U, const double* C, int64_t ldc, int c, double scale, const Blk<T>& Y, double beta,
           const int* gate = nullptr) {
-    CK(stage_coef<AU>(U.width, c, C, ldc, static_cast<SU*>(h->Cs), c, scale, st(), gate));
+    {
+      Prof p(h, EIG_K_OTHER, 0.0, 0.0);
+      CK(stage_coef<AU>(U.width, c, C, ldc, static_cast<SU*>(h->Cs), c, scale, st(), gate));
+    }
+    const double nn = double(h->n);
+    Prof p(h, EIG_K_UPDATE, 2.0 * nn * U.width * c, E * nn * (U.width + c * (beta != 0.0 ? 2.0 : 1.0)));
     CK(eig::update<AU>(h->n, U, static_cast<SU*>(h->Cs), c, Y, beta, st(), gate));
     return EIG_OK;
   }
@@ -235,8 +298,14 @@ struct Ops {
     const int w = src.width;
     int rc = gram(src, src, true, gate);
     if (rc) return rc;
-    CK(chol_rinv(w, h->n, h->Gp, w, h->Rinv, h->cholw, h->flags + slot, st(), gate));
+    {
+      Prof p(h, EIG_K_CHOL, 2.0 * w * double(w) * w / 3.0, 0.0);
+      CK(chol_rinv(w, h->n, h->Gp, w, h->Rinv, h->cholw, h->flags + slot, st(), gate));
+    }
     return upd(src, h->Rinv, w, w, 1.0, dst, 0.0, gate);
+  }
+  double spmm_bytes(int w, int terms) const {
+    return (4.0 + E) * double(h->nnz) + 4.0 * double(h->n + 1) + E * double(h->n) * w * (1 + terms);
   }
   // project D against Q (D -= Q Q^T D)
   int project(const Blk<T>& Q, const Blk<T>& D) {
@@ -254,18 +323,28 @@ struct Ops {
     if ((rc = cholqr(Dsrc, Dmid, F_CHOL1))) return rc;
     // conditional third pass (shifted CholeskyQR3): Dmid -> Dsrc -> Dmid
     if ((rc = cholqr(Dmid, Dsrc, F_CHOL3, h->flags + F_CHOL1))) return rc;
-    CK(copy_blk<T>(h->n, Dsrc, Dmid, st(), h->flags + F_CHOL1));
+    {
+      Prof p(h, EIG_K_OTHER, 0.0, 0.0);
+      CK(copy_blk<T>(h->n, Dsrc, Dmid, st(), h->flags + F_CHOL1));
+    }
     if ((rc = project(Q, Dmid))) return rc;
     return cholqr(Dmid, Ddst, F_CHOL2);
   }
   int spmm(const T* V, int64_t ldv, int w, T* Y, int64_t ldy) {
+    Prof p(h, EIG_K_SPMM, 2.0 * double(h->nnz) * w, spmm_bytes(w, 1));
     CK(eig::spmm<AU>(csr(), w, V, ldv, Y, ldy, 1.0, 0.0, nullptr, 0, 0.0, st()));
+    return EIG_OK;
+  }
+  int spmm3(const T* V, int w, T* Y, double alpha, double beta, const T* U, double gamma) {
+    Prof p(h, EIG_K_SPMM, 2.0 * double(h->nnz) * w + 4.0 * double(h->n) * w, spmm_bytes(w, 3));
+    CK(eig::spmm<AU>(csr(), w, V, ld(), Y, ld(), alpha, beta, U, ld(), gamma, st()));
     return EIG_OK;
   }
   int spmm_blk(const Blk<T>& V, const Blk<T>& Y) {
     for (int t = 0; t < V.nseg; ++t) {
       const int w = V.start[t + 1] - V.start[t];
       // Y has the same segmentation by construction
+      Prof p(h, EIG_K_SPMM, 2.0 * double(h->nnz) * w, spmm_bytes(w, 1));
       CK(eig::spmm<AU>(csr(), w, V.ptr[t], V.ld[t], Y.ptr[t], Y.ld[t], 1.0, 0.0, nullptr, 0, 0.0, st()));
     }
     return EIG_OK;
@@ -274,19 +353,35 @@ struct Ops {
   int rr(const Blk<T>& S, const Blk<T>& ASb) {
     int rc = gram(S, ASb, true);
     if (rc) return rc;
+    const double sw = S.width;
+    Prof p(h, EIG_K_SYEV, (4.0 / 3.0 + 6.0) * sw * sw * sw, 0.0);
     CK(syev(S.width, h->Gp, S.width, h->lamd, h->Z, S.width, h->syevw, h->flags + F_SYEV, st()));
+    return EIG_OK;
+  }
+  int hl(int s, int nnow, int nlock, int npn) {
+    Prof p(h, EIG_K_HL, 4.0 * double(s) * (s - nnow) * (nnow - nlock), 0.0);
+    CK(hl_trick(s, nnow, nlock, h->Z, s, h->CP, npn, h->hlw, h->st));
+    return EIG_OK;
+  }
+  int axpby_(int w, const T* U, double a, const T* V, double b, T* Y) {
+    Prof p(h, EIG_K_OTHER, 4.0 * double(h->n) * w, 3.0 * E * double(h->n) * w);
+    CK(eig::axpby<AU>(h->n, w, U, ld(), a, V, ld(), b, Y, ld(), st()));
     return EIG_OK;
   }
   // residual norms (and R into Rdst when non-null); copies norms, lam and
   // flags to the host and synchronises.
   int resid(const T* X, const T* AX, int w, T* Rdst, bool precond) {
     const T* td = precond ? FormData<AU>::tdiag(h) : nullptr;
-    CK(eig::residual<AU>(h->n, w, X, ld(), AX, ld(), h->lamd, td, Rdst, ld(), h->xn, h->rn, h->rscr, st()));
+    {
+      Prof p(h, EIG_K_RESIDUAL, 6.0 * double(h->n) * w, E * double(h->n) * w * (Rdst ? 3.0 : 2.0));
+      CK(eig::residual<AU>(h->n, w, X, ld(), AX, ld(), h->lamd, td, Rdst, ld(), h->xn, h->rn, h->rscr, st()));
+    }
     CK(cudaMemcpyAsync(h->hpin, h->xn, sizeof(double) * w, cudaMemcpyDeviceToHost, st()));
     CK(cudaMemcpyAsync(h->hpin + h->kmax, h->rn, sizeof(double) * w, cudaMemcpyDeviceToHost, st()));
     CK(cudaMemcpyAsync(h->hpin + 2 * h->kmax, h->lamd, sizeof(double) * w, cudaMemcpyDeviceToHost, st()));
     CK(cudaMemcpyAsync(h->hpin + 3 * h->kmax, h->flags, sizeof(int) * NFLAGS, cudaMemcpyDeviceToHost, st()));
     CK(cudaStreamSynchronize(st()));
+    prof_flush(h);
     return EIG_OK;
   }
 };
@@ -456,7 +551,7 @@ int lobpcg_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* swit
     if ((rc = o.rr(Sb, ASb))) return rc;
     // improved Hetmaniuk-Lehoucq: C = [Z(:, :nnow) | C_P]
     const int npn = L.nnow - L.nlock;
-    CK(hl_trick(s, L.nnow, L.nlock, h->Z, s, h->CP, npn, h->hlw, h->st));
+    if ((rc = o.hl(s, L.nnow, L.nlock, npn))) return rc;
     // X, AX <- S C_X, AS C_X ; P, AP <- S C_P, AS C_P (next buffers)
     const int nx = 1 - L.cur;
     void* Sn = h->S[nx];
@@ -465,12 +560,22 @@ int lobpcg_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* swit
       using SU = typename Pol<AU>::S;
       SU* Cs = static_cast<SU*>(h->Cs);
       const int c = L.nnow + npn;
-      CK(stage_coef<AU>(s, L.nnow, h->Z, s, Cs, c, 1.0, h->st));
-      CK(stage_coef<AU>(s, npn, h->CP, npn, Cs + L.nnow, c, 1.0, h->st));
+      {
+        Prof p(h, EIG_K_OTHER, 0.0, 0.0);
+        CK(stage_coef<AU>(s, L.nnow, h->Z, s, Cs, c, 1.0, h->st));
+        CK(stage_coef<AU>(s, npn, h->CP, npn, Cs + L.nnow, c, 1.0, h->st));
+      }
       Blk<T> Yn = cat(view<T>(Sn, ld, 0, L.nnow), view<T>(Sn, ld, k, npn));
       Blk<T> AYn = cat(view<T>(ASn, ld, 0, L.nnow), view<T>(ASn, ld, k, npn));
-      CK(eig::update<AU>(h->n, Sb, Cs, c, Yn, 0.0, h->st));
-      CK(eig::update<AU>(h->n, ASb, Cs, c, AYn, 0.0, h->st));
+      const double fl = 2.0 * double(h->n) * s * c, by = Ops<AU, AG>::E * double(h->n) * (s + c);
+      {
+        Prof p(h, EIG_K_UPDATE, fl, by);
+        CK(eig::update<AU>(h->n, Sb, Cs, c, Yn, 0.0, h->st));
+      }
+      {
+        Prof p(h, EIG_K_UPDATE, fl, by);
+        CK(eig::update<AU>(h->n, ASb, Cs, c, AYn, 0.0, h->st));
+      }
     }
     L.cur = nx;
     L.np = npn;
@@ -542,13 +647,13 @@ int chebsi_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* swit
     const double tau = 2.0 / sigma;
     T* bufs[3] = {X, X + k, X + 2 * k};
     // Y1 = (sigma / e) (AX - c X)
-    CK(axpby<AU>(h->n, L.nnow, AX, ld, sigma / e, X, ld, -sigma * c / e, bufs[1], ld, h->st));
+    if ((rc = o.axpby_(L.nnow, AX, sigma / e, X, -sigma * c / e, bufs[1]))) return rc;
     int ip = 0, iy = 1;
     for (int d = 2; d <= h->opt.cheb_degree; ++d) {
       const double sn = 1.0 / (tau - sigma);
       const int inew = 3 - ip - iy;
-      CK(eig::spmm<AU>(o.csr(), L.nnow, bufs[iy], ld, bufs[inew], ld, 2.0 * sn / e, -2.0 * sn * c / e, bufs[ip], ld,
-                       -sigma * sn, h->st));
+      if ((rc = o.spmm3(bufs[iy], L.nnow, bufs[inew], 2.0 * sn / e, -2.0 * sn * c / e, bufs[ip], -sigma * sn)))
+        return rc;
       ip = iy;
       iy = inew;
       sigma = sn;
@@ -589,26 +694,52 @@ int chebsi_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* swit
 }
 
 // Convert the iterate of the float32 phase to double-float storage.
+// LOBPCG keeps X, P, AX, AP implicitly consistent, so after the conversion
+// [X, P] is re-orthonormalised (the float32 blocks are orthonormal only to
+// about 1e-7), AX and AP are recomputed by SpMM and a Rayleigh-Ritz step on X
+// restores Ritz vectors; without this the residual would stall near the
+// float32 level.
 int promote(eig_handle* h, LState& L, bool lobpcg) {
+  using T = dd;
   const int64_t ld = h->LDS;
   const int k = h->kmax;
-  const int nx = 1 - L.cur;
-  // X, AX (and P, AP) into the other buffers, then switch to them
-  CK(convert2d(h->n, L.nnow, h->S[L.cur], ld, EIG_F32, h->S[nx], ld, EIG_DF64, h->st));
-  CK(convert2d(h->n, L.nnow, h->AS[L.cur], ld, EIG_F32, h->AS[nx], ld, EIG_DF64, h->st));
-  if (lobpcg && L.np > 0) {
-    CK(convert2d(h->n, L.np, static_cast<float*>(h->S[L.cur]) + k + L.poff, ld, EIG_F32,
+  const int cur = L.cur, nx = 1 - L.cur;
+  CK(convert2d(h->n, L.nnow, h->S[cur], ld, EIG_F32, h->S[nx], ld, EIG_DF64, h->st));
+  CK(convert2d(h->n, L.nnow, h->AS[cur], ld, EIG_F32, h->AS[nx], ld, EIG_DF64, h->st));
+  if (lobpcg && L.np > 0)
+    CK(convert2d(h->n, L.np, static_cast<float*>(h->S[cur]) + k + L.poff, ld, EIG_F32,
                  static_cast<dd*>(h->S[nx]) + k, ld, EIG_DF64, h->st));
-    CK(convert2d(h->n, L.np, static_cast<float*>(h->AS[L.cur]) + k + L.poff, ld, EIG_F32,
-                 static_cast<dd*>(h->AS[nx]) + k, ld, EIG_DF64, h->st));
-    L.poff = 0;
-  }
   if (L.have_drop) {
     const int wd = lobpcg ? 2 * h->hdrop : h->hdrop;
     CK(convert2d(h->n, wd, h->Sd, wd, EIG_F32, h->Wt, wd, EIG_DF64, h->st));
     std::swap(h->Sd, h->Wt);
   }
-  L.cur = nx;
+  L.poff = 0;
+  if (!lobpcg) {
+    L.cur = nx;
+    return EIG_OK;
+  }
+  Ops<Arith::DF64, Arith::DF64> o(h);
+  Blk<T> D = cat(view<T>(h->S[nx], ld, 0, L.nnow), view<T>(h->S[nx], ld, k, L.np));
+  Blk<T> mid = view<T>(h->S[cur], ld, 0, L.nnow + L.np);
+  Blk<T> Q;
+  if (h->opt.deflate_ones) Q.add(h->udd, 1, 1);
+  int rc = o.orth(Q, D, mid, D);
+  if (rc) return rc;
+  Blk<T> X = view<T>(h->S[nx], ld, 0, L.nnow);
+  Blk<T> AX = view<T>(h->AS[nx], ld, 0, L.nnow);
+  if ((rc = o.spmm_blk(X, AX))) return rc;
+  if (L.np > 0 && (rc = o.spmm(static_cast<T*>(h->S[nx]) + k, ld, L.np, static_cast<T*>(h->AS[nx]) + k, ld)))
+    return rc;
+  if ((rc = o.rr(X, AX))) return rc;
+  if ((rc = o.upd(X, h->Z, L.nnow, L.nnow, 1.0, view<T>(h->S[cur], ld, 0, L.nnow), 0.0))) return rc;
+  if ((rc = o.upd(AX, h->Z, L.nnow, L.nnow, 1.0, view<T>(h->AS[cur], ld, 0, L.nnow), 0.0))) return rc;
+  if (L.np > 0) {
+    CK(cudaMemcpy2DAsync(static_cast<T*>(h->S[cur]) + k, sizeof(T) * ld, static_cast<T*>(h->S[nx]) + k,
+                         sizeof(T) * ld, sizeof(T) * L.np, h->n, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpy2DAsync(static_cast<T*>(h->AS[cur]) + k, sizeof(T) * ld, static_cast<T*>(h->AS[nx]) + k,
+                         sizeof(T) * ld, sizeof(T) * L.np, h->n, cudaMemcpyDeviceToDevice, h->st));
+  }
   return EIG_OK;
 }
 
@@ -651,6 +782,7 @@ int solve_impl(eig_handle* h) {
   h->history.clear();
   h->widths.clear();
   h->iters = 0;
+  std::memset(h->kst, 0, sizeof(h->kst));
   CK(cudaMemsetAsync(h->flags, 0, sizeof(int) * NFLAGS, h->st));
   const bool lob = h->opt.algo == EIG_LOBPCG;
   bool done = false, sw = false;
@@ -921,6 +1053,7 @@ int eig_solve(eig_handle* h) {
   auto t0 = std::chrono::steady_clock::now();
   int rc = solve_impl(h);
   cudaStreamSynchronize(h->st);
+  prof_flush(h);
   auto t1 = std::chrono::steady_clock::now();
   h->time_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
   h->status = rc;
@@ -941,12 +1074,15 @@ int eig_query(const eig_handle* h, eig_result* out) {
   out->widths = h->widths.empty() ? nullptr : h->widths.data();
   out->time_ms = h->time_ms;
   out->normA = h->opt.normA;
+  out->kstats = &h->kst[0][0];
   return EIG_OK;
 }
 
 void eig_destroy(eig_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
+  prof_flush(h);
+  for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   free_all(h);
   delete h;
 }

@@ -232,9 +232,9 @@ def test_cholqr2_shifted_path():
     assert st == 1
     Q = Wd.cpu().numpy()
     assert np.linalg.norm(Q.T @ Q - np.eye(w)) < 1e-12
-    # same span as the input (the oracle's shifted CholeskyQR3 result)
-    ref = B.cholqr2(Wm)
-    assert np.linalg.norm(Q @ (Q.T @ ref) - ref) < 1e-8
+    # Q captures the column space of W (directions with singular values near
+    # 1e-11 are fixed only to about u / sigma, so spans are not compared)
+    assert np.linalg.norm(Wm - Q @ (Q.T @ Wm)) < 1e-13 * np.linalg.norm(Wm)
 
 
 # ---------------------------------------------------------------------------
