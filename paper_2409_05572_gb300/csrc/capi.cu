@@ -97,8 +97,11 @@ int cholqr2_t(int64_t n, int w, void* W, int64_t ldw, int* status_out, cudaStrea
   auto pass = [&](const Blk<T>& src, const Blk<T>& dst, int slot, const int* gate) -> int {
     if (gram<A>(n, src, src, true, static_cast<double*>(G.p), w, static_cast<double*>(scr.p), st, gate))
       return EIG_ECUDA;
+    const double u = sizeof(T) == 4 ? 5.960464477539063e-08
+                                    : (sizeof(T) == 8 && A == Arith::DF64 ? 1.7763568394002505e-15
+                                                                         : 1.1102230246251565e-16);
     if (chol_rinv(w, n, static_cast<double*>(G.p), w, static_cast<double*>(Rinv.p), static_cast<double*>(work.p),
-                  fl + slot, st, gate))
+                  fl + slot, st, gate, u))
       return EIG_ECUDA;
     if (stage_coef<A>(w, w, static_cast<double*>(Rinv.p), w, static_cast<S*>(Cs.p), w, 1.0, st, gate))
       return EIG_ECUDA;

@@ -58,7 +58,7 @@ __device__ bool chol_upper_inplace(double* Rm, int w, int ld, const double* diag
 __global__ void __launch_bounds__(512) chol_rinv_kernel(int w, int64_t nrows, const double* __restrict__ G,
                                                         int64_t ldg, double* __restrict__ Rinv,
                                                         double* __restrict__ work, int* status,
-                                                        const int* gate) {
+                                                        const int* gate, double u) {
   if (gate && *gate == 0) return;
   extern __shared__ double smem[];
   __shared__ double sh[2];
@@ -78,7 +78,6 @@ __global__ void __launch_bounds__(512) chol_rinv_kernel(int w, int64_t nrows, co
     if (threadIdx.x == 0) {
       double tr = 0.0;
       for (int i = 0; i < w; ++i) tr += diag0[i];
-      const double u = 1.1102230246251565e-16;
       sh[1] = 11.0 * (double(nrows) * w + double(w) * (w + 1)) * u * tr;
     }
     __syncthreads();
@@ -117,7 +116,7 @@ __global__ void __launch_bounds__(512) chol_rinv_kernel(int w, int64_t nrows, co
 }
 
 cudaError_t chol_rinv(int w, int64_t nrows, const double* G, int64_t ldg, double* Rinv, double* work,
-                      int* status, cudaStream_t st, const int* gate) {
+                      int* status, cudaStream_t st, const int* gate, double unit_round) {
   const size_t need = (size_t(w) * w + w) * sizeof(double);
   const size_t shm = need <= 160 * 1024 ? need : 0;
   static bool attr = false;
@@ -125,7 +124,7 @@ cudaError_t chol_rinv(int w, int64_t nrows, const double* G, int64_t ldg, double
     cudaFuncSetAttribute(chol_rinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     attr = true;
   }
-  chol_rinv_kernel<<<1, 512, shm, st>>>(w, nrows, G, ldg, Rinv, work, status, gate);
+  chol_rinv_kernel<<<1, 512, shm, st>>>(w, nrows, G, ldg, Rinv, work, status, gate, unit_round);
   return cudaGetLastError();
 }
 
@@ -135,42 +134,43 @@ cudaError_t chol_rinv(int w, int64_t nrows, const double* G, int64_t ldg, double
 // k+1..s-1), tau[k]; d, e: diagonal and subdiagonal of T = Q^T A Q with
 // Q = H_0 H_1 ... H_{s-3}, H_k = I - tau_k v_k v_k^T.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  // 256-thread block reduction; all threads get the result
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < 8; ++i) t += red[i];
+  return t;
+}
+
 __global__ void __launch_bounds__(256) sytrd_kernel(int s, double* __restrict__ Wm, double* __restrict__ Vh,
                                                     double* __restrict__ tau, double* __restrict__ d,
                                                     double* __restrict__ e, double* __restrict__ p) {
   cg::grid_group grid = cg::this_grid();
-  extern __shared__ double vsh[];  // s doubles: current reflector
-  __shared__ double red[256];
-  __shared__ double scal[4];
+  extern __shared__ double sh[];  // vsh[s], psh[s]
+  double* vsh = sh;
+  double* psh = sh + s;
+  __shared__ double red[8];
   const int nb = gridDim.x, b = blockIdx.x, t = threadIdx.x;
+  const int warp = t >> 5, lane = t & 31;
+  const int gw = b * 8 + warp, nw = nb * 8;
   for (int k = 0; k + 2 < s; ++k) {
-    const int m = s - k - 1;  // length of x = Wm[k+1:, k]
-    // (a) reflector from column k (every CTA computes it identically)
+    const int m = s - k - 1;  // x = A[k+1:, k] = A[k, k+1:] (symmetric storage)
+    const double* rowk = Wm + int64_t(k) * s + (k + 1);
     double part = 0.0, part_tail = 0.0;
     for (int i = t; i < m; i += blockDim.x) {
-      const double x = Wm[(k + 1 + i) * s + k];
+      const double x = rowk[i];
       vsh[i] = x;
       part += x * x;
       if (i > 0) part_tail += x * x;
     }
-    red[t] = part;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (t < o) red[t] += red[t + o];
-      __syncthreads();
-    }
-    const double nrm2 = red[0];
-    __syncthreads();
-    red[t] = part_tail;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (t < o) red[t] += red[t + o];
-      __syncthreads();
-    }
-    const double tail2 = red[0];
-    __syncthreads();
-    double tk, alpha;
+    const double nrm2 = block_sum(part, red);
+    const double tail2 = block_sum(part_tail, red);
     const double x0 = vsh[0];
+    double tk, alpha;
     if (tail2 == 0.0) {
       tk = 0.0;
       alpha = x0;
@@ -179,61 +179,55 @@ __global__ void __launch_bounds__(256) sytrd_kernel(int s, double* __restrict__ 
       alpha = x0 >= 0.0 ? -nrm : nrm;
       const double v0 = x0 - alpha;
       tk = 2.0 / (tail2 + v0 * v0);
+      __syncthreads();
       if (t == 0) vsh[0] = v0;
     }
     __syncthreads();
     if (b == 0) {
-      for (int i = t; i < m; i += blockDim.x) Vh[k * s + k + 1 + i] = vsh[i];
+      for (int i = t; i < m; i += blockDim.x) Vh[int64_t(k) * s + k + 1 + i] = vsh[i];
       if (t == 0) {
         tau[k] = tk;
         e[k] = alpha;
-        d[k] = Wm[k * s + k];
+        d[k] = Wm[int64_t(k) * s + k];
       }
     }
     if (tk != 0.0) {
-      // (b) p = tau * W_sub v for this CTA's rows
-      for (int i = b * blockDim.x + t; i < m; i += nb * blockDim.x) {
-        const double* wr = Wm + (k + 1 + i) * s + (k + 1);
+      // p = tau W_sub v: one warp per row, lanes along the row
+      for (int i = gw; i < m; i += nw) {
+        const double* wr = Wm + int64_t(k + 1 + i) * s + (k + 1);
         double acc = 0.0;
-        for (int j = 0; j < m; ++j) acc += wr[j] * vsh[j];
-        p[i] = tk * acc;
+        for (int j = lane; j < m; j += 32) acc += wr[j] * vsh[j];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) p[i] = tk * acc;
       }
     }
     grid.sync();
     if (tk != 0.0) {
-      // (c) w = p - (tau/2)(p^T v) v  (computed redundantly by every CTA)
       double pv = 0.0;
-      for (int i = t; i < m; i += blockDim.x) pv += p[i] * vsh[i];
-      red[t] = pv;
-      __syncthreads();
-      for (int o = 128; o > 0; o >>= 1) {
-        if (t < o) red[t] += red[t + o];
-        __syncthreads();
+      for (int i = t; i < m; i += blockDim.x) {
+        const double pi = p[i];
+        psh[i] = pi;
+        pv += pi * vsh[i];
       }
-      const double K = 0.5 * tk * red[0];
-      __syncthreads();
-      // (d) rank-2 update of this CTA's rows: W -= v w^T + w v^T
-      for (int i = b; i < m; i += nb) {
+      const double K = 0.5 * tk * block_sum(pv, red);
+      // rank-2 update W -= v w^T + w v^T, w = p - K v; one warp per row
+      for (int i = gw; i < m; i += nw) {
         const double vi = vsh[i];
-        const double wi = p[i] - K * vi;
-        double* wr = Wm + (k + 1 + i) * s + (k + 1);
-        for (int j = t; j < m; j += blockDim.x) {
-          const double wj = p[j] - K * vsh[j];
-          wr[j] -= vi * wj + wi * vsh[j];
-        }
+        const double wi = psh[i] - K * vi;
+        double* wr = Wm + int64_t(k + 1 + i) * s + (k + 1);
+        for (int j = lane; j < m; j += 32) wr[j] -= vi * (psh[j] - K * vsh[j]) + wi * vsh[j];
       }
     }
     grid.sync();
   }
   if (b == 0 && t == 0) {
     if (s >= 2) {
-      d[s - 2] = Wm[(s - 2) * s + (s - 2)];
-      e[s - 2] = Wm[(s - 1) * s + (s - 2)];
+      d[s - 2] = Wm[int64_t(s - 2) * s + (s - 2)];
+      e[s - 2] = Wm[int64_t(s - 1) * s + (s - 2)];
     }
-    d[s - 1] = Wm[(s - 1) * s + (s - 1)];
+    d[s - 1] = Wm[int64_t(s - 1) * s + (s - 1)];
     e[s - 1] = 0.0;
   }
-  (void)scal;
 }
 
 // ---------------------------------------------------------------------------
@@ -271,7 +265,15 @@ __global__ void tql_kernel(int s, double* __restrict__ d, double* __restrict__ e
       for (int i = m - 1; i >= l; --i) {
         const double f = sn * e[i];
         const double bb = cs * e[i];
-        r = hypot(f, g);
+        const double hh = f * f + g * g;
+        double rinv;
+        if (hh > 1e-280 && hh < 1e280) {
+          rinv = rsqrt(hh);
+          r = hh * rinv;
+        } else {
+          r = hypot(f, g);
+          rinv = r != 0.0 ? 1.0 / r : 0.0;
+        }
         e[i + 1] = r;
         if (r == 0.0) {
           d[i + 1] -= p;
@@ -279,8 +281,8 @@ __global__ void tql_kernel(int s, double* __restrict__ d, double* __restrict__ e
           early = true;
           break;
         }
-        sn = f / r;
-        cs = g / r;
+        sn = f * rinv;
+        cs = g * rinv;
         g = d[i + 1] - p;
         r = (d[i] - g) * sn + 2.0 * cs * bb;
         p = sn * r;
@@ -304,24 +306,6 @@ __global__ void tql_kernel(int s, double* __restrict__ d, double* __restrict__ e
   *status = st;
 }
 
-// Q = H_0 H_1 ... H_{s-3} (row-major s x s), one thread per column.
-__global__ void form_q_kernel(int s, const double* __restrict__ Vh, const double* __restrict__ tau,
-                              double* __restrict__ Q) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= s) return;
-  for (int i = 0; i < s; ++i) Q[int64_t(i) * s + j] = (i == j) ? 1.0 : 0.0;
-  for (int k = s - 3; k >= 0; --k) {
-    if (j <= k) continue;  // column j <= k is still e_j on rows > k
-    const double tk = tau[k];
-    if (tk == 0.0) continue;
-    const double* v = Vh + int64_t(k) * s;
-    double dot = 0.0;
-    for (int i = k + 1; i < s; ++i) dot += v[i] * Q[int64_t(i) * s + j];
-    const double f = tk * dot;
-    for (int i = k + 1; i < s; ++i) Q[int64_t(i) * s + j] -= f * v[i];
-  }
-}
-
 // rank[c] = position of d[c] in ascending order (ties by index); lam sorted
 __global__ void rank_kernel(int s, const double* __restrict__ d, int* __restrict__ rank,
                             double* __restrict__ lam) {
@@ -337,18 +321,16 @@ __global__ void rank_kernel(int s, const double* __restrict__ d, int* __restrict
   lam[r] = v;
 }
 
-// Z[row][rank[c]] = (Q G_1 G_2 ...)[row][c]; RPB rows per CTA kept in shared
-// memory as [col][row].
-__global__ void apply_rot_kernel(int s, int rpb, const double* __restrict__ Q, const int* __restrict__ ri,
-                                 const double* __restrict__ rc, const double* __restrict__ rs,
-                                 const int64_t* __restrict__ nrot, const int* __restrict__ rank,
-                                 double* __restrict__ Z, int64_t ldz) {
+// Eigenvectors of T: Z_T = I G_1 G_2 ..., one thread per row (RPB rows per
+// CTA kept in shared memory as [col][row]); written column-major (ZTc[j][i]).
+__global__ void rot_accum_kernel(int s, int rpb, const int* __restrict__ ri, const double* __restrict__ rc,
+                                 const double* __restrict__ rs, const int64_t* __restrict__ nrot,
+                                 double* __restrict__ ZTc) {
   extern __shared__ double zs[];  // s * rpb
   const int r0 = blockIdx.x * rpb;
   for (int idx = threadIdx.x; idx < s * rpb; idx += blockDim.x) {
-    const int rr = idx / s, c = idx % s;
-    const int row = r0 + rr;
-    zs[c * rpb + rr] = row < s ? Q[int64_t(row) * s + c] : 0.0;
+    const int c = idx / rpb, rr = idx % rpb;
+    zs[idx] = (r0 + rr == c) ? 1.0 : 0.0;
   }
   __syncthreads();
   const int64_t nr = *nrot;
@@ -364,10 +346,39 @@ __global__ void apply_rot_kernel(int s, int rpb, const double* __restrict__ Q, c
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < s * rpb; idx += blockDim.x) {
-    const int rr = idx / s, c = idx % s;
+    const int c = idx / rpb, rr = idx % rpb;
     const int row = r0 + rr;
-    if (row < s) Z[int64_t(row) * ldz + rank[c]] = zs[c * rpb + rr];
+    if (row < s) ZTc[int64_t(c) * s + row] = zs[idx];
   }
+}
+
+// Z(:, rank[j]) = H_0 H_1 ... H_{s-3} Z_T(:, j): one warp per eigenvector,
+// the vector in shared memory, lanes along the reflector.
+__global__ void __launch_bounds__(256) backtrans_kernel(int s, int wpb, const double* __restrict__ Vh,
+                                                        const double* __restrict__ tau,
+                                                        const double* __restrict__ ZTc,
+                                                        const int* __restrict__ rank, double* __restrict__ Z,
+                                                        int64_t ldz) {
+  extern __shared__ double zw[];  // wpb warps x s
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * wpb + warp;
+  if (j >= s) return;
+  double* z = zw + int64_t(warp) * s;
+  for (int i = lane; i < s; i += 32) z[i] = ZTc[int64_t(j) * s + i];
+  __syncwarp();
+  for (int k = s - 3; k >= 0; --k) {
+    const double tk = tau[k];
+    if (tk == 0.0) continue;
+    const double* v = Vh + int64_t(k) * s;
+    double dot = 0.0;
+    for (int i = k + 1 + lane; i < s; i += 32) dot += v[i] * z[i];
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    const double f = tk * dot;
+    for (int i = k + 1 + lane; i < s; i += 32) z[i] -= f * v[i];
+    __syncwarp();
+  }
+  const int col = rank[j];
+  for (int i = lane; i < s; i += 32) Z[int64_t(i) * ldz + col] = z[i];
 }
 
 __global__ void small_tridiag_kernel(int s, const double* Wm, double* d, double* e, double* tau) {
@@ -395,7 +406,7 @@ size_t syev_work_bytes(int s) {
   const size_t ss = size_t(s) * s;
   const size_t cap = 64 * ss + 1024;
   return (3 * ss + 6 * size_t(s)) * sizeof(double) + cap * (2 * sizeof(double) + sizeof(int)) +
-         size_t(s) * sizeof(int) + 64;
+         size_t(s) * sizeof(int) + 256;
 }
 
 struct SyevWork {
@@ -438,18 +449,15 @@ cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, in
   const int64_t ss = int64_t(s) * s;
   copy_sym_kernel<<<(unsigned)cdiv(ss, 256), 256, 0, st>>>(s, A, lda, w.Wm);
   if (s >= 3) {
-    int nb = s / 32;
-    if (nb < 1) nb = 1;
+    int nb = (s + 7) / 8;  // about one warp per row of the trailing matrix
     if (nb > num_sms()) nb = num_sms();
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int per_sm = 0;
-    const size_t shm = size_t(s) * sizeof(double);
+    const size_t shm = 2 * size_t(s) * sizeof(double);
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(sytrd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+      cudaFuncSetAttribute(sytrd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
       attr = true;
     }
+    int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sytrd_kernel, 256, shm);
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int sv = s;
@@ -461,17 +469,22 @@ cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, in
     small_tridiag_kernel<<<1, 32, 0, st>>>(s, w.Wm, w.d, w.e, w.tau);
   }
   tql_kernel<<<1, 32, 0, st>>>(s, w.d, w.e, w.ri, w.rc, w.rs, w.cap, w.nrot, status_dev ? status_dev : w.status);
-  form_q_kernel<<<(unsigned)cdiv(s, 32), 32, 0, st>>>(s, w.Vh, w.tau, w.Q);
   rank_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.d, w.rank, lam);
   int rpb = 32;
   while (rpb > 1 && size_t(s) * rpb * 8 > 200 * 1024) rpb >>= 1;
   static bool attr2 = false;
   if (!attr2) {
-    cudaFuncSetAttribute(apply_rot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(rot_accum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(backtrans_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     attr2 = true;
   }
-  apply_rot_kernel<<<(unsigned)cdiv(s, rpb), 128, size_t(s) * rpb * 8, st>>>(s, rpb, w.Q, w.ri, w.rc, w.rs,
-                                                                               w.nrot, w.rank, Z, ldz);
+  // w.Q holds Z_T column-major
+  rot_accum_kernel<<<(unsigned)cdiv(s, rpb), 64, size_t(s) * rpb * 8, st>>>(s, rpb, w.ri, w.rc, w.rs, w.nrot,
+                                                                              w.Q);
+  int wpb = 8;
+  while (wpb > 1 && size_t(wpb) * s * 8 > 200 * 1024) --wpb;
+  backtrans_kernel<<<(unsigned)cdiv(s, wpb), 32 * wpb, size_t(wpb) * s * 8, st>>>(s, wpb, w.Vh, w.tau, w.Q, w.rank,
+                                                                                 Z, ldz);
   return cudaGetLastError();
 }
 

@@ -273,6 +273,10 @@ struct Ops {
   int64_t ld() const { return h->LDS; }
 
   static constexpr double E = sizeof(T);
+  // unit roundoff of the block storage (shift of the shifted CholeskyQR)
+  static constexpr double kUnitRound = sizeof(T) == 4 ? 5.960464477539063e-08
+                                       : (std::is_same<T, dd>::value ? 1.7763568394002505e-15
+                                                                     : 1.1102230246251565e-16);
   // G = U^T V into h->Gp (leading dimension b)
   int gram(const Blk<T>& U, const Blk<T>& V, bool sym, const int* gate = nullptr) {
     const double nn = double(h->n), a = U.width, b = V.width;
@@ -300,7 +304,7 @@ struct Ops {
     if (rc) return rc;
     {
       Prof p(h, EIG_K_CHOL, 2.0 * w * double(w) * w / 3.0, 0.0);
-      CK(chol_rinv(w, h->n, h->Gp, w, h->Rinv, h->cholw, h->flags + slot, st(), gate));
+      CK(chol_rinv(w, h->n, h->Gp, w, h->Rinv, h->cholw, h->flags + slot, st(), gate, kUnitRound));
     }
     return upd(src, h->Rinv, w, w, 1.0, dst, 0.0, gate);
   }
@@ -380,6 +384,7 @@ struct Ops {
     CK(cudaMemcpyAsync(h->hpin + h->kmax, h->rn, sizeof(double) * w, cudaMemcpyDeviceToHost, st()));
     CK(cudaMemcpyAsync(h->hpin + 2 * h->kmax, h->lamd, sizeof(double) * w, cudaMemcpyDeviceToHost, st()));
     CK(cudaMemcpyAsync(h->hpin + 3 * h->kmax, h->flags, sizeof(int) * NFLAGS, cudaMemcpyDeviceToHost, st()));
+    CK(cudaMemsetAsync(h->flags, 0, sizeof(int) * NFLAGS, st()));
     CK(cudaStreamSynchronize(st()));
     prof_flush(h);
     return EIG_OK;
@@ -455,9 +460,9 @@ int lobpcg_init(eig_handle* h, LState& L) {
   Blk<T> AX = view<T>(h->AS[1], ld, 0, k);
   if ((rc = o.spmm_blk(Xd, AX))) return rc;
   if ((rc = o.rr(Xd, AX))) return rc;
-  // X <- X Z, AX <- AX Z into buffer 0
+  // X <- X Z into buffer 0, AX = A X
   if ((rc = o.upd(Xd, h->Z, k, k, 1.0, view<T>(h->S[0], ld, 0, k), 0.0))) return rc;
-  if ((rc = o.upd(AX, h->Z, k, k, 1.0, view<T>(h->AS[0], ld, 0, k), 0.0))) return rc;
+  if ((rc = o.spmm(static_cast<T*>(h->S[0]), ld, k, static_cast<T*>(h->AS[0]), ld))) return rc;
   L.cur = 0;
   L.nnow = k;
   L.np = 0;
@@ -566,16 +571,15 @@ int lobpcg_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* swit
         CK(stage_coef<AU>(s, npn, h->CP, npn, Cs + L.nnow, c, 1.0, h->st));
       }
       Blk<T> Yn = cat(view<T>(Sn, ld, 0, L.nnow), view<T>(Sn, ld, k, npn));
-      Blk<T> AYn = cat(view<T>(ASn, ld, 0, L.nnow), view<T>(ASn, ld, k, npn));
       const double fl = 2.0 * double(h->n) * s * c, by = Ops<AU, AG>::E * double(h->n) * (s + c);
       {
         Prof p(h, EIG_K_UPDATE, fl, by);
         CK(eig::update<AU>(h->n, Sb, Cs, c, Yn, 0.0, h->st));
       }
-      {
-        Prof p(h, EIG_K_UPDATE, fl, by);
-        CK(eig::update<AU>(h->n, ASb, Cs, c, AYn, 0.0, h->st));
-      }
+      // AX, AP of the new blocks by SpMM (nnz/n is small, so A X costs far
+      // less than AS C and keeps AX consistent with X)
+      if ((rc = o.spmm(static_cast<T*>(Sn), ld, L.nnow, static_cast<T*>(ASn), ld))) return rc;
+      if ((rc = o.spmm(static_cast<T*>(Sn) + k, ld, npn, static_cast<T*>(ASn) + k, ld))) return rc;
     }
     L.cur = nx;
     L.np = npn;
@@ -679,9 +683,9 @@ int chebsi_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* swit
     if ((rc = o.spmm_blk(Xo, AXo))) return rc;
     h->widths.push_back(L.nnow);
     if ((rc = o.rr(Xo, AXo))) return rc;
-    // X <- X Z, AX <- AX Z back into the current buffers
+    // X <- X Z back into the current buffer, AX = A X
     if ((rc = o.upd(Xo, h->Z, L.nnow, L.nnow, 1.0, view<T>(Sc, ld, 0, L.nnow), 0.0))) return rc;
-    if ((rc = o.upd(AXo, h->Z, L.nnow, L.nnow, 1.0, view<T>(ASc, ld, 0, L.nnow), 0.0))) return rc;
+    if ((rc = o.spmm(X, ld, L.nnow, AX, ld))) return rc;
     if (L.se.ifshrink(j, L.nnow)) {
       const int hd = h->hdrop;
       CK(cudaMemcpy2DAsync(h->Sd, sizeof(T) * hd, static_cast<T*>(Sc) + nes, sizeof(T) * ld, sizeof(T) * hd,
@@ -733,7 +737,7 @@ int promote(eig_handle* h, LState& L, bool lobpcg) {
     return rc;
   if ((rc = o.rr(X, AX))) return rc;
   if ((rc = o.upd(X, h->Z, L.nnow, L.nnow, 1.0, view<T>(h->S[cur], ld, 0, L.nnow), 0.0))) return rc;
-  if ((rc = o.upd(AX, h->Z, L.nnow, L.nnow, 1.0, view<T>(h->AS[cur], ld, 0, L.nnow), 0.0))) return rc;
+  if ((rc = o.spmm(static_cast<T*>(h->S[cur]), ld, L.nnow, static_cast<T*>(h->AS[cur]), ld))) return rc;
   if (L.np > 0) {
     CK(cudaMemcpy2DAsync(static_cast<T*>(h->S[cur]) + k, sizeof(T) * ld, static_cast<T*>(h->S[nx]) + k,
                          sizeof(T) * ld, sizeof(T) * L.np, h->n, cudaMemcpyDeviceToDevice, h->st));
