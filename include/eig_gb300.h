@@ -87,6 +87,29 @@ int eig_spmm(int64_t n, const int32_t *rowptr, const int32_t *colind, const void
 int eig_gram(int64_t n, int a, int b, const void *U, int64_t ldu, const void *V, int64_t ldv,
              int arith, int sym, double *G, int64_t ldg, void *stream);
 
+/* ---- allocation-free Gram product (no counterpart in the paper) ---------
+ * Same product, arguments and result as eig_gram, for callers that cannot
+ * allocate device memory while they run: a serving process that gave all of
+ * HBM to its own memory pool at start-up, or host code running where a
+ * cudaMalloc / cudaFree (which can synchronise the device or fail under
+ * memory pressure) is not allowed.  Instead of cudaMallocAsync it uses one
+ * fixed scratch array of EIG_NOALLOC_SCRATCH_DOUBLES float64 elements
+ * (16 MiB) built into the library; every GPU that loads the library keeps it
+ * until the process exits.  Calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *  - Returns EIG_EINVAL when a * b > EIG_NOALLOC_SCRATCH_DOUBLES (the result
+ *    would not fit even without splitting the reduction); large n is fine, the
+ *    reduction is then split over fewer CTAs.
+ *  - The first call on each device looks up the scratch address on that
+ *    device (cudaGetSymbolAddress); make that first call before any CUDA
+ *    stream capture.
+ *  - All calls share the scratch: calls whose kernels may overlap on the GPU
+ *    (unordered streams, several host threads) race and must be serialised
+ *    by the caller.  Nothing in the scratch needs to start at zero. */
+#define EIG_NOALLOC_SCRATCH_DOUBLES (2 * 1024 * 1024)
+int eig_gram_noalloc(int64_t n, int a, int b, const void *U, int64_t ldu, const void *V,
+                     int64_t ldv, int arith, int sym, double *G, int64_t ldg, void *stream);
+
 /* ---- a4 / a11: block update (X <- S C_X, P <- S C_P, W <- W - Q C) ------
  * Y = U C + beta * Y.  U: n x s block, C: s x c float64 row-major (device,
  * leading dimension ldc), Y: n x c block; U and Y use the element format of

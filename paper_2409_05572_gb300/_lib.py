@@ -24,7 +24,7 @@ STRATEGIES = {"none": 0, "fix": 1, "slope": 2, "slopek": 3}
 ALGOS = {"lobpcg": 0, "chebsi": 1}
 FORMS = {"df64": 0, "f64": 1, "mixed": 2}
 
-EXPORTS = ("eig_convert", "eig_spmm", "eig_gram", "eig_block_update", "eig_residual", "eig_cholqr2",
+EXPORTS = ("eig_convert", "eig_spmm", "eig_gram", "eig_gram_noalloc", "eig_block_update", "eig_residual", "eig_cholqr2",
            "eig_syev", "eig_hl_trick", "eig_options_default", "eig_create", "eig_solve", "eig_query",
            "eig_destroy", "eig_strerror")
 
@@ -75,6 +75,7 @@ def load(path: str = LIB_PATH):
         "eig_convert": [i64, p, i32, p, i32, p],
         "eig_spmm": [i64, p, p, p, i32, i32, p, i64, p, i64, d, d, p, i64, d, p],
         "eig_gram": [i64, i32, i32, p, i64, p, i64, i32, i32, p, i64, p],
+        "eig_gram_noalloc": [i64, i32, i32, p, i64, p, i64, i32, i32, p, i64, p],
         "eig_block_update": [i64, i32, i32, p, i64, p, i64, p, i64, d, i32, p],
         "eig_residual": [i64, i32, p, i64, p, i64, p, p, p, i64, p, p, i32, p],
         "eig_cholqr2": [i64, i32, p, i64, i32, C.POINTER(C.c_int), p],
@@ -165,6 +166,16 @@ def eig_spmm(n, rowptr, colind, val, dtype, w, V, ldv, Y, ldy, alpha=1.0, beta=0
 def eig_gram(n, a, b, U, ldu, V, ldv, arith, sym, G, ldg, stream=None):
     return _check("eig_gram", load().eig_gram(n, a, b, _ptr(U), ldu, _ptr(V), ldv, arith, int(sym), _ptr(G), ldg,
                                               _stream(stream)))
+
+
+def eig_gram_noalloc(n, a, b, U, ldu, V, ldv, arith, sym, G, ldg, stream=None):
+    """eig_gram without device allocation (fixed built-in scratch, shared by
+    all calls; a * b must not exceed NOALLOC_SCRATCH_DOUBLES)."""
+    return _check("eig_gram_noalloc", load().eig_gram_noalloc(n, a, b, _ptr(U), ldu, _ptr(V), ldv, arith, int(sym),
+                                                              _ptr(G), ldg, _stream(stream)))
+
+
+NOALLOC_SCRATCH_DOUBLES = 2 * 1024 * 1024
 
 
 def eig_block_update(n, s, c, U, ldu, Cm, ldc, Y, ldy, beta, arith, stream=None):

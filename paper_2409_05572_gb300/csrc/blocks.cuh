@@ -28,6 +28,14 @@ cudaError_t gram(int64_t n, const Blk<typename Pol<A>::T>& U, const Blk<typename
                  bool sym, double* G, int64_t ldg, double* scratch, cudaStream_t st,
                  const int* gate = nullptr);
 
+// gram() with the split-K count limited so the partial tiles fit in
+// max_scratch_elems float64 elements; cudaErrorInvalidValue if even one
+// split does not fit (a * b > max_scratch_elems).
+template <Arith A>
+cudaError_t gram_capped(int64_t n, const Blk<typename Pol<A>::T>& U, const Blk<typename Pol<A>::T>& V,
+                        bool sym, double* G, int64_t ldg, double* scratch, size_t max_scratch_elems,
+                        cudaStream_t st);
+
 // Cs[i][j] (leading dimension ldo) = staged(scale * C[i][j]) for an s x c
 // float64 matrix.
 template <Arith A>

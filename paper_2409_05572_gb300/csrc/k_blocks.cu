@@ -391,6 +391,29 @@ cudaError_t gram(int64_t n, const Blk<typename Pol<A>::T>& U, const Blk<typename
   return cudaGetLastError();
 }
 
+// Same product with the split count capped so that the partial tiles fit in
+// max_scratch_elems float64 elements (used by the allocation-free entry
+// point, whose scratch has a fixed size).
+template <Arith A>
+cudaError_t gram_capped(int64_t n, const Blk<typename Pol<A>::T>& U, const Blk<typename Pol<A>::T>& V,
+                        bool sym, double* G, int64_t ldg, double* scratch, size_t max_scratch_elems,
+                        cudaStream_t st) {
+  const int a = U.width, b = V.width;
+  if (a <= 0 || b <= 0) return cudaSuccess;
+  const size_t ab = size_t(a) * size_t(b);
+  if (ab > max_scratch_elems) return cudaErrorInvalidValue;
+  int ns = gram_nsplit(n, a, b, sym);
+  const size_t cap = max_scratch_elems / ab;
+  if (size_t(ns) > cap) ns = int(cap);
+  int64_t rps = cdiv(n, ns);
+  rps = cdiv(rps, GK) * GK;
+  dim3 grid((b + GT - 1) / GT, (a + GT - 1) / GT, ns);
+  gram_kernel<A><<<grid, 256, 0, st>>>(n, U, V, sym, rps, scratch, nullptr);
+  const int64_t tot = int64_t(a) * b;
+  gram_reduce_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(a, b, ns, sym, scratch, G, ldg, nullptr);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // K3: block update Y = U C + beta Y (row-streaming GEMM, C staged).
 // CTA (tn, tm) computes rows [64 tm, 64 tm + 64) x columns [64 tn, ...);
@@ -726,5 +749,13 @@ EIG_INST(Arith::F64)
 EIG_INST(Arith::DF64)
 EIG_INST(Arith::F32)
 EIG_INST(Arith::C32)
+
+#define EIG_INST_CAPPED(A)                                                                          \
+  template cudaError_t gram_capped<A>(int64_t, const Blk<Pol<A>::T>&, const Blk<Pol<A>::T>&, bool, \
+                                      double*, int64_t, double*, size_t, cudaStream_t);
+EIG_INST_CAPPED(Arith::F64)
+EIG_INST_CAPPED(Arith::DF64)
+EIG_INST_CAPPED(Arith::F32)
+EIG_INST_CAPPED(Arith::C32)
 
 }  // namespace eig
