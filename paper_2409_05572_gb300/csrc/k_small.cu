@@ -236,9 +236,19 @@ __global__ void __launch_bounds__(256) sytrd_kernel(int s, double* __restrict__ 
 // eigenvector columns (i, i+1) is appended to (ri, rc, rs):
 //   z_i <- c z_i - s z_{i+1},  z_{i+1} <- s z_i + c z_{i+1}.
 // ---------------------------------------------------------------------------
-__global__ void tql_kernel(int s, double* __restrict__ d, double* __restrict__ e, int* __restrict__ ri,
+__global__ void tql_kernel(int s, double* __restrict__ dg, double* __restrict__ eg, int* __restrict__ ri,
                            double* __restrict__ rc, double* __restrict__ rs, int64_t cap,
                            int64_t* nrot, int* status) {
+  // d and e live in shared memory while the single thread iterates: the
+  // rotation chain is latency bound and global round trips would dominate.
+  extern __shared__ double de[];
+  double* d = de;
+  double* e = de + s;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    d[i] = dg[i];
+    e[i] = eg[i];
+  }
+  __syncthreads();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double eps = 2.220446049250313e-16;
   int64_t cnt = 0;
@@ -304,6 +314,10 @@ __global__ void tql_kernel(int s, double* __restrict__ d, double* __restrict__ e
   if (cnt > cap) st = 2;
   *nrot = cnt < cap ? cnt : cap;
   *status = st;
+  for (int i = 0; i < s; ++i) {
+    dg[i] = d[i];
+    eg[i] = e[i];
+  }
 }
 
 // rank[c] = position of d[c] in ascending order (ties by index); lam sorted
@@ -336,13 +350,27 @@ __global__ void rot_accum_kernel(int s, int rpb, const int* __restrict__ ri, con
   const int64_t nr = *nrot;
   const int t = threadIdx.x;
   if (t < rpb) {
+    // Within a QL sweep consecutive rotations act on (i, i+1) then
+    // (i-1, i): the new z_i is carried in a register instead of a shared
+    // memory round trip.
+    int prev = -2;
+    double carry = 0.0;
     for (int64_t q = 0; q < nr; ++q) {
       const int i = __ldg(ri + q);
       const double c = __ldg(rc + q), sn = __ldg(rs + q);
-      const double a = zs[i * rpb + t], b = zs[(i + 1) * rpb + t];
-      zs[i * rpb + t] = c * a - sn * b;
+      double b;
+      if (i + 1 == prev) {
+        b = carry;
+      } else {
+        if (prev >= 0) zs[prev * rpb + t] = carry;
+        b = zs[(i + 1) * rpb + t];
+      }
+      const double a = zs[i * rpb + t];
       zs[(i + 1) * rpb + t] = sn * a + c * b;
+      carry = c * a - sn * b;
+      prev = i;
     }
+    if (prev >= 0) zs[prev * rpb + t] = carry;
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < s * rpb; idx += blockDim.x) {
@@ -468,7 +496,13 @@ cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, in
     // s <= 2: the matrix is already tridiagonal and Q = I
     small_tridiag_kernel<<<1, 32, 0, st>>>(s, w.Wm, w.d, w.e, w.tau);
   }
-  tql_kernel<<<1, 32, 0, st>>>(s, w.d, w.e, w.ri, w.rc, w.rs, w.cap, w.nrot, status_dev ? status_dev : w.status);
+  static bool attr3 = false;
+  if (!attr3) {
+    cudaFuncSetAttribute(tql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr3 = true;
+  }
+  tql_kernel<<<1, 32, 2 * size_t(s) * sizeof(double), st>>>(s, w.d, w.e, w.ri, w.rc, w.rs, w.cap, w.nrot,
+                                                             status_dev ? status_dev : w.status);
   rank_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.d, w.rank, lam);
   int rpb = 32;
   while (rpb > 1 && size_t(s) * rpb * 8 > 200 * 1024) rpb >>= 1;

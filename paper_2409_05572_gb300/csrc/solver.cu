@@ -18,6 +18,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -118,7 +119,7 @@ struct eig_handle {
   int nev = 0, kmax = 0, nes = 0, strategy = 0;
   eig_options opt{};
   cudaStream_t st = nullptr;
-  int LDS = 0, hdrop = 0, wtw = 0;
+  int LDS = 0, hdrop = 0, wtw = 0, cqmax = 0;
 
   // CSR (device)
   int32_t *rowptr = nullptr, *colind = nullptr;
@@ -177,6 +178,15 @@ struct eig_handle {
 namespace {
 
 constexpr int F_CHOL1 = 0, F_CHOL2 = 1, F_CHOL3 = 2, F_SYEV = 4, NFLAGS = 8;
+
+bool debug_on() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("EIG_DEBUG");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
 
 // CUDA-event bracket of one kernel class when profiling is on
 cudaEvent_t ev_get(eig_handle* h) {
@@ -300,6 +310,7 @@ struct Ops {
   // one CholeskyQR pass: dst = src R^{-1}; status into flags[slot]
   int cholqr(const Blk<T>& src, const Blk<T>& dst, int slot, const int* gate = nullptr) {
     const int w = src.width;
+    if (w > h->cqmax) return EIG_EINVAL;  // work buffers are sized for cqmax
     int rc = gram(src, src, true, gate);
     if (rc) return rc;
     {
@@ -311,6 +322,30 @@ struct Ops {
   double spmm_bytes(int w, int terms) const {
     return (4.0 + E) * double(h->nnz) + 4.0 * double(h->n + 1) + E * double(h->n) * w * (1 + terms);
   }
+  // debug: min / max column norm of a block (EIG_DEBUG=1 only)
+  void dbg(const char* label, const Blk<T>& B) {
+    if (!debug_on() || B.width == 0) return;
+    if (gram(B, B, true)) return;
+    std::vector<double> g(size_t(B.width) * B.width);
+    cudaMemcpyAsync(g.data(), h->Gp, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, st());
+    cudaStreamSynchronize(st());
+    double mn = 1e300, mx = -1e300, off = 0.0;
+    int nan = 0, first_nan_col = -1;
+    for (int i = 0; i < B.width; ++i) {
+      mn = std::min(mn, g[size_t(i) * B.width + i]);
+      mx = std::max(mx, g[size_t(i) * B.width + i]);
+      for (int j = 0; j < B.width; ++j) {
+        const double v = g[size_t(i) * B.width + j];
+        if (!std::isfinite(v)) {
+          ++nan;
+          if (first_nan_col < 0) first_nan_col = j;
+        }
+        if (i != j) off = std::max(off, std::fabs(v));
+      }
+    }
+    std::fprintf(stderr, "[eig]   %s: w=%d diag(G) in [%.3e, %.3e], max offdiag %.3e, nonfinite %d (col %d)\n",
+                 label, B.width, mn, mx, off, nan, first_nan_col);
+  }
   // project D against Q (D -= Q Q^T D)
   int project(const Blk<T>& Q, const Blk<T>& D) {
     if (Q.width == 0) return EIG_OK;
@@ -321,10 +356,29 @@ struct Ops {
   // Orthonormal basis of (I - Q Q^T) Dsrc, written to Ddst: two passes of
   // projection + CholeskyQR (a third CholeskyQR when the first needed the
   // shift).  Dmid is scratch; Dsrc is clobbered (Ddst may alias Dsrc).
-  int orth(const Blk<T>& Q, const Blk<T>& Dsrc, const Blk<T>& Dmid, const Blk<T>& Ddst) {
+  int orth(const Blk<T>& Q, const Blk<T>& Dsrc, const Blk<T>& Dmid, const Blk<T>& Ddst, bool trace = false) {
     int rc;
     if ((rc = project(Q, Dsrc))) return rc;
+    if (trace) dbg("  after projection 1", Dsrc);
     if ((rc = cholqr(Dsrc, Dmid, F_CHOL1))) return rc;
+    if (trace) {
+      int f[4];
+      const int w = Dsrc.width;
+      std::vector<double> g(size_t(w) * w), ri(size_t(w) * w);
+      cudaMemcpyAsync(f, h->flags, sizeof(f), cudaMemcpyDeviceToHost, st());
+      cudaMemcpyAsync(g.data(), h->Gp, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, st());
+      cudaMemcpyAsync(ri.data(), h->Rinv, sizeof(double) * ri.size(), cudaMemcpyDeviceToHost, st());
+      cudaStreamSynchronize(st());
+      std::fprintf(stderr, "[eig]   flags after cholqr 1: %d %d %d\n", f[0], f[1], f[2]);
+      for (int i = 0; i < std::min(w, 4); ++i) {
+        std::fprintf(stderr, "[eig]   G[%d] =", i);
+        for (int j = 0; j < std::min(w, 6); ++j) std::fprintf(stderr, " %.4e", g[size_t(i) * w + j]);
+        std::fprintf(stderr, " | Rinv:");
+        for (int j = 0; j < std::min(w, 6); ++j) std::fprintf(stderr, " %.4e", ri[size_t(i) * w + j]);
+        std::fprintf(stderr, "\n");
+      }
+      dbg("  after cholqr 1", Dmid);
+    }
     // conditional third pass (shifted CholeskyQR3): Dmid -> Dsrc -> Dmid
     if ((rc = cholqr(Dmid, Dsrc, F_CHOL3, h->flags + F_CHOL1))) return rc;
     {
@@ -419,6 +473,9 @@ ConvInfo conv_test(eig_handle* h, int w) {
   }
   ci.r = r;
   ci.breakdown = fl[F_CHOL1] == 2 || fl[F_CHOL2] == 2 || fl[F_CHOL3] == 2 || fl[F_SYEV] != 0;
+  if (debug_on())
+    std::fprintf(stderr, "[eig] j=%d w=%d r=%.3e nlock=%d flags chol=%d/%d/%d syev=%d\n", h->iters + 1, w, r,
+                 ci.nlock, fl[F_CHOL1], fl[F_CHOL2], fl[F_CHOL3], fl[F_SYEV]);
   return ci;
 }
 
@@ -537,7 +594,10 @@ int lobpcg_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* swit
       Blk<T> Dmid = view<T>(h->Wt, h->wtw, 0, 2 * hd);
       Blk<T> Ddst = cat(view<T>(Sc, ld, L.nnow, hd), view<T>(Sc, ld, k + L.poff + L.np, hd));
       Blk<T> Sfull = cat(Q, Wb);
-      if ((rc = o.orth(Sfull, Dsrc, Dmid, Ddst))) return rc;
+      o.dbg("S before expansion", Sfull);
+      o.dbg("S_drop before orth", Dsrc);
+      if ((rc = o.orth(Sfull, Dsrc, Dmid, Ddst, debug_on()))) return rc;
+      o.dbg("S_drop after orth", Ddst);
       Blk<T> ADdst = cat(view<T>(ASc, ld, L.nnow, hd), view<T>(ASc, ld, k + L.poff + L.np, hd));
       if ((rc = o.spmm_blk(Ddst, ADdst))) return rc;
       L.nnow += hd;
@@ -581,6 +641,11 @@ int lobpcg_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* swit
       if ((rc = o.spmm(static_cast<T*>(Sn), ld, L.nnow, static_cast<T*>(ASn), ld))) return rc;
       if ((rc = o.spmm(static_cast<T*>(Sn) + k, ld, npn, static_cast<T*>(ASn) + k, ld))) return rc;
     }
+    if (debug_on()) {
+      o.dbg("new X", view<T>(Sn, ld, 0, L.nnow));
+      o.dbg("new P", view<T>(Sn, ld, k, npn));
+      o.dbg("C_P (as block)", view<T>(Sn, ld, k, npn));
+    }
     L.cur = nx;
     L.np = npn;
     L.poff = 0;
@@ -595,6 +660,7 @@ int lobpcg_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* swit
       L.nnow = nes;
       L.np = q;
       L.have_drop = true;
+      if (debug_on()) o.dbg("S_drop at shrink", view<T>(h->Sd, 2 * hd, 0, 2 * hd));
     }
   }
   return EIG_ENOTCONV;
@@ -715,8 +781,16 @@ int promote(eig_handle* h, LState& L, bool lobpcg) {
                  static_cast<dd*>(h->S[nx]) + k, ld, EIG_DF64, h->st));
   if (L.have_drop) {
     const int wd = lobpcg ? 2 * h->hdrop : h->hdrop;
+    if (debug_on()) {
+      Ops<Arith::F32, Arith::C32> o32(h);
+      o32.dbg("S_drop (float) before promotion", view<float>(h->Sd, wd, 0, wd));
+    }
     CK(convert2d(h->n, wd, h->Sd, wd, EIG_F32, h->Wt, wd, EIG_DF64, h->st));
     std::swap(h->Sd, h->Wt);
+    if (debug_on()) {
+      Ops<Arith::DF64, Arith::DF64> o64(h);
+      o64.dbg("S_drop (double-float) after promotion", view<dd>(h->Sd, wd, 0, wd));
+    }
   }
   L.poff = 0;
   if (!lobpcg) {
@@ -1029,8 +1103,11 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
   const int smax = 3 * k_max + 1;
   h->smax = smax;
   AL(h->Gp, sizeof(double) * size_t(smax) * smax);
-  AL(h->Rinv, sizeof(double) * size_t(h->wtw) * h->wtw);
-  AL(h->cholw, sizeof(double) * (size_t(h->wtw) * h->wtw + h->wtw));
+  // CholeskyQR widths: W (<= k_max), S_drop (2 (k_max - nes)) and, when the
+  // mixed form promotes, [X, P] (<= 2 k_max)
+  h->cqmax = std::max(h->wtw, 2 * k_max);
+  AL(h->Rinv, sizeof(double) * size_t(h->cqmax) * h->cqmax);
+  AL(h->cholw, sizeof(double) * (size_t(h->cqmax) * h->cqmax + h->cqmax));
   AL(h->Z, sizeof(double) * size_t(smax) * smax);
   AL(h->lamd, sizeof(double) * smax);
   AL(h->CP, sizeof(double) * size_t(smax) * k_max);
