@@ -1,0 +1,677 @@
+// Small dense symmetric eigensolver of the Rayleigh-Ritz step (arXiv:2409.05572,
+// Algorithms 1 and 3: "compute the spectral decomposition A_p = Z Lambda Z^H").
+//
+// GB300 executes scalar FP64 with very long latency (a Givens rotation of the
+// sequential QL chain costs about 1 us in float64), so the eigensolver is
+// split in two stages:
+//
+//  1. float32 decomposition: Householder tridiagonalisation (cooperative,
+//     grid-synchronised kernel, one warp per row of the trailing matrix),
+//     implicit QL with Wilkinson shifts on the tridiagonal (Bowdler, Martin,
+//     Reinsch and Wilkinson 1968) recording its Givens rotations, row-parallel
+//     accumulation of the rotations and a warp-per-vector back-transformation.
+//  2. refinement to float64 accuracy with the iteration of Ogita and Aishima
+//     (Japan J. Indust. Appl. Math. 35, 2018): with R = I - X^T X and
+//     S = X^T A X, lambda_i = S_ii / (1 - R_ii) and X <- X (I + E),
+//     E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i) for separated
+//     pairs, E_ij = R_ij / 2 inside clusters of nearly equal eigenvalues.  The
+//     products run in this library's double-float Gram / update kernels (all
+//     SMs, no sequential chain).  Clusters are finally diagonalised by a
+//     cyclic Jacobi iteration on their (small) block of X^T A X.
+//
+// The float64 QL path (stage 1 in float64, no refinement) is kept as
+// syev_qr64 for comparison and testing.
+#include <cooperative_groups.h>
+
+#include <cstdio>
+
+#include "blocks.cuh"
+#include "small.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace eig {
+
+template <typename R> struct RealT;
+template <> struct RealT<float> {
+  static __device__ __forceinline__ float eps() { return 1.1920928955078125e-07f; }
+  static __device__ __forceinline__ float rs(float x) { return rsqrtf(x); }
+  static __device__ __forceinline__ float hyp(float a, float b) { return hypotf(a, b); }
+  static constexpr float lo = 1e-35f, hi = 1e35f;
+};
+template <> struct RealT<double> {
+  static __device__ __forceinline__ double eps() { return 2.220446049250313e-16; }
+  static __device__ __forceinline__ double rs(double x) { return rsqrt(x); }
+  static __device__ __forceinline__ double hyp(double a, double b) { return hypot(a, b); }
+  static constexpr double lo = 1e-280, hi = 1e280;
+};
+
+template <typename R>
+__device__ __forceinline__ R block_sum(R v, R* red) {
+  // 256-thread block reduction; all threads get the result
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  R t = 0;
+  for (int i = 0; i < 8; ++i) t += red[i];
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// stage 1 kernels (templated on the working precision R)
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void copy_sym_kernel(int s, const double* __restrict__ A, int64_t lda, R* __restrict__ Wm) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(s) * s) return;
+  const int i = int(idx / s), j = int(idx % s);
+  Wm[idx] = R(0.5 * (A[int64_t(i) * lda + j] + A[int64_t(j) * lda + i]));
+}
+
+// Householder tridiagonalisation T = Q^T A Q, Q = H_0 ... H_{s-3},
+// H_k = I - tau_k v_k v_k^T (v_k in row k of Vh, entries k+1..s-1).
+template <typename R>
+__global__ void __launch_bounds__(256) sytrd_kernel(int s, R* __restrict__ Wm, R* __restrict__ Vh,
+                                                    R* __restrict__ tau, R* __restrict__ d, R* __restrict__ e,
+                                                    R* __restrict__ p) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ unsigned char shraw[];
+  R* vsh = reinterpret_cast<R*>(shraw);
+  R* psh = vsh + s;
+  __shared__ R red[8];
+  const int nb = gridDim.x, b = blockIdx.x, t = threadIdx.x;
+  const int warp = t >> 5, lane = t & 31;
+  const int gw = b * 8 + warp, nw = nb * 8;
+  for (int k = 0; k + 2 < s; ++k) {
+    const int m = s - k - 1;  // x = A[k+1:, k] = A[k, k+1:] (symmetric storage)
+    const R* rowk = Wm + int64_t(k) * s + (k + 1);
+    R part = 0, part_tail = 0;
+    for (int i = t; i < m; i += blockDim.x) {
+      const R x = rowk[i];
+      vsh[i] = x;
+      part += x * x;
+      if (i > 0) part_tail += x * x;
+    }
+    const R nrm2 = block_sum(part, red);
+    const R tail2 = block_sum(part_tail, red);
+    const R x0 = vsh[0];
+    R tk, alpha;
+    if (tail2 == R(0)) {
+      tk = 0;
+      alpha = x0;
+    } else {
+      const R nrm = sqrt(nrm2);
+      alpha = x0 >= R(0) ? -nrm : nrm;
+      const R v0 = x0 - alpha;
+      tk = R(2) / (tail2 + v0 * v0);
+      __syncthreads();
+      if (t == 0) vsh[0] = v0;
+    }
+    __syncthreads();
+    if (b == 0) {
+      for (int i = t; i < m; i += blockDim.x) Vh[int64_t(k) * s + k + 1 + i] = vsh[i];
+      if (t == 0) {
+        tau[k] = tk;
+        e[k] = alpha;
+        d[k] = Wm[int64_t(k) * s + k];
+      }
+    }
+    if (tk != R(0)) {
+      for (int i = gw; i < m; i += nw) {
+        const R* wr = Wm + int64_t(k + 1 + i) * s + (k + 1);
+        R acc = 0;
+        for (int j = lane; j < m; j += 32) acc += wr[j] * vsh[j];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) p[i] = tk * acc;
+      }
+    }
+    grid.sync();
+    if (tk != R(0)) {
+      R pv = 0;
+      for (int i = t; i < m; i += blockDim.x) {
+        const R pi = p[i];
+        psh[i] = pi;
+        pv += pi * vsh[i];
+      }
+      const R K = R(0.5) * tk * block_sum(pv, red);
+      for (int i = gw; i < m; i += nw) {
+        const R vi = vsh[i];
+        const R wi = psh[i] - K * vi;
+        R* wr = Wm + int64_t(k + 1 + i) * s + (k + 1);
+        for (int j = lane; j < m; j += 32) wr[j] -= vi * (psh[j] - K * vsh[j]) + wi * vsh[j];
+      }
+    }
+    grid.sync();
+  }
+  if (b == 0 && t == 0) {
+    if (s >= 2) {
+      d[s - 2] = Wm[int64_t(s - 2) * s + (s - 2)];
+      e[s - 2] = Wm[int64_t(s - 1) * s + (s - 2)];
+    }
+    d[s - 1] = Wm[int64_t(s - 1) * s + (s - 1)];
+    e[s - 1] = 0;
+  }
+}
+
+template <typename R>
+__global__ void small_tridiag_kernel(int s, const R* Wm, R* d, R* e, R* tau) {
+  if (threadIdx.x != 0) return;
+  d[0] = Wm[0];
+  e[0] = 0;
+  tau[0] = 0;
+  if (s == 2) {
+    d[1] = Wm[3];
+    e[0] = Wm[2];
+    e[1] = 0;
+    tau[1] = 0;
+  }
+}
+
+// Implicit QL with Wilkinson shifts on (d, e), e[i] = T[i+1][i], one thread,
+// d and e in shared memory.  Every Givens rotation applied to eigenvector
+// columns (i, i+1) is appended: z_i <- c z_i - s z_{i+1},
+// z_{i+1} <- s z_i + c z_{i+1}.
+template <typename R>
+__global__ void tql_kernel(int s, R* __restrict__ dg, R* __restrict__ eg, int* __restrict__ ri, R* __restrict__ rc,
+                           R* __restrict__ rs, int64_t cap, int64_t* nrot, int* status) {
+  extern __shared__ unsigned char shraw[];
+  R* d = reinterpret_cast<R*>(shraw);
+  R* e = d + s;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    d[i] = dg[i];
+    e[i] = eg[i];
+  }
+  __syncthreads();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const R eps = RealT<R>::eps();
+  int64_t cnt = 0;
+  int st = 0;
+  e[s - 1] = 0;
+  for (int l = 0; l < s && st == 0; ++l) {
+    int iter = 0;
+    for (;;) {
+      int m = l;
+      for (; m < s - 1; ++m) {
+        const R dd = fabs(d[m]) + fabs(d[m + 1]);
+        if (fabs(e[m]) <= eps * dd) break;
+      }
+      if (m == l) break;
+      if (++iter > 60) {
+        st = 1;
+        break;
+      }
+      R g = (d[l + 1] - d[l]) / (R(2) * e[l]);
+      R r = RealT<R>::hyp(g, R(1));
+      g = d[m] - d[l] + e[l] / (g + copysign(r, g));
+      R sn = 1, cs = 1, p = 0;
+      bool early = false;
+      for (int i = m - 1; i >= l; --i) {
+        const R f = sn * e[i];
+        const R bb = cs * e[i];
+        const R hh = f * f + g * g;
+        R rinv;
+        if (hh > RealT<R>::lo && hh < RealT<R>::hi) {
+          rinv = RealT<R>::rs(hh);
+          r = hh * rinv;
+        } else {
+          r = RealT<R>::hyp(f, g);
+          rinv = r != R(0) ? R(1) / r : R(0);
+        }
+        e[i + 1] = r;
+        if (r == R(0)) {
+          d[i + 1] -= p;
+          e[m] = 0;
+          early = true;
+          break;
+        }
+        sn = f * rinv;
+        cs = g * rinv;
+        g = d[i + 1] - p;
+        r = (d[i] - g) * sn + R(2) * cs * bb;
+        p = sn * r;
+        d[i + 1] = g + p;
+        g = cs * r - bb;
+        if (cnt < cap) {
+          ri[cnt] = i;
+          rc[cnt] = cs;
+          rs[cnt] = sn;
+        }
+        ++cnt;
+      }
+      if (early) continue;
+      d[l] -= p;
+      e[l] = g;
+      e[m] = 0;
+    }
+  }
+  if (cnt > cap) st = 2;
+  *nrot = cnt < cap ? cnt : cap;
+  *status = st;
+  for (int i = 0; i < s; ++i) {
+    dg[i] = d[i];
+    eg[i] = e[i];
+  }
+}
+
+// rank[c] = position of d[c] in ascending order (ties by index)
+template <typename R>
+__global__ void rank_kernel(int s, const R* __restrict__ d, int* __restrict__ rank, double* __restrict__ lam) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= s) return;
+  const R v = d[c];
+  int r = 0;
+  for (int k = 0; k < s; ++k) {
+    const R u = d[k];
+    r += (u < v) || (u == v && k < c);
+  }
+  rank[c] = r;
+  if (lam) lam[r] = double(v);
+}
+
+// Z_T = I G_1 G_2 ..., one thread per row, rows kept in shared memory as
+// [col][row]; the new z_i of a rotation chain is carried in a register.
+template <typename R>
+__global__ void rot_accum_kernel(int s, int rpb, const int* __restrict__ ri, const R* __restrict__ rc,
+                                 const R* __restrict__ rs, const int64_t* __restrict__ nrot, R* __restrict__ ZTc) {
+  extern __shared__ unsigned char shraw[];
+  R* zs = reinterpret_cast<R*>(shraw);  // s * rpb
+  const int r0 = blockIdx.x * rpb;
+  for (int idx = threadIdx.x; idx < s * rpb; idx += blockDim.x) {
+    const int c = idx / rpb, rr = idx % rpb;
+    zs[idx] = (r0 + rr == c) ? R(1) : R(0);
+  }
+  __syncthreads();
+  const int64_t nr = *nrot;
+  const int t = threadIdx.x;
+  if (t < rpb) {
+    int prev = -2;
+    R carry = 0;
+    for (int64_t q = 0; q < nr; ++q) {
+      const int i = __ldg(ri + q);
+      const R c = __ldg(rc + q), sn = __ldg(rs + q);
+      R b;
+      if (i + 1 == prev) {
+        b = carry;
+      } else {
+        if (prev >= 0) zs[prev * rpb + t] = carry;
+        b = zs[(i + 1) * rpb + t];
+      }
+      const R a = zs[i * rpb + t];
+      zs[(i + 1) * rpb + t] = sn * a + c * b;
+      carry = c * a - sn * b;
+      prev = i;
+    }
+    if (prev >= 0) zs[prev * rpb + t] = carry;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < s * rpb; idx += blockDim.x) {
+    const int c = idx / rpb, rr = idx % rpb;
+    const int row = r0 + rr;
+    if (row < s) ZTc[int64_t(c) * s + row] = zs[idx];
+  }
+}
+
+// Z(:, rank[j]) = H_0 ... H_{s-3} Z_T(:, j); one warp per vector.  Output in
+// float64 (Zd, leading dimension ldz).
+template <typename R>
+__global__ void __launch_bounds__(256) backtrans_kernel(int s, int wpb, const R* __restrict__ Vh,
+                                                        const R* __restrict__ tau, const R* __restrict__ ZTc,
+                                                        const int* __restrict__ rank, double* __restrict__ Zd,
+                                                        int64_t ldz) {
+  extern __shared__ unsigned char shraw[];
+  R* zw = reinterpret_cast<R*>(shraw);  // wpb warps x s
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * wpb + warp;
+  if (j >= s) return;
+  R* z = zw + int64_t(warp) * s;
+  for (int i = lane; i < s; i += 32) z[i] = ZTc[int64_t(j) * s + i];
+  __syncwarp();
+  for (int k = s - 3; k >= 0; --k) {
+    const R tk = tau[k];
+    if (tk == R(0)) continue;
+    const R* v = Vh + int64_t(k) * s;
+    R dot = 0;
+    for (int i = k + 1 + lane; i < s; i += 32) dot += v[i] * z[i];
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    const R f = tk * dot;
+    for (int i = k + 1 + lane; i < s; i += 32) z[i] -= f * v[i];
+    __syncwarp();
+  }
+  const int col = rank[j];
+  for (int i = lane; i < s; i += 32) Zd[int64_t(i) * ldz + col] = double(z[i]);
+}
+
+template <typename R>
+struct QLWork {
+  R *Wm, *Vh, *ZT, *tau, *d, *e, *p, *rc, *rs;
+  int *ri, *rank, *status;
+  int64_t* nrot;
+  int64_t cap;
+};
+
+struct Carver {
+  char* c;
+  explicit Carver(void* base) : c(static_cast<char*>(base)) {}
+  template <typename T>
+  T* take(size_t n) {
+    T* r = reinterpret_cast<T*>(c);
+    c += (n * sizeof(T) + 255) & ~size_t(255);
+    return r;
+  }
+};
+
+template <typename R>
+size_t ql_work_bytes(int s) {
+  const size_t ss = size_t(s) * s, cap = 8 * ss + 1024;
+  return 3 * (ss * sizeof(R) + 256) + 4 * (size_t(s) * sizeof(R) + 256) + 2 * (cap * sizeof(R) + 256) +
+         (cap * sizeof(int) + 256) + (size_t(s) * sizeof(int) + 256) + 512;
+}
+
+template <typename R>
+QLWork<R> ql_carve(int s, Carver& cv) {
+  QLWork<R> w;
+  const size_t ss = size_t(s) * s;
+  w.cap = int64_t(8 * ss + 1024);
+  w.Wm = cv.take<R>(ss);
+  w.Vh = cv.take<R>(ss);
+  w.ZT = cv.take<R>(ss);
+  w.tau = cv.take<R>(s);
+  w.d = cv.take<R>(s);
+  w.e = cv.take<R>(s);
+  w.p = cv.take<R>(s);
+  w.rc = cv.take<R>(w.cap);
+  w.rs = cv.take<R>(w.cap);
+  w.ri = cv.take<int>(w.cap);
+  w.rank = cv.take<int>(s);
+  w.status = cv.take<int>(4);
+  w.nrot = cv.take<int64_t>(2);
+  return w;
+}
+
+// Stage 1 in precision R: eigenvalues (ascending) into lam (if non-null) and
+// eigenvectors (float64, columns in ascending order) into Zd.
+template <typename R>
+cudaError_t ql_eig(int s, const double* A, int64_t lda, double* lam, double* Zd, int64_t ldz, QLWork<R>& w,
+                   int* status_dev, cudaStream_t st) {
+  const int64_t ss = int64_t(s) * s;
+  copy_sym_kernel<R><<<(unsigned)cdiv(ss, 256), 256, 0, st>>>(s, A, lda, w.Wm);
+  if (s >= 3) {
+    int nb = (s + 7) / 8;
+    if (nb > num_sms()) nb = num_sms();
+    const size_t shm = 2 * size_t(s) * sizeof(R);
+    cudaFuncSetAttribute(sytrd_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sytrd_kernel<R>, 256, shm);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int sv = s;
+    void* args[] = {&sv, &w.Wm, &w.Vh, &w.tau, &w.d, &w.e, &w.p};
+    cudaError_t err = cudaLaunchCooperativeKernel((void*)sytrd_kernel<R>, dim3(nb), dim3(256), args, shm, st);
+    if (err != cudaSuccess) return err;
+  } else {
+    small_tridiag_kernel<R><<<1, 32, 0, st>>>(s, w.Wm, w.d, w.e, w.tau);
+  }
+  cudaFuncSetAttribute(tql_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  tql_kernel<R><<<1, 32, 2 * size_t(s) * sizeof(R), st>>>(s, w.d, w.e, w.ri, w.rc, w.rs, w.cap, w.nrot,
+                                                          status_dev ? status_dev : w.status);
+  rank_kernel<R><<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.d, w.rank, lam);
+  int rpb = 32;
+  while (rpb > 1 && size_t(s) * rpb * sizeof(R) > 200 * 1024) rpb >>= 1;
+  cudaFuncSetAttribute(rot_accum_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+  cudaFuncSetAttribute(backtrans_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+  rot_accum_kernel<R><<<(unsigned)cdiv(s, rpb), 64, size_t(s) * rpb * sizeof(R), st>>>(s, rpb, w.ri, w.rc, w.rs,
+                                                                                       w.nrot, w.ZT);
+  int wpb = 8;
+  while (wpb > 1 && size_t(wpb) * s * sizeof(R) > 200 * 1024) --wpb;
+  backtrans_kernel<R><<<(unsigned)cdiv(s, wpb), 32 * wpb, size_t(wpb) * s * sizeof(R), st>>>(
+      s, wpb, w.Vh, w.tau, w.ZT, w.rank, Zd, ldz);
+  return cudaGetLastError();
+}
+
+size_t syev_qr64_work_bytes(int s) { return ql_work_bytes<double>(s); }
+
+cudaError_t syev_qr64(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
+                      int* status_dev, cudaStream_t st) {
+  if (s <= 0) return cudaSuccess;
+  Carver cv(work);
+  QLWork<double> w = ql_carve<double>(s, cv);
+  return ql_eig<double>(s, A, lda, lam, Z, ldz, w, status_dev, st);
+}
+
+// ---------------------------------------------------------------------------
+// stage 2: Ogita-Aishima refinement in double-float arithmetic
+// ---------------------------------------------------------------------------
+constexpr int OA_ITERS = 4;
+constexpr int MAX_CLUSTER = 48;  // two 48 x 48 float64 blocks fit in static shared memory
+
+// lambda_i = S_ii / G_ii (G = X^T X, so 1 - R_ii = G_ii)
+__global__ void oa_lambda_kernel(int s, const double* __restrict__ G, const double* __restrict__ S,
+                                 double* __restrict__ lam) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < s) lam[i] = S[int64_t(i) * s + i] / G[int64_t(i) * s + i];
+}
+
+// Clusters: consecutive lam (ascending up to the refinement's changes) whose
+// gaps are at most tau = tau_rel * max |lam|.  cid[i] = first index of i's
+// cluster.  One thread (s sequential comparisons).
+__global__ void cluster_kernel(int s, const double* __restrict__ lam, double tau_rel, int* __restrict__ cid,
+                               int* __restrict__ status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double mx = 0.0;
+  for (int i = 0; i < s; ++i) mx = fmax(mx, fabs(lam[i]));
+  const double tau = tau_rel * mx;
+  int start = 0, worst = 1;
+  cid[0] = 0;
+  for (int i = 1; i < s; ++i) {
+    if (fabs(lam[i] - lam[i - 1]) <= tau) {
+      cid[i] = start;
+    } else {
+      start = i;
+      cid[i] = i;
+    }
+    worst = max(worst, i - start + 1);
+  }
+  if (worst > MAX_CLUSTER) *status = 3;
+}
+
+// E = correction of the Ogita-Aishima step (float64, s x s row-major)
+__global__ void oa_e_kernel(int s, const double* __restrict__ G, const double* __restrict__ S,
+                            const double* __restrict__ lam, const int* __restrict__ cid, double* __restrict__ E) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(s) * s) return;
+  const int i = int(idx / s), j = int(idx % s);
+  const double Rij = (i == j ? 1.0 : 0.0) - G[idx];
+  if (cid[i] == cid[j]) {
+    E[idx] = 0.5 * Rij;
+  } else {
+    E[idx] = (S[idx] + lam[j] * Rij) / (lam[j] - lam[i]);
+  }
+}
+
+// Cyclic Jacobi on each cluster block of S (one warp per cluster): writes the
+// block rotation V_C into Q (s x s, identity elsewhere) and the block's
+// eigenvalues into lam.
+__global__ void cluster_jacobi_kernel(int s, const double* __restrict__ S, const int* __restrict__ cid,
+                                      double* __restrict__ Q, double* __restrict__ lam) {
+  __shared__ double a[MAX_CLUSTER * MAX_CLUSTER];
+  __shared__ double v[MAX_CLUSTER * MAX_CLUSTER];
+  __shared__ double cs[2];
+  const int start = blockIdx.x;
+  if (start >= s || cid[start] != start) return;
+  int m = 1;
+  while (start + m < s && cid[start + m] == start) ++m;
+  if (m == 1 || m > MAX_CLUSTER) return;
+  const int lane = threadIdx.x;
+  for (int idx = lane; idx < m * m; idx += 32) {
+    const int i = idx / m, j = idx % m;
+    a[idx] = 0.5 * (S[int64_t(start + i) * s + start + j] + S[int64_t(start + j) * s + start + i]);
+    v[idx] = i == j ? 1.0 : 0.0;
+  }
+  __syncwarp();
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, nrm = 0.0;
+    for (int idx = lane; idx < m * m; idx += 32) {
+      const int i = idx / m, j = idx % m;
+      nrm += a[idx] * a[idx];
+      if (i != j) off += a[idx] * a[idx];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    }
+    if (off <= 1e-32 * nrm || off == 0.0) break;
+    for (int p = 0; p < m - 1; ++p) {
+      for (int q = p + 1; q < m; ++q) {
+        if (lane == 0) {
+          const double apq = a[p * m + q];
+          double c = 1.0, sn = 0.0;
+          if (fabs(apq) > 1e-300) {
+            const double theta = (a[q * m + q] - a[p * m + p]) / (2.0 * apq);
+            const double t = copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            sn = t * c;
+          }
+          cs[0] = c;
+          cs[1] = sn;
+        }
+        __syncwarp();
+        const double c = cs[0], sn = cs[1];
+        if (sn != 0.0) {
+          // columns p, q of a and v
+          for (int r = lane; r < m; r += 32) {
+            const double ap = a[r * m + p], aq = a[r * m + q];
+            a[r * m + p] = c * ap - sn * aq;
+            a[r * m + q] = sn * ap + c * aq;
+            const double vp = v[r * m + p], vq = v[r * m + q];
+            v[r * m + p] = c * vp - sn * vq;
+            v[r * m + q] = sn * vp + c * vq;
+          }
+          __syncwarp();
+          // rows p, q of a
+          for (int r = lane; r < m; r += 32) {
+            const double ap = a[p * m + r], aq = a[q * m + r];
+            a[p * m + r] = c * ap - sn * aq;
+            a[q * m + r] = sn * ap + c * aq;
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  for (int idx = lane; idx < m * m; idx += 32) {
+    const int i = idx / m, j = idx % m;
+    Q[int64_t(start + i) * s + start + j] = v[idx];
+  }
+  for (int i = lane; i < m; i += 32) lam[start + i] = a[i * m + i];
+}
+
+__global__ void eye_kernel(int s, double* __restrict__ Q) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx < int64_t(s) * s) Q[idx] = (idx / s == idx % s) ? 1.0 : 0.0;
+}
+
+// Z(:, rank[j]) = X(:, j), lam_out[rank[j]] = lam[j]
+__global__ void permute_kernel(int s, const dd* __restrict__ X, const int* __restrict__ rank,
+                               const double* __restrict__ lam, double* __restrict__ Z, int64_t ldz,
+                               double* __restrict__ lam_out) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(s) * s) return;
+  const int i = int(idx / s), j = int(idx % s);
+  const dd x = X[idx];
+  Z[int64_t(i) * ldz + rank[j]] = (double)x.hi + (double)x.lo;
+  if (i == 0) lam_out[rank[j]] = lam[j];
+}
+
+struct RefWork {
+  QLWork<float> ql;
+  double *Zd, *G, *S, *E, *Q, *lam, *scr;
+  dd *Add, *X, *X2, *AX, *Cs;
+  int* cid;
+  int* rank;
+};
+
+static size_t ref_bytes(int s) {
+  const size_t ss = size_t(s) * s;
+  const size_t scr = gram_scratch_elems(s, s, s, true);
+  return ql_work_bytes<float>(s) + 5 * (ss * 8 + 256) + (size_t(s) * 8 + 256) + (scr * 8 + 256) +
+         5 * (ss * sizeof(dd) + 256) + 2 * (size_t(s) * 4 + 256) + 1024;
+}
+
+size_t syev_work_bytes(int s) { return ref_bytes(s); }
+
+static RefWork ref_carve(int s, void* base) {
+  Carver cv(base);
+  RefWork w;
+  w.ql = ql_carve<float>(s, cv);
+  const size_t ss = size_t(s) * s;
+  w.Zd = cv.take<double>(ss);
+  w.G = cv.take<double>(ss);
+  w.S = cv.take<double>(ss);
+  w.E = cv.take<double>(ss);
+  w.Q = cv.take<double>(ss);
+  w.lam = cv.take<double>(s);
+  w.scr = cv.take<double>(gram_scratch_elems(s, s, s, true));
+  w.Add = cv.take<dd>(ss);
+  w.X = cv.take<dd>(ss);
+  w.X2 = cv.take<dd>(ss);
+  w.AX = cv.take<dd>(ss);
+  w.Cs = cv.take<dd>(ss);
+  w.cid = cv.take<int>(s);
+  w.rank = cv.take<int>(s);
+  return w;
+}
+
+static Blk<dd> sq(dd* p, int s) {
+  Blk<dd> b;
+  b.add(p, s, s);
+  return b;
+}
+
+// G = X^T X, AX = A X, S = X^T A X for the current X (double-float)
+static cudaError_t oa_products(int s, RefWork& w, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = gram<Arith::DF64>(s, sq(w.X, s), sq(w.X, s), true, w.G, s, w.scr, st))) return e;
+  if ((e = convert2d(s, s, w.X, s, EIG_DF64, w.Zd, s, EIG_F64, st))) return e;
+  if ((e = stage_coef<Arith::DF64>(s, s, w.Zd, s, w.Cs, s, 1.0, st))) return e;
+  if ((e = update<Arith::DF64>(s, sq(w.Add, s), w.Cs, s, sq(w.AX, s), 0.0, st))) return e;
+  return gram<Arith::DF64>(s, sq(w.X, s), sq(w.AX, s), true, w.S, s, w.scr, st);
+}
+
+cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
+                 int* status_dev, cudaStream_t st) {
+  if (s <= 0) return cudaSuccess;
+  RefWork w = ref_carve(s, work);
+  const int64_t ss = int64_t(s) * s;
+  const unsigned gb = (unsigned)cdiv(ss, 256);
+  cudaError_t e;
+  // stage 1: float32 decomposition (eigenvectors sorted ascending into Zd)
+  if ((e = ql_eig<float>(s, A, lda, nullptr, w.Zd, s, w.ql, status_dev, st))) return e;
+  if ((e = convert2d(s, s, w.Zd, s, EIG_F64, w.X, s, EIG_DF64, st))) return e;
+  if ((e = convert2d(s, s, A, lda, EIG_F64, w.Add, s, EIG_DF64, st))) return e;
+  // stage 2: Ogita-Aishima refinement
+  const double tau_rel = 3e-6;
+  for (int it = 0; it < OA_ITERS; ++it) {
+    if ((e = oa_products(s, w, st))) return e;
+    oa_lambda_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.G, w.S, w.lam);
+    if (it == 0) cluster_kernel<<<1, 32, 0, st>>>(s, w.lam, tau_rel, w.cid, status_dev ? status_dev : w.ql.status);
+    oa_e_kernel<<<gb, 256, 0, st>>>(s, w.G, w.S, w.lam, w.cid, w.E);
+    // X2 = X + X E
+    if ((e = cudaMemcpyAsync(w.X2, w.X, sizeof(dd) * ss, cudaMemcpyDeviceToDevice, st))) return e;
+    if ((e = stage_coef<Arith::DF64>(s, s, w.E, s, w.Cs, s, 1.0, st))) return e;
+    if ((e = update<Arith::DF64>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 1.0, st))) return e;
+    std::swap(w.X, w.X2);
+  }
+  // final: eigenvalues, cluster diagonalisation, ascending order
+  if ((e = oa_products(s, w, st))) return e;
+  oa_lambda_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.G, w.S, w.lam);
+  eye_kernel<<<gb, 256, 0, st>>>(s, w.Q);
+  cluster_jacobi_kernel<<<s, 32, 0, st>>>(s, w.S, w.cid, w.Q, w.lam);
+  if ((e = stage_coef<Arith::DF64>(s, s, w.Q, s, w.Cs, s, 1.0, st))) return e;
+  if ((e = update<Arith::DF64>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 0.0, st))) return e;
+  rank_kernel<double><<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.lam, w.rank, nullptr);
+  permute_kernel<<<gb, 256, 0, st>>>(s, w.X2, w.rank, w.lam, Z, ldz, lam);
+  return cudaGetLastError();
+}
+
+}  // namespace eig

@@ -12,11 +12,18 @@ cudaError_t chol_rinv(int w, int64_t nrows, const double* G, int64_t ldg, double
                       int* status, cudaStream_t st, const int* gate = nullptr,
                       double unit_round = 1.1102230246251565e-16);
 
-// A = Z diag(lam) Z^T, lam ascending; work of syev_work_bytes(s) bytes;
-// *status_dev: 0 ok, 1 QL did not converge, 2 rotation list overflow.
+// A = Z diag(lam) Z^T, lam ascending, Z float64 (leading dimension ldz):
+// float32 Householder + implicit QL, then Ogita-Aishima refinement in
+// double-float and Jacobi on clusters (k_syev.cu).  work of syev_work_bytes(s)
+// bytes; *status_dev: 0 ok, 1 QL did not converge, 2 rotation list overflow,
+// 3 a cluster of nearly equal eigenvalues is larger than the Jacobi stage takes.
 size_t syev_work_bytes(int s);
 cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
                  int* status_dev, cudaStream_t st);
+// The same decomposition entirely in float64 (QL path, no refinement).
+size_t syev_qr64_work_bytes(int s);
+cudaError_t syev_qr64(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
+                      int* status_dev, cudaStream_t st);
 
 // improved Hetmaniuk-Lehoucq: CP = Z(:, nnow:s) Q, Q from Householder QR of
 // Z(nlock:nnow, nnow:s)^T; work of hl_work_bytes() bytes.

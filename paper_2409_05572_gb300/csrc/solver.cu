@@ -179,6 +179,16 @@ namespace {
 
 constexpr int F_CHOL1 = 0, F_CHOL2 = 1, F_CHOL3 = 2, F_SYEV = 4, NFLAGS = 8;
 
+// EIG_SYEV=qr64 selects the all-float64 QL eigensolver (comparison path)
+bool use_qr64() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("EIG_SYEV");
+    v = (e && std::strcmp(e, "qr64") == 0) ? 1 : 0;
+  }
+  return v == 1;
+}
+
 bool debug_on() {
   static int v = -1;
   if (v < 0) {
@@ -413,7 +423,10 @@ struct Ops {
     if (rc) return rc;
     const double sw = S.width;
     Prof p(h, EIG_K_SYEV, (4.0 / 3.0 + 6.0) * sw * sw * sw, 0.0);
-    CK(syev(S.width, h->Gp, S.width, h->lamd, h->Z, S.width, h->syevw, h->flags + F_SYEV, st()));
+    if (use_qr64())
+      CK(syev_qr64(S.width, h->Gp, S.width, h->lamd, h->Z, S.width, h->syevw, h->flags + F_SYEV, st()));
+    else
+      CK(syev(S.width, h->Gp, S.width, h->lamd, h->Z, S.width, h->syevw, h->flags + F_SYEV, st()));
     return EIG_OK;
   }
   int hl(int s, int nnow, int nlock, int npn) {
@@ -1117,7 +1130,7 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
   AL(h->xn, sizeof(double) * smax);
   AL(h->rn, sizeof(double) * smax);
   AL(h->Cs, sizeof(double) * size_t(smax) * (2 * k_max + 1));
-  AL(h->syevw, syev_work_bytes(smax));
+  AL(h->syevw, std::max(syev_work_bytes(smax), syev_qr64_work_bytes(smax)));
   AL(h->hlw, hl_work_bytes(smax, k_max, 0) + sizeof(double) * size_t(smax) * smax);
   AL(h->flags, sizeof(int) * NFLAGS);
   AL(h->V, sizeof(double) * size_t(n) * nev);
