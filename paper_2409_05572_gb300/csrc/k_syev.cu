@@ -24,6 +24,7 @@
 #include <cooperative_groups.h>
 
 #include <cstdio>
+#include <cstdlib>
 
 #include "blocks.cuh"
 #include "small.cuh"
@@ -35,13 +36,11 @@ namespace eig {
 template <typename R> struct RealT;
 template <> struct RealT<float> {
   static __device__ __forceinline__ float eps() { return 1.1920928955078125e-07f; }
-  static __device__ __forceinline__ float rs(float x) { return rsqrtf(x); }
   static __device__ __forceinline__ float hyp(float a, float b) { return hypotf(a, b); }
   static constexpr float lo = 1e-35f, hi = 1e35f;
 };
 template <> struct RealT<double> {
   static __device__ __forceinline__ double eps() { return 2.220446049250313e-16; }
-  static __device__ __forceinline__ double rs(double x) { return rsqrt(x); }
   static __device__ __forceinline__ double hyp(double a, double b) { return hypot(a, b); }
   static constexpr double lo = 1e-280, hi = 1e280;
 };
@@ -210,15 +209,14 @@ __global__ void tql_kernel(int s, R* __restrict__ dg, R* __restrict__ eg, int* _
       for (int i = m - 1; i >= l; --i) {
         const R f = sn * e[i];
         const R bb = cs * e[i];
+        // correctly rounded square root and divisions keep c^2 + s^2 = 1 to
+        // one ulp; an approximate reciprocal square root biases every
+        // rotation and the eigenvectors lose orthogonality over the chain
         const R hh = f * f + g * g;
-        R rinv;
-        if (hh > RealT<R>::lo && hh < RealT<R>::hi) {
-          rinv = RealT<R>::rs(hh);
-          r = hh * rinv;
-        } else {
+        if (hh > RealT<R>::lo && hh < RealT<R>::hi)
+          r = sqrt(hh);
+        else
           r = RealT<R>::hyp(f, g);
-          rinv = r != R(0) ? R(1) / r : R(0);
-        }
         e[i + 1] = r;
         if (r == R(0)) {
           d[i + 1] -= p;
@@ -226,8 +224,8 @@ __global__ void tql_kernel(int s, R* __restrict__ dg, R* __restrict__ eg, int* _
           early = true;
           break;
         }
-        sn = f * rinv;
-        cs = g * rinv;
+        sn = f / r;
+        cs = g / r;
         g = d[i + 1] - p;
         r = (d[i] - g) * sn + R(2) * cs * bb;
         p = sn * r;
@@ -442,7 +440,7 @@ cudaError_t syev_qr64(int s, const double* A, int64_t lda, double* lam, double* 
 // ---------------------------------------------------------------------------
 // stage 2: Ogita-Aishima refinement in double-float arithmetic
 // ---------------------------------------------------------------------------
-constexpr int OA_ITERS = 4;
+constexpr int OA_ITERS = 5;
 constexpr int MAX_CLUSTER = 48;  // two 48 x 48 float64 blocks fit in static shared memory
 
 // lambda_i = S_ii / G_ii (G = X^T X, so 1 - R_ii = G_ii)
@@ -649,12 +647,28 @@ cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, in
   if ((e = ql_eig<float>(s, A, lda, nullptr, w.Zd, s, w.ql, status_dev, st))) return e;
   if ((e = convert2d(s, s, w.Zd, s, EIG_F64, w.X, s, EIG_DF64, st))) return e;
   if ((e = convert2d(s, s, A, lda, EIG_F64, w.Add, s, EIG_DF64, st))) return e;
-  // stage 2: Ogita-Aishima refinement
+  // stage 2: Ogita-Aishima refinement.  Inside a cluster the columns of X
+  // only span an approximate invariant subspace, so before each correction
+  // the cluster blocks of X^T A X are diagonalised (Jacobi) and X rotated:
+  // otherwise the off-cluster corrections use Rayleigh quotients that are not
+  // eigenvalue estimates and the cluster subspace stops converging.
   const double tau_rel = 3e-6;
-  for (int it = 0; it < OA_ITERS; ++it) {
+  static int n_iters = -1;
+  if (n_iters < 0) {
+    const char* ev = std::getenv("EIG_OA_ITERS");  // debugging override
+    n_iters = ev ? std::atoi(ev) : OA_ITERS;
+  }
+  for (int it = 0; it < n_iters; ++it) {
     if ((e = oa_products(s, w, st))) return e;
     oa_lambda_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.G, w.S, w.lam);
     if (it == 0) cluster_kernel<<<1, 32, 0, st>>>(s, w.lam, tau_rel, w.cid, status_dev ? status_dev : w.ql.status);
+    eye_kernel<<<gb, 256, 0, st>>>(s, w.Q);
+    cluster_jacobi_kernel<<<s, 32, 0, st>>>(s, w.S, w.cid, w.Q, w.lam);
+    if ((e = stage_coef<Arith::DF64>(s, s, w.Q, s, w.Cs, s, 1.0, st))) return e;
+    if ((e = update<Arith::DF64>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 0.0, st))) return e;
+    std::swap(w.X, w.X2);
+    if ((e = oa_products(s, w, st))) return e;
+    oa_lambda_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.G, w.S, w.lam);
     oa_e_kernel<<<gb, 256, 0, st>>>(s, w.G, w.S, w.lam, w.cid, w.E);
     // X2 = X + X E
     if ((e = cudaMemcpyAsync(w.X2, w.X, sizeof(dd) * ss, cudaMemcpyDeviceToDevice, st))) return e;

@@ -189,14 +189,15 @@ bool use_qr64() {
   return v == 1;
 }
 
-bool debug_on() {
+int debug_level() {
   static int v = -1;
   if (v < 0) {
     const char* e = std::getenv("EIG_DEBUG");
-    v = (e && e[0] == '1') ? 1 : 0;
+    v = (e && e[0] >= '1' && e[0] <= '9') ? e[0] - '0' : 0;
   }
-  return v == 1;
+  return v;
 }
+bool debug_on() { return debug_level() >= 1; }
 
 // CUDA-event bracket of one kernel class when profiling is on
 cudaEvent_t ev_get(eig_handle* h) {
@@ -332,6 +333,48 @@ struct Ops {
   double spmm_bytes(int w, int terms) const {
     return (4.0 + E) * double(h->nnz) + 4.0 * double(h->n + 1) + E * double(h->n) * w * (1 + terms);
   }
+  // debug (EIG_DEBUG=2): eigenvalues of the same projected matrix by the
+  // float64 QL path, compared with the refined eigensolver's
+  void compare_syev(int s) {
+    std::vector<double> ap(size_t(s) * s), l1(s), l2(s);
+    cudaMemcpyAsync(ap.data(), h->Gp, sizeof(double) * ap.size(), cudaMemcpyDeviceToHost, st());
+    cudaMemcpyAsync(l1.data(), h->lamd, sizeof(double) * s, cudaMemcpyDeviceToHost, st());
+    double *dA = nullptr, *dl = nullptr, *dZ = nullptr;
+    void* wk = nullptr;
+    int* fl = nullptr;
+    cudaMalloc(&dA, sizeof(double) * ap.size());
+    cudaMalloc(&dl, sizeof(double) * s);
+    cudaMalloc(&dZ, sizeof(double) * ap.size());
+    cudaMalloc(&wk, syev_qr64_work_bytes(s));
+    cudaMalloc(&fl, 16);
+    cudaMemcpyAsync(dA, h->Gp, sizeof(double) * ap.size(), cudaMemcpyDeviceToDevice, st());
+    syev_qr64(s, dA, s, dl, dZ, s, wk, fl, st());
+    cudaMemcpyAsync(l2.data(), dl, sizeof(double) * s, cudaMemcpyDeviceToHost, st());
+    cudaStreamSynchronize(st());
+    double nrm = 0.0, worst = 0.0;
+    int wi = 0;
+    for (int i = 0; i < s; ++i) nrm = std::max(nrm, std::fabs(l2[i]));
+    for (int i = 0; i < s; ++i)
+      if (std::fabs(l1[i] - l2[i]) > worst) {
+        worst = std::fabs(l1[i] - l2[i]);
+        wi = i;
+      }
+    std::fprintf(stderr, "[eig]   syev check s=%d: max |dlam|/|A_p| = %.2e at %d (lam %.12f vs %.12f)\n", s,
+                 worst / nrm, wi, l1[wi], l2[wi]);
+    if (worst / nrm > 1e-11 && std::getenv("EIG_DUMP_AP")) {
+      FILE* f = std::fopen(std::getenv("EIG_DUMP_AP"), "wb");
+      if (f) {
+        std::fwrite(&s, sizeof(int), 1, f);
+        std::fwrite(ap.data(), sizeof(double), ap.size(), f);
+        std::fclose(f);
+      }
+    }
+    cudaFree(dA);
+    cudaFree(dl);
+    cudaFree(dZ);
+    cudaFree(wk);
+    cudaFree(fl);
+  }
   // debug: min / max column norm of a block (EIG_DEBUG=1 only)
   void dbg(const char* label, const Blk<T>& B) {
     if (!debug_on() || B.width == 0) return;
@@ -427,6 +470,7 @@ struct Ops {
       CK(syev_qr64(S.width, h->Gp, S.width, h->lamd, h->Z, S.width, h->syevw, h->flags + F_SYEV, st()));
     else
       CK(syev(S.width, h->Gp, S.width, h->lamd, h->Z, S.width, h->syevw, h->flags + F_SYEV, st()));
+    if (debug_level() >= 2) compare_syev(S.width);
     return EIG_OK;
   }
   int hl(int s, int nnow, int nlock, int npn) {
