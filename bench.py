@@ -218,7 +218,9 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the fixed-block comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--ref-iters", type=int, default=150,
+    ap.add_argument("--max-iter", type=int, default=1000,
+                    help="iteration cap per solve (profiling runs use a small cap)")
+    ap.add_argument("--ref-iters", type=int, default=322,
                     help="iterations per solve used to scale the reference arm's per-iteration time")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -247,7 +249,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     # stopping test of Eq. conv at tol/2 so that ||Av - lv|| / ||A|| <= tol holds
     solver = L.Solver((rp, ci, va), nev=nev, k_max=k, strategy=args.strategy, X0=X0d, normA=normA,
-                      tol=0.5 * tol, form=args.form, stream=stream, profile=1)
+                      tol=0.5 * tol, form=args.form, stream=stream, profile=1, max_iter=args.max_iter)
 
     def barrier():
         if dist is not None:
