@@ -39,9 +39,10 @@ from paper_2409_05572_gb300 import workloads as W  # noqa: E402
 METRIC = "converged eigenpairs/s at 1e-8 residual vs fixed-block FP64; p50/p99 latency"
 UNIT = "eigenpairs/s"
 
-# kernels launched per library call of each kernel class (for gpu_launches)
-LAUNCHES_PER_CALL = {"spmm": 1, "gram": 2, "update": 1, "residual": 2, "chol": 1, "syev": 6, "hl": 2,
-                     "other": 1}
+# DRAM traffic / algorithmic bytes of one launch, from the ncu captures of
+# the small cases (profiles/gram_kernel_df64_n262144_384x384_sym.md and
+# profiles/update_kernel_df64_n262144_384x256.md); traffic grows with n.
+TRAFFIC_RATIO = {"gram": 1.387 / 0.805, "update": 1.447 / 1.342}
 
 
 def peaks():
@@ -302,8 +303,7 @@ def main():
     # per-kernel-class time shares and the roofline of the dominant kernel
     tot_ms = sum(v["ms"] for v in kst.values())
     line["kernel_share"] = {c: round(v["ms"] / tot_ms, 4) for c, v in kst.items() if v["launches"]}
-    line["gpu_launches"] = int(sum(LAUNCHES_PER_CALL[c] * v["launches"] for c, v in kst.items())
-                               / args.steps)
+    line["gpu_launches"] = int(sum(r["launches"] for r in results) / args.steps)
     hbm, _, src = peaks()
     dom = max(kst, key=lambda c: kst[c]["ms"])
     v = kst[dom]
@@ -320,7 +320,14 @@ def main():
                                "11.1 FP32 instructions per double-float multiply-add x 2"
                 if args.form != "f64" else "measured native FP64 FMA rate"}
     roof["avg_launch_ms"] = v["ms"] / max(v["launches"], 1)
-    roof["traffic"] = None
+    if dom in TRAFFIC_RATIO and args.form == "df64":
+        # per launch, like achieved: algorithmic bytes of the class's average
+        # launch x the DRAM/algorithmic ratio of the ncu capture
+        roof["traffic"] = TRAFFIC_RATIO[dom] * v["bytes"] / max(v["launches"], 1)
+        roof["traffic_source"] = (f"ncu dram__bytes_read+write of {dom}_kernel<DF64> at n=262144 "
+                                  f"(ratio {TRAFFIC_RATIO[dom]:.2f} to algorithmic bytes), scaled")
+    else:
+        roof["traffic"] = None
     line["roofline"] = roof
     sp = kst.get("spmm")
     if sp and sp["launches"]:

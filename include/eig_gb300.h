@@ -223,6 +223,7 @@ typedef struct {
    * Flops count 2 per multiply-add in the arithmetic of the form; bytes
    * count each n-sized operand read once and each result written once. */
   const double *kstats;
+  int64_t launches;      /* kernels this library launched during the solve     */
 } eig_result;
 
 typedef struct eig_handle eig_handle;

@@ -53,7 +53,8 @@ class eig_result(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("n_shrink", C.c_int), ("n_expand", C.c_int),
                 ("nev", C.c_int), ("lambda_", C.POINTER(C.c_double)), ("resid", C.POINTER(C.c_double)),
                 ("V", C.c_void_p), ("history", C.POINTER(C.c_double)), ("widths", C.POINTER(C.c_int)),
-                ("time_ms", C.c_double), ("normA", C.c_double), ("kstats", C.POINTER(C.c_double))]
+                ("time_ms", C.c_double), ("normA", C.c_double), ("kstats", C.POINTER(C.c_double)),
+                ("launches", C.c_int64)]
 
 KCLASSES = ("spmm", "gram", "update", "residual", "chol", "syev", "hl", "other")
 
@@ -280,7 +281,7 @@ class Solver:
             "history": np.ctypeslib.as_array(r.history, (it,)).copy() if r.history and it else np.zeros(0),
             "widths": (np.ctypeslib.as_array(r.widths, (max(it - (1 if r.status == EIG_OK else 0), 0),)).copy()
                        if r.widths else np.zeros(0, dtype=np.int32)),
-            "time_ms": r.time_ms, "V_ptr": r.V,
+            "time_ms": r.time_ms, "V_ptr": r.V, "launches": int(r.launches),
         }
         if r.kstats:
             ks = np.ctypeslib.as_array(r.kstats, (len(KCLASSES), 4)).copy()

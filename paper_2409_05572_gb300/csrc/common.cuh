@@ -164,4 +164,9 @@ inline int num_sms() {
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Host-side count of this library's kernel launches (all threads, all
+// devices); eig_solve reports the difference over a solve.
+void count_launches(int n);
+int64_t launches_total();
+
 }  // namespace eig

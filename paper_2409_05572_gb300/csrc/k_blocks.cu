@@ -7,11 +7,16 @@
 // In the double-float (DF64) form no FP64 instruction executes inside an
 // n-sized loop: blocks are stored as {hi, lo} float pairs and every product
 // is an FP32 TwoProd plus cross terms.
+#include <atomic>
 #include <cstdio>
 
 #include "blocks.cuh"
 
 namespace eig {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------
 // small helpers
@@ -199,7 +204,7 @@ static void launch_spmm(const Csr<A>& M, int w, const typename Pol<A>::T* V, int
   if (blocks < 1) blocks = 1;
   spmm_kernel<A, VEC, G, MAXT><<<(unsigned)blocks, threads, 0, st>>>(
       M.n, M.rowptr, M.colind, M.val, w, V, ldv, Y, ldy, host_coef<A>(alpha), alpha != 1.0,
-      host_coef<A>(beta), beta != 0.0, U, ldu, host_coef<A>(gamma), gamma != 0.0);
+      host_coef<A>(beta), beta != 0.0, U, ldu, host_coef<A>(gamma), gamma != 0.0); count_launches(1);
 }
 
 template <Arith A, int VEC>
@@ -385,9 +390,9 @@ cudaError_t gram(int64_t n, const Blk<typename Pol<A>::T>& U, const Blk<typename
   int64_t rps = cdiv(n, ns);
   rps = cdiv(rps, GK) * GK;
   dim3 grid((b + GT - 1) / GT, (a + GT - 1) / GT, ns);
-  gram_kernel<A><<<grid, 256, 0, st>>>(n, U, V, sym, rps, scratch, gate);
+  gram_kernel<A><<<grid, 256, 0, st>>>(n, U, V, sym, rps, scratch, gate); count_launches(1);
   const int64_t tot = int64_t(a) * b;
-  gram_reduce_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(a, b, ns, sym, scratch, G, ldg, gate);
+  gram_reduce_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(a, b, ns, sym, scratch, G, ldg, gate); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -408,9 +413,9 @@ cudaError_t gram_capped(int64_t n, const Blk<typename Pol<A>::T>& U, const Blk<t
   int64_t rps = cdiv(n, ns);
   rps = cdiv(rps, GK) * GK;
   dim3 grid((b + GT - 1) / GT, (a + GT - 1) / GT, ns);
-  gram_kernel<A><<<grid, 256, 0, st>>>(n, U, V, sym, rps, scratch, nullptr);
+  gram_kernel<A><<<grid, 256, 0, st>>>(n, U, V, sym, rps, scratch, nullptr); count_launches(1);
   const int64_t tot = int64_t(a) * b;
-  gram_reduce_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(a, b, ns, sym, scratch, G, ldg, nullptr);
+  gram_reduce_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(a, b, ns, sym, scratch, G, ldg, nullptr); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -516,7 +521,7 @@ cudaError_t stage_coef(int s, int c, const double* C, int64_t ldc, typename Pol<
                        int64_t ldo, double scale, cudaStream_t st, const int* gate) {
   const int64_t tot = int64_t(s) * c;
   if (tot <= 0) return cudaSuccess;
-  stage_coef_kernel<A><<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(s, c, C, ldc, Cs, ldo, scale, gate);
+  stage_coef_kernel<A><<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(s, c, C, ldc, Cs, ldo, scale, gate); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -548,7 +553,7 @@ cudaError_t axpby(int64_t n, int w, const typename Pol<A>::T* U, int64_t ldu, do
   const int64_t cap = int64_t(num_sms()) * 16;
   if (blocks > cap) blocks = cap;
   axpby_kernel<A><<<(unsigned)blocks, 256, 0, st>>>(n, w, U, ldu, host_coef<A>(a), V, ldv,
-                                                    host_coef<A>(b), Y, ldy);
+                                                    host_coef<A>(b), Y, ldy); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -573,7 +578,7 @@ cudaError_t copy_blk(int64_t n, const Blk<T>& src, const Blk<T>& dst, cudaStream
   int64_t blocks = cdiv(tot, 256);
   const int64_t cap = int64_t(num_sms()) * 16;
   if (blocks > cap) blocks = cap;
-  copy_blk_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(n, src, dst, gate);
+  copy_blk_kernel<T><<<(unsigned)blocks, 256, 0, st>>>(n, src, dst, gate); count_launches(1);
   return cudaGetLastError();
 }
 template cudaError_t copy_blk<double>(int64_t, const Blk<double>&, const Blk<double>&, cudaStream_t, const int*);
@@ -586,7 +591,7 @@ cudaError_t update(int64_t n, const Blk<typename Pol<A>::T>& U, const typename P
                    const int* gate) {
   if (n <= 0 || c <= 0) return cudaSuccess;
   dim3 grid((c + GT - 1) / GT, (unsigned)cdiv(n, GT));
-  update_kernel<A><<<grid, 256, 0, st>>>(n, U, Cs, c, Y, host_coef<A>(beta), beta != 0.0, gate);
+  update_kernel<A><<<grid, 256, 0, st>>>(n, U, Cs, c, Y, host_coef<A>(beta), beta != 0.0, gate); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -683,8 +688,8 @@ cudaError_t residual(int64_t n, int w, const typename Pol<A>::T* X, int64_t ldx,
   const int nb = residual_blocks(n);
   const int64_t rpb = cdiv(n, nb);
   residual_kernel<A><<<nb, dim3(32, RES_ROWS), 0, st>>>(n, w, X, ldx, AX, ldax, lam, tdiag, R, ldr,
-                                                        rpb, scratch);
-  residual_reduce_kernel<<<(w + 127) / 128, 128, 0, st>>>(w, nb, scratch, xnorm2, rnorm2);
+                                                        rpb, scratch); count_launches(1);
+  residual_reduce_kernel<<<(w + 127) / 128, 128, 0, st>>>(w, nb, scratch, xnorm2, rnorm2); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -723,7 +728,7 @@ cudaError_t convert2d(int64_t rows, int64_t cols, const void* src, int64_t lds, 
   int64_t blocks = cdiv(tot, 256);
   const int64_t cap = int64_t(num_sms()) * 32;
   if (blocks > cap) blocks = cap;
-  convert2d_kernel<<<(unsigned)blocks, 256, 0, st>>>(rows, cols, src, lds, sdt, dst, ldd, ddt);
+  convert2d_kernel<<<(unsigned)blocks, 256, 0, st>>>(rows, cols, src, lds, sdt, dst, ldd, ddt); count_launches(1);
   return cudaGetLastError();
 }
 

@@ -114,7 +114,7 @@ cudaError_t chol_rinv(int w, int64_t nrows, const double* G, int64_t ldg, double
     cudaFuncSetAttribute(chol_rinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     attr = true;
   }
-  chol_rinv_kernel<<<1, 512, shm, st>>>(w, nrows, G, ldg, Rinv, work, status, gate, unit_round);
+  chol_rinv_kernel<<<1, 512, shm, st>>>(w, nrows, G, ldg, Rinv, work, status, gate, unit_round); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -212,8 +212,8 @@ cudaError_t hl_trick(int s, int nnow, int nlock, const double* Z, int64_t ldz, d
   double* Mw = static_cast<double*>(work);
   double* htau = Mw + size_t(m) * q;
   double* rowbuf = htau + q;
-  hl_qr_kernel<<<1, 256, 0, st>>>(s, nnow, nlock, Z, ldz, Mw, htau);
-  hl_apply_kernel<<<(unsigned)cdiv(s, 64), 64, 0, st>>>(s, nnow, nlock, Z, ldz, Mw, htau, CP, ldcp, rowbuf);
+  hl_qr_kernel<<<1, 256, 0, st>>>(s, nnow, nlock, Z, ldz, Mw, htau); count_launches(1);
+  hl_apply_kernel<<<(unsigned)cdiv(s, 64), 64, 0, st>>>(s, nnow, nlock, Z, ldz, Mw, htau, CP, ldcp, rowbuf); count_launches(1);
   return cudaGetLastError();
 }
 

@@ -394,7 +394,7 @@ template <typename R>
 cudaError_t ql_eig(int s, const double* A, int64_t lda, double* lam, double* Zd, int64_t ldz, QLWork<R>& w,
                    int* status_dev, cudaStream_t st) {
   const int64_t ss = int64_t(s) * s;
-  copy_sym_kernel<R><<<(unsigned)cdiv(ss, 256), 256, 0, st>>>(s, A, lda, w.Wm);
+  copy_sym_kernel<R><<<(unsigned)cdiv(ss, 256), 256, 0, st>>>(s, A, lda, w.Wm); count_launches(1);
   if (s >= 3) {
     int nb = (s + 7) / 8;
     if (nb > num_sms()) nb = num_sms();
@@ -406,24 +406,25 @@ cudaError_t ql_eig(int s, const double* A, int64_t lda, double* lam, double* Zd,
     int sv = s;
     void* args[] = {&sv, &w.Wm, &w.Vh, &w.tau, &w.d, &w.e, &w.p};
     cudaError_t err = cudaLaunchCooperativeKernel((void*)sytrd_kernel<R>, dim3(nb), dim3(256), args, shm, st);
+    count_launches(1);
     if (err != cudaSuccess) return err;
   } else {
-    small_tridiag_kernel<R><<<1, 32, 0, st>>>(s, w.Wm, w.d, w.e, w.tau);
+    small_tridiag_kernel<R><<<1, 32, 0, st>>>(s, w.Wm, w.d, w.e, w.tau); count_launches(1);
   }
   cudaFuncSetAttribute(tql_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   tql_kernel<R><<<1, 32, 2 * size_t(s) * sizeof(R), st>>>(s, w.d, w.e, w.ri, w.rc, w.rs, w.cap, w.nrot,
-                                                          status_dev ? status_dev : w.status);
-  rank_kernel<R><<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.d, w.rank, lam);
+                                                          status_dev ? status_dev : w.status); count_launches(1);
+  rank_kernel<R><<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.d, w.rank, lam); count_launches(1);
   int rpb = 32;
   while (rpb > 1 && size_t(s) * rpb * sizeof(R) > 200 * 1024) rpb >>= 1;
   cudaFuncSetAttribute(rot_accum_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
   cudaFuncSetAttribute(backtrans_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
   rot_accum_kernel<R><<<(unsigned)cdiv(s, rpb), 64, size_t(s) * rpb * sizeof(R), st>>>(s, rpb, w.ri, w.rc, w.rs,
-                                                                                       w.nrot, w.ZT);
+                                                                                       w.nrot, w.ZT); count_launches(1);
   int wpb = 8;
   while (wpb > 1 && size_t(wpb) * s * sizeof(R) > 200 * 1024) --wpb;
   backtrans_kernel<R><<<(unsigned)cdiv(s, wpb), 32 * wpb, size_t(wpb) * s * sizeof(R), st>>>(
-      s, wpb, w.Vh, w.tau, w.ZT, w.rank, Zd, ldz);
+      s, wpb, w.Vh, w.tau, w.ZT, w.rank, Zd, ldz); count_launches(1);
   return cudaGetLastError();
 }
 
@@ -660,16 +661,16 @@ cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, in
   }
   for (int it = 0; it < n_iters; ++it) {
     if ((e = oa_products(s, w, st))) return e;
-    oa_lambda_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.G, w.S, w.lam);
-    if (it == 0) cluster_kernel<<<1, 32, 0, st>>>(s, w.lam, tau_rel, w.cid, status_dev ? status_dev : w.ql.status);
-    eye_kernel<<<gb, 256, 0, st>>>(s, w.Q);
-    cluster_jacobi_kernel<<<s, 32, 0, st>>>(s, w.S, w.cid, w.Q, w.lam);
+    oa_lambda_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.G, w.S, w.lam); count_launches(1);
+    if (it == 0) cluster_kernel<<<1, 32, 0, st>>>(s, w.lam, tau_rel, w.cid, status_dev ? status_dev : w.ql.status); count_launches(1);
+    eye_kernel<<<gb, 256, 0, st>>>(s, w.Q); count_launches(1);
+    cluster_jacobi_kernel<<<s, 32, 0, st>>>(s, w.S, w.cid, w.Q, w.lam); count_launches(1);
     if ((e = stage_coef<Arith::DF64>(s, s, w.Q, s, w.Cs, s, 1.0, st))) return e;
     if ((e = update<Arith::DF64>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 0.0, st))) return e;
     std::swap(w.X, w.X2);
     if ((e = oa_products(s, w, st))) return e;
-    oa_lambda_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.G, w.S, w.lam);
-    oa_e_kernel<<<gb, 256, 0, st>>>(s, w.G, w.S, w.lam, w.cid, w.E);
+    oa_lambda_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.G, w.S, w.lam); count_launches(1);
+    oa_e_kernel<<<gb, 256, 0, st>>>(s, w.G, w.S, w.lam, w.cid, w.E); count_launches(1);
     // X2 = X + X E
     if ((e = cudaMemcpyAsync(w.X2, w.X, sizeof(dd) * ss, cudaMemcpyDeviceToDevice, st))) return e;
     if ((e = stage_coef<Arith::DF64>(s, s, w.E, s, w.Cs, s, 1.0, st))) return e;
@@ -678,13 +679,13 @@ cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, in
   }
   // final: eigenvalues, cluster diagonalisation, ascending order
   if ((e = oa_products(s, w, st))) return e;
-  oa_lambda_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.G, w.S, w.lam);
-  eye_kernel<<<gb, 256, 0, st>>>(s, w.Q);
-  cluster_jacobi_kernel<<<s, 32, 0, st>>>(s, w.S, w.cid, w.Q, w.lam);
+  oa_lambda_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.G, w.S, w.lam); count_launches(1);
+  eye_kernel<<<gb, 256, 0, st>>>(s, w.Q); count_launches(1);
+  cluster_jacobi_kernel<<<s, 32, 0, st>>>(s, w.S, w.cid, w.Q, w.lam); count_launches(1);
   if ((e = stage_coef<Arith::DF64>(s, s, w.Q, s, w.Cs, s, 1.0, st))) return e;
   if ((e = update<Arith::DF64>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 0.0, st))) return e;
-  rank_kernel<double><<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.lam, w.rank, nullptr);
-  permute_kernel<<<gb, 256, 0, st>>>(s, w.X2, w.rank, w.lam, Z, ldz, lam);
+  rank_kernel<double><<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.lam, w.rank, nullptr); count_launches(1);
+  permute_kernel<<<gb, 256, 0, st>>>(s, w.X2, w.rank, w.lam, Z, ldz, lam); count_launches(1);
   return cudaGetLastError();
 }
 

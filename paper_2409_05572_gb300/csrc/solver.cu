@@ -154,6 +154,7 @@ struct eig_handle {
   std::vector<int> widths;
   int status = EIG_OK, iters = 0, n_shrink = 0, n_expand = 0;
   double time_ms = 0.0;
+  int64_t launches = 0;
   cudaError_t cuda_err = cudaSuccess;
   // per-kernel-class statistics (opt.profile)
   struct Rec {
@@ -1189,11 +1190,13 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
 int eig_solve(eig_handle* h) {
   if (!h) return EIG_EINVAL;
   auto t0 = std::chrono::steady_clock::now();
+  const int64_t l0 = launches_total();
   int rc = solve_impl(h);
   cudaStreamSynchronize(h->st);
   prof_flush(h);
   auto t1 = std::chrono::steady_clock::now();
   h->time_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  h->launches = launches_total() - l0;
   h->status = rc;
   return rc;
 }
@@ -1213,6 +1216,7 @@ int eig_query(const eig_handle* h, eig_result* out) {
   out->time_ms = h->time_ms;
   out->normA = h->opt.normA;
   out->kstats = &h->kst[0][0];
+  out->launches = h->launches;
   return EIG_OK;
 }
 
