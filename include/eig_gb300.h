@@ -244,6 +244,36 @@ int eig_query(const eig_handle *h, eig_result *out);
 void eig_destroy(eig_handle *h);
 const char *eig_strerror(int status);
 
+/* ---- serving: many independent solves advanced together ----------------
+ * A request loop for the serving workload of many eigenproblems of different
+ * n, nev and k_max.  eig_submit copies the request (host CSR, host X0 and the
+ * options) into the server and returns a ticket; it rejects (EIG_EREJECT) a
+ * request whose device footprint (eig_footprint) exceeds the whole budget.
+ * eig_server_step admits queued requests in submission order while their
+ * footprint fits mem_budget_bytes and fewer than max_active solves run, then
+ * advances every active solve by one iteration (Algorithm 3 / 1 each, with
+ * their own shrink / expand decisions); each solve runs on its own CUDA
+ * stream so their kernels overlap.  A finished solve's results (eigenvalues,
+ * residuals, history, eigenvectors copied to host memory) are kept until
+ * eig_release; its device memory and slot are freed at once.  eig_poll sets
+ * *ready and fills *out (V is then a HOST pointer, n x nev row-major;
+ * time_ms = completion - submission).  Single-threaded: one host thread
+ * drives a server. */
+typedef struct {
+  size_t mem_budget_bytes;   /* device bytes the active solves may hold  */
+  int max_active;            /* most solves advanced per step            */
+} eig_server_opts;
+typedef struct eig_server eig_server;
+
+size_t eig_footprint(int64_t n, int64_t nnz, int nev, int k_max, const eig_options *opt);
+int eig_server_create(const eig_server_opts *opts, eig_server **out);
+int eig_submit(eig_server *s, const eig_csr *A, int nev, int k_max, int strategy,
+               const eig_options *opt, uint64_t *ticket);
+int eig_server_step(eig_server *s, int *n_active, int *n_queued);
+int eig_poll(eig_server *s, uint64_t ticket, eig_result *out, int *ready);
+int eig_release(eig_server *s, uint64_t ticket);
+void eig_server_destroy(eig_server *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,9 +24,10 @@ STRATEGIES = {"none": 0, "fix": 1, "slope": 2, "slopek": 3}
 ALGOS = {"lobpcg": 0, "chebsi": 1}
 FORMS = {"df64": 0, "f64": 1, "mixed": 2}
 
-EXPORTS = ("eig_convert", "eig_spmm", "eig_gram", "eig_gram_noalloc", "eig_block_update", "eig_residual", "eig_cholqr2",
-           "eig_syev", "eig_hl_trick", "eig_options_default", "eig_create", "eig_solve", "eig_query",
-           "eig_destroy", "eig_strerror")
+EXPORTS = ("eig_convert", "eig_spmm", "eig_gram", "eig_gram_noalloc", "eig_block_update", "eig_residual",
+           "eig_cholqr2", "eig_syev", "eig_hl_trick", "eig_options_default", "eig_create", "eig_solve",
+           "eig_query", "eig_destroy", "eig_strerror", "eig_footprint", "eig_server_create", "eig_submit",
+           "eig_server_step", "eig_poll", "eig_release", "eig_server_destroy")
 
 
 class EigError(RuntimeError):
@@ -47,6 +48,10 @@ class eig_options(C.Structure):
                 ("cheb_upper", C.c_double), ("precond", C.c_int), ("deflate_ones", C.c_int),
                 ("normA", C.c_double), ("mixed_switch", C.c_double), ("X0", C.c_void_p),
                 ("x0_on_device", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int)]
+
+
+class eig_server_opts(C.Structure):
+    _fields_ = [("mem_budget_bytes", C.c_size_t), ("max_active", C.c_int)]
 
 
 class eig_result(C.Structure):
@@ -88,12 +93,21 @@ def load(path: str = LIB_PATH):
         "eig_query": [p, C.POINTER(eig_result)],
         "eig_destroy": [p],
         "eig_strerror": [i32],
+        "eig_server_create": [C.POINTER(eig_server_opts), C.POINTER(C.c_void_p)],
+        "eig_submit": [p, C.POINTER(eig_csr), i32, i32, i32, C.POINTER(eig_options), C.POINTER(C.c_uint64)],
+        "eig_server_step": [p, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+        "eig_poll": [p, C.c_uint64, C.POINTER(eig_result), C.POINTER(C.c_int)],
+        "eig_release": [p, C.c_uint64],
+        "eig_server_destroy": [p],
+        "eig_footprint": [i64, i64, i32, i32, C.POINTER(eig_options)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = C.c_int
     lib.eig_destroy.restype = None
+    lib.eig_server_destroy.restype = None
+    lib.eig_footprint.restype = C.c_size_t
     lib.eig_strerror.restype = C.c_char_p
     _lib = lib
     return lib
@@ -324,3 +338,83 @@ def _cuda_copy_d2d(dst, src, nbytes):
     (float64 -> float64)."""
     _check("eig_convert", load().eig_convert(nbytes // 8, C.c_void_p(src), EIG_F64, C.c_void_p(dst), EIG_F64,
                                              _stream(None)))
+
+
+def make_options(algo="lobpcg", form="df64", tol=1e-10, max_iter=1000, nes=0, normA=None, **kw):
+    opt = eig_options()
+    load().eig_options_default(C.byref(opt))
+    opt.algo = ALGOS[algo]
+    opt.form = FORMS[form]
+    opt.tol = tol
+    opt.max_iter = max_iter
+    opt.nes = nes
+    for k, v in kw.items():
+        if not hasattr(opt, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(opt, k, v)
+    if normA is not None:
+        opt.normA = float(normA)
+    return opt
+
+
+def footprint(n, nnz, nev, k_max, **opts):
+    opt = make_options(**opts)
+    return int(load().eig_footprint(n, nnz, nev, k_max, C.byref(opt)))
+
+
+class Server:
+    """Serving loop (eig_server_*): submit host problems, step, poll."""
+
+    def __init__(self, mem_budget_bytes, max_active=64):
+        o = eig_server_opts(mem_budget_bytes, max_active)
+        h = C.c_void_p()
+        _check("eig_server_create", load().eig_server_create(C.byref(o), C.byref(h)))
+        self._h = h
+
+    def submit(self, A, X0, nev, k_max, strategy="fix", normA=None, **opts):
+        rp = np.ascontiguousarray(A.indptr, dtype=np.int32)
+        ci = np.ascontiguousarray(A.indices, dtype=np.int32)
+        va = np.ascontiguousarray(A.data, dtype=np.float64)
+        x0 = np.ascontiguousarray(X0, dtype=np.float64)
+        csr = eig_csr(A.n, ci.size, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0)
+        opt = make_options(normA=normA, **opts)
+        opt.X0 = x0.ctypes.data
+        opt.x0_on_device = 0
+        t = C.c_uint64()
+        _check("eig_submit", load().eig_submit(self._h, C.byref(csr), nev, k_max, STRATEGIES[strategy],
+                                               C.byref(opt), C.byref(t)))
+        return t.value
+
+    def step(self):
+        a, q = C.c_int(), C.c_int()
+        _check("eig_server_step", load().eig_server_step(self._h, C.byref(a), C.byref(q)))
+        return a.value, q.value
+
+    def poll(self, ticket, n=None):
+        r = eig_result()
+        ready = C.c_int()
+        _check("eig_poll", load().eig_poll(self._h, ticket, C.byref(r), C.byref(ready)))
+        if not ready.value:
+            return None
+        nev, it = r.nev, r.iters
+        out = {"status": r.status, "iters": it, "n_shrink": r.n_shrink, "n_expand": r.n_expand,
+               "lam": np.ctypeslib.as_array(r.lambda_, (nev,)).copy() if r.lambda_ else None,
+               "resid": np.ctypeslib.as_array(r.resid, (nev,)).copy() if r.resid else None,
+               "latency_ms": r.time_ms}
+        if r.V and n is not None:
+            out["V"] = np.ctypeslib.as_array(C.cast(r.V, C.POINTER(C.c_double)), (n, nev)).copy()
+        return out
+
+    def release(self, ticket):
+        _check("eig_release", load().eig_release(self._h, ticket))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().eig_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

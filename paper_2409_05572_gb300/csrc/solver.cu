@@ -486,7 +486,9 @@ struct Ops {
   }
   // residual norms (and R into Rdst when non-null); copies norms, lam and
   // flags to the host and synchronises.
-  int resid(const T* X, const T* AX, int w, T* Rdst, bool precond) {
+  // residual + asynchronous copy of norms, Ritz values and status flags to
+  // the host (pinned); the caller synchronises the stream before reading.
+  int resid_launch(const T* X, const T* AX, int w, T* Rdst, bool precond) {
     const T* td = precond ? FormData<AU>::tdiag(h) : nullptr;
     {
       Prof p(h, EIG_K_RESIDUAL, 6.0 * double(h->n) * w, E * double(h->n) * w * (Rdst ? 3.0 : 2.0));
@@ -497,8 +499,6 @@ struct Ops {
     CK(cudaMemcpyAsync(h->hpin + 2 * h->kmax, h->lamd, sizeof(double) * w, cudaMemcpyDeviceToHost, st()));
     CK(cudaMemcpyAsync(h->hpin + 3 * h->kmax, h->flags, sizeof(int) * NFLAGS, cudaMemcpyDeviceToHost, st()));
     CK(cudaMemsetAsync(h->flags, 0, sizeof(int) * NFLAGS, st()));
-    CK(cudaStreamSynchronize(st()));
-    prof_flush(h);
     return EIG_OK;
   }
 };
@@ -588,27 +588,36 @@ int lobpcg_init(eig_handle* h, LState& L) {
   return EIG_OK;
 }
 
-// Runs iterations until convergence, max_iter, or (when switch_r > 0) the
-// residual falls to switch_r; returns EIG_OK with *done set on convergence.
+// One LOBPCG iteration is split at its single host crossing: lob_pre
+// launches R = T (AX - X Lambda) into the W slot and the copy of the norms to
+// the host; after the stream is synchronised lob_post takes the convergence
+// and strategy decisions and launches the rest of the iteration.  *done is
+// set on convergence, *switched when the residual reached switch_r (the
+// iteration is then redone in the next precision).
 template <Arith AU, Arith AG>
-int lobpcg_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* switched) {
+int lob_pre(eig_handle* h, LState& L) {
+  using T = typename Pol<AU>::T;
+  Ops<AU, AG> o(h);
+  T* X = static_cast<T*>(h->S[L.cur]);
+  T* AX = static_cast<T*>(h->AS[L.cur]);
+  return o.resid_launch(X, AX, L.nnow, X + 2 * h->kmax, h->opt.precond != 0);
+}
+
+template <Arith AU, Arith AG>
+int lob_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switched) {
   using T = typename Pol<AU>::T;
   Ops<AU, AG> o(h);
   const int64_t ld = h->LDS;
   const int k = h->kmax, nes = h->nes;
-  const bool pre = h->opt.precond != 0;
   *done = false;
   *switched = false;
   int rc;
-  while (L.j < h->opt.max_iter) {
+  {
     const int j = L.j + 1;
     void* Sc = h->S[L.cur];
     void* ASc = h->AS[L.cur];
     T* X = static_cast<T*>(Sc);
-    T* AX = static_cast<T*>(ASc);
     T* Wslot = X + 2 * k;
-    // R = T (AX - X Lambda) into the W slot, norms to the host
-    if ((rc = o.resid(X, AX, L.nnow, Wslot, pre))) return rc;
     ConvInfo ci = conv_test(h, L.nnow);
     if (ci.breakdown) return EIG_EBREAKDOWN;
     h->history.push_back(ci.r);
@@ -721,7 +730,7 @@ int lobpcg_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* swit
       if (debug_on()) o.dbg("S_drop at shrink", view<T>(h->Sd, 2 * hd, 0, 2 * hd));
     }
   }
-  return EIG_ENOTCONV;
+  return EIG_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -734,7 +743,14 @@ int chebsi_init(eig_handle* h, LState& L) {
 }
 
 template <Arith AU, Arith AG>
-int chebsi_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* switched) {
+int cheb_pre(eig_handle* h, LState& L) {
+  using T = typename Pol<AU>::T;
+  Ops<AU, AG> o(h);
+  return o.resid_launch(static_cast<T*>(h->S[L.cur]), static_cast<T*>(h->AS[L.cur]), L.nnow, nullptr, false);
+}
+
+template <Arith AU, Arith AG>
+int cheb_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switched) {
   using T = typename Pol<AU>::T;
   Ops<AU, AG> o(h);
   const int64_t ld = h->LDS;
@@ -742,13 +758,12 @@ int chebsi_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* swit
   *done = false;
   *switched = false;
   int rc;
-  while (L.j < h->opt.max_iter) {
+  {
     const int j = L.j + 1;
     void* Sc = h->S[L.cur];
     void* ASc = h->AS[L.cur];
     T* X = static_cast<T*>(Sc);
     T* AX = static_cast<T*>(ASc);
-    if ((rc = o.resid(X, AX, L.nnow, nullptr, false))) return rc;
     ConvInfo ci = conv_test(h, L.nnow);
     if (ci.breakdown) return EIG_EBREAKDOWN;
     h->history.push_back(ci.r);
@@ -818,7 +833,7 @@ int chebsi_run(eig_handle* h, LState& L, double switch_r, bool* done, bool* swit
       L.have_drop = true;
     }
   }
-  return EIG_ENOTCONV;
+  return EIG_OK;
 }
 
 // Convert the iterate of the float32 phase to double-float storage.
@@ -904,64 +919,114 @@ int final_pass(eig_handle* h, const void* Xsrc, int src_dt) {
   return EIG_OK;
 }
 
-int solve_impl(eig_handle* h) {
+// Resumable solve: init() once, then repeat pre() (launch the residual and
+// the copy of its norms), a synchronisation of h->st, and post() (decide and
+// launch the rest of the iteration) until finished.  eig_solve runs this
+// loop; the serving loop interleaves many of them.
+enum Phase { PH_F64 = 0, PH_MIX32 = 1, PH_DF64 = 2 };
+
+struct Stepper {
+  eig_handle* h = nullptr;
   LState L;
-  L.se.kind = h->strategy;
-  L.se.nes = h->nes;
-  L.se.nex = h->kmax;
-  L.se.je = h->opt.je;
-  L.se.js = h->opt.js;
-  L.se.jp = h->opt.jp;
-  L.se.j_warm = h->opt.j_warm;
-  L.se.mu = h->opt.mu;
-  L.se.r_warm = h->opt.r_warm;
-  h->history.clear();
-  h->widths.clear();
-  h->iters = 0;
-  std::memset(h->kst, 0, sizeof(h->kst));
-  CK(cudaMemsetAsync(h->flags, 0, sizeof(int) * NFLAGS, h->st));
-  const bool lob = h->opt.algo == EIG_LOBPCG;
-  bool done = false, sw = false;
-  int rc;
-  const void* Xfinal = nullptr;
-  int dt = EIG_DF64;
-  if (h->opt.form == EIG_FORM_F64) {
-    rc = lob ? lobpcg_init<Arith::F64, Arith::F64>(h, L) : chebsi_init<Arith::F64, Arith::F64>(h, L);
-    if (rc) return rc;
-    rc = lob ? lobpcg_run<Arith::F64, Arith::F64>(h, L, 0.0, &done, &sw)
-             : chebsi_run<Arith::F64, Arith::F64>(h, L, 0.0, &done, &sw);
-    dt = EIG_F64;
-  } else {
-    if (h->opt.form == EIG_FORM_MIXED) {
-      rc = lob ? lobpcg_init<Arith::F32, Arith::C32>(h, L) : chebsi_init<Arith::F32, Arith::C32>(h, L);
-      if (rc) return rc;
-      rc = lob ? lobpcg_run<Arith::F32, Arith::C32>(h, L, h->opt.mixed_switch, &done, &sw)
-               : chebsi_run<Arith::F32, Arith::C32>(h, L, h->opt.mixed_switch, &done, &sw);
-      if (rc != EIG_OK && rc != EIG_ENOTCONV) return rc;
-      // promote to double-float storage in every case: the final pass and
-      // any remaining iterations read double-float blocks
-      const int rc1 = rc;
-      int prc = promote(h, L, lob);
-      if (prc) return prc;
-      if (!done && rc1 == EIG_OK) {
-        rc = lob ? lobpcg_run<Arith::DF64, Arith::DF64>(h, L, 0.0, &done, &sw)
-                 : chebsi_run<Arith::DF64, Arith::DF64>(h, L, 0.0, &done, &sw);
-      }
-    } else {
-      rc = lob ? lobpcg_init<Arith::DF64, Arith::DF64>(h, L) : chebsi_init<Arith::DF64, Arith::DF64>(h, L);
-      if (rc) return rc;
-      rc = lob ? lobpcg_run<Arith::DF64, Arith::DF64>(h, L, 0.0, &done, &sw)
-               : chebsi_run<Arith::DF64, Arith::DF64>(h, L, 0.0, &done, &sw);
+  int phase = PH_DF64;
+  bool lob = true;
+  bool finished = false;
+  int status = EIG_OK;
+
+  int init() {
+    L = LState();
+    L.se.kind = h->strategy;
+    L.se.nes = h->nes;
+    L.se.nex = h->kmax;
+    L.se.je = h->opt.je;
+    L.se.js = h->opt.js;
+    L.se.jp = h->opt.jp;
+    L.se.j_warm = h->opt.j_warm;
+    L.se.mu = h->opt.mu;
+    L.se.r_warm = h->opt.r_warm;
+    h->history.clear();
+    h->widths.clear();
+    h->iters = 0;
+    h->n_shrink = h->n_expand = 0;
+    std::memset(h->kst, 0, sizeof(h->kst));
+    finished = false;
+    status = EIG_OK;
+    CK(cudaMemsetAsync(h->flags, 0, sizeof(int) * NFLAGS, h->st));
+    lob = h->opt.algo == EIG_LOBPCG;
+    phase = h->opt.form == EIG_FORM_F64 ? PH_F64 : (h->opt.form == EIG_FORM_MIXED ? PH_MIX32 : PH_DF64);
+    switch (phase) {
+      case PH_F64: return lob ? lobpcg_init<Arith::F64, Arith::F64>(h, L) : chebsi_init<Arith::F64, Arith::F64>(h, L);
+      case PH_MIX32: return lob ? lobpcg_init<Arith::F32, Arith::C32>(h, L) : chebsi_init<Arith::F32, Arith::C32>(h, L);
+      default: return lob ? lobpcg_init<Arith::DF64, Arith::DF64>(h, L) : chebsi_init<Arith::DF64, Arith::DF64>(h, L);
     }
-    dt = EIG_DF64;
   }
-  if (rc != EIG_OK && rc != EIG_ENOTCONV) return rc;
-  Xfinal = h->S[L.cur];
-  h->n_shrink = L.se.n_shrink;
-  h->n_expand = L.se.n_expand;
-  int frc = final_pass(h, Xfinal, dt);
-  if (frc) return frc;
-  return finish(h, rc);
+  int pre() {
+    switch (phase) {
+      case PH_F64: return lob ? lob_pre<Arith::F64, Arith::F64>(h, L) : cheb_pre<Arith::F64, Arith::F64>(h, L);
+      case PH_MIX32: return lob ? lob_pre<Arith::F32, Arith::C32>(h, L) : cheb_pre<Arith::F32, Arith::C32>(h, L);
+      default: return lob ? lob_pre<Arith::DF64, Arith::DF64>(h, L) : cheb_pre<Arith::DF64, Arith::DF64>(h, L);
+    }
+  }
+  int end(int st) {
+    h->n_shrink = L.se.n_shrink;
+    h->n_expand = L.se.n_expand;
+    int frc = final_pass(h, h->S[L.cur], phase == PH_F64 ? EIG_F64 : EIG_DF64);
+    finished = true;
+    status = frc ? frc : st;
+    return status;
+  }
+  int post() {
+    bool done = false, sw = false;
+    int rc;
+    const double sr = phase == PH_MIX32 ? h->opt.mixed_switch : 0.0;
+    switch (phase) {
+      case PH_F64:
+        rc = lob ? lob_post<Arith::F64, Arith::F64>(h, L, sr, &done, &sw)
+                 : cheb_post<Arith::F64, Arith::F64>(h, L, sr, &done, &sw);
+        break;
+      case PH_MIX32:
+        rc = lob ? lob_post<Arith::F32, Arith::C32>(h, L, sr, &done, &sw)
+                 : cheb_post<Arith::F32, Arith::C32>(h, L, sr, &done, &sw);
+        break;
+      default:
+        rc = lob ? lob_post<Arith::DF64, Arith::DF64>(h, L, sr, &done, &sw)
+                 : cheb_post<Arith::DF64, Arith::DF64>(h, L, sr, &done, &sw);
+    }
+    if (rc) {
+      finished = true;
+      status = rc;
+      return rc;
+    }
+    const bool out_of_iters = !done && !sw && L.j >= h->opt.max_iter;
+    if (phase == PH_MIX32 && (sw || done || out_of_iters)) {
+      // promote to double-float storage: the remaining iterations and the
+      // final pass read double-float blocks
+      if ((rc = promote(h, L, lob))) {
+        finished = true;
+        status = rc;
+        return rc;
+      }
+      phase = PH_DF64;
+      if (sw) return EIG_OK;
+    }
+    if (done) return end(EIG_OK);
+    if (out_of_iters) return end(EIG_ENOTCONV);
+    return EIG_OK;
+  }
+};
+
+int solve_impl(eig_handle* h) {
+  Stepper st;
+  st.h = h;
+  int rc = st.init();
+  if (rc) return rc;
+  while (!st.finished) {
+    if ((rc = st.pre())) return rc;
+    CK(cudaStreamSynchronize(h->st));
+    prof_flush(h);
+    st.post();
+  }
+  return st.status;
 }
 
 int finish(eig_handle* h, int status) {
@@ -1026,6 +1091,30 @@ __global__ void fill_kernel(int64_t n, double v, double* x) {
 }
 
 }  // namespace
+
+// Device bytes eig_create allocates (same formulas as its allocations).
+size_t footprint_bytes(int64_t n, int64_t nnz, int nev, int k_max, int nes, int form, int precond,
+                       int deflate, int on_device) {
+  const size_t LDS = size_t((3 * k_max + 3) / 4 * 4);
+  const size_t hd = size_t(k_max - nes);
+  const size_t wtw = std::max(size_t(k_max), 2 * hd);
+  const size_t cq = std::max(wtw, size_t(2 * k_max));
+  const size_t smax = size_t(3 * k_max + 1);
+  size_t b = 0;
+  if (!on_device) b += 4 * size_t(n + 1) + 4 * size_t(nnz);
+  b += 8 * size_t(nnz) * 2;                      // float64 + double-float values
+  if (form == EIG_FORM_MIXED) b += 4 * size_t(nnz);
+  if (precond) b += 20 * size_t(n);
+  if (deflate) b += 20 * size_t(n);
+  b += 4 * 8 * size_t(n) * LDS;                  // S, AS (two copies each)
+  b += 2 * 8 * size_t(n) * std::max(wtw, size_t(nev));
+  b += 8 * size_t(n) * nev;                      // V
+  b += 8 * (smax * smax * 2 + cq * cq * 2 + cq + smax * k_max + smax * (2 * k_max + 1) + 4 * smax);
+  b += 8 * (size_t(2) * num_sms() * 4 * 64 * 64 + smax * smax + 4096);
+  b += 8 * residual_scratch_elems(n, k_max);
+  b += syev_work_bytes(int(smax)) + hl_work_bytes(int(smax), k_max, 0) + 8 * smax * smax;
+  return b + b / 16 + (size_t(32) << 20);        // allocator rounding and slack
+}
 
 // ---------------------------------------------------------------------------
 // C ABI
@@ -1175,7 +1264,7 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
   AL(h->xn, sizeof(double) * smax);
   AL(h->rn, sizeof(double) * smax);
   AL(h->Cs, sizeof(double) * size_t(smax) * (2 * k_max + 1));
-  AL(h->syevw, std::max(syev_work_bytes(smax), syev_qr64_work_bytes(smax)));
+  AL(h->syevw, use_qr64() ? std::max(syev_work_bytes(smax), syev_qr64_work_bytes(smax)) : syev_work_bytes(smax));
   AL(h->hlw, hl_work_bytes(smax, k_max, 0) + sizeof(double) * size_t(smax) * smax);
   AL(h->flags, sizeof(int) * NFLAGS);
   AL(h->V, sizeof(double) * size_t(n) * nev);
@@ -1228,5 +1317,248 @@ void eig_destroy(eig_handle* h) {
   free_all(h);
   delete h;
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Serving: a request loop over independent solves.  eig_submit queues a
+// request (host data copied); eig_server_step admits queued requests in
+// arrival order while their device footprint fits the memory budget and a
+// slot is free, then advances every active solve by one iteration: first the
+// residual and norm copy of every solve is launched on its own stream, then
+// each stream is synchronised in turn and its decisions taken and the rest of
+// its iteration launched, so the solves' kernels overlap on the device and
+// each takes its shrink / expand decisions independently.  A finished solve
+// copies its results to host memory, frees its device memory and its slot.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Request {
+  uint64_t ticket = 0;
+  int64_t n = 0, nnz = 0;
+  std::vector<int32_t> rowptr, colind;
+  std::vector<double> val, X0;
+  int nev = 0, k_max = 0, strategy = 0;
+  eig_options opt{};
+  size_t footprint = 0;
+  std::chrono::steady_clock::time_point t_submit, t_done;
+  // active state
+  eig_handle* h = nullptr;
+  cudaStream_t st = nullptr;
+  Stepper stp;
+  // results
+  bool done = false;
+  int status = EIG_OK;
+  int iters = 0, n_shrink = 0, n_expand = 0;
+  std::vector<double> lam, resid, history, V;
+  std::vector<int> widths;
+};
+
+}  // namespace
+
+struct eig_server {
+  eig_server_opts opt{};
+  uint64_t next_ticket = 1;
+  size_t in_use = 0;
+  std::vector<Request*> queue, active;
+  std::vector<Request*> finished;
+  ~eig_server() {
+    for (auto* r : queue) delete r;
+    for (auto* r : active) {
+      if (r->h) eig_destroy(r->h);
+      if (r->st) cudaStreamDestroy(r->st);
+      delete r;
+    }
+    for (auto* r : finished) delete r;
+  }
+};
+
+namespace {
+
+Request* find_req(eig_server* s, uint64_t t) {
+  for (auto* r : s->finished)
+    if (r->ticket == t) return r;
+  for (auto* r : s->active)
+    if (r->ticket == t) return r;
+  for (auto* r : s->queue)
+    if (r->ticket == t) return r;
+  return nullptr;
+}
+
+int admit(eig_server* s, Request* r) {
+  if (cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking) != cudaSuccess) return EIG_ECUDA;
+  eig_csr A{r->n, r->nnz, r->rowptr.data(), r->colind.data(), r->val.data(), 0};
+  eig_options o = r->opt;
+  o.X0 = r->X0.data();
+  o.x0_on_device = 0;
+  o.stream = r->st;
+  int rc = eig_create(&A, r->nev, r->k_max, r->strategy, &o, &r->h);
+  if (rc) return rc;
+  r->stp = Stepper();
+  r->stp.h = r->h;
+  rc = r->stp.init();
+  if (rc) return rc;
+  s->in_use += r->footprint;
+  return EIG_OK;
+}
+
+void retire(eig_server* s, Request* r) {
+  eig_handle* h = r->h;
+  r->status = r->stp.status;
+  r->iters = h->iters;
+  r->n_shrink = h->n_shrink;
+  r->n_expand = h->n_expand;
+  r->lam = h->lam;
+  r->resid = h->resid;
+  r->history = h->history;
+  r->widths = h->widths;
+  r->V.resize(size_t(r->n) * r->nev);
+  if (r->status == EIG_OK || r->status == EIG_ENOTCONV)
+    cudaMemcpyAsync(r->V.data(), h->V, sizeof(double) * r->V.size(), cudaMemcpyDeviceToHost, r->st);
+  cudaStreamSynchronize(r->st);
+  r->t_done = std::chrono::steady_clock::now();
+  r->done = true;
+  eig_destroy(h);
+  r->h = nullptr;
+  cudaStreamDestroy(r->st);
+  r->st = nullptr;
+  s->in_use -= std::min(s->in_use, r->footprint);
+  r->rowptr.clear();
+  r->colind.clear();
+  r->val.clear();
+  r->X0.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t eig_footprint(int64_t n, int64_t nnz, int nev, int k_max, const eig_options* opt) {
+  eig_options d;
+  eig_options_default(&d);
+  const eig_options* o = opt ? opt : &d;
+  const int nes = o->nes > 0 ? o->nes : nev + 5;
+  return footprint_bytes(n, nnz, nev, k_max, nes, o->form, o->precond, o->deflate_ones, 0);
+}
+
+int eig_server_create(const eig_server_opts* opts, eig_server** out) {
+  if (!opts || !out || opts->mem_budget_bytes == 0 || opts->max_active < 1) return EIG_EINVAL;
+  eig_server* s = new eig_server();
+  s->opt = *opts;
+  *out = s;
+  return EIG_OK;
+}
+
+int eig_submit(eig_server* s, const eig_csr* A, int nev, int k_max, int strategy, const eig_options* opt,
+               uint64_t* ticket) {
+  if (!s || !A || !opt || !ticket || A->on_device || !opt->X0 || opt->x0_on_device) return EIG_EINVAL;
+  const int nes = opt->nes > 0 ? opt->nes : nev + 5;
+  if (A->n <= 0 || nev < 1 || nes < nev || nes >= k_max || k_max > A->n || !(opt->normA > 0.0)) return EIG_EINVAL;
+  Request* r = new Request();
+  r->ticket = s->next_ticket++;
+  r->n = A->n;
+  r->nnz = A->nnz;
+  r->rowptr.assign(A->rowptr, A->rowptr + A->n + 1);
+  r->colind.assign(A->colind, A->colind + A->nnz);
+  r->val.assign(A->val, A->val + A->nnz);
+  r->X0.assign(opt->X0, opt->X0 + size_t(A->n) * k_max);
+  r->nev = nev;
+  r->k_max = k_max;
+  r->strategy = strategy;
+  r->opt = *opt;
+  r->footprint = footprint_bytes(A->n, A->nnz, nev, k_max, nes, opt->form, opt->precond, opt->deflate_ones, 0);
+  r->t_submit = std::chrono::steady_clock::now();
+  if (r->footprint > s->opt.mem_budget_bytes) {
+    delete r;
+    return EIG_EREJECT;
+  }
+  s->queue.push_back(r);
+  *ticket = r->ticket;
+  return EIG_OK;
+}
+
+int eig_server_step(eig_server* s, int* n_active, int* n_queued) {
+  if (!s) return EIG_EINVAL;
+  // admission in arrival order
+  while (!s->queue.empty() && int(s->active.size()) < s->opt.max_active &&
+         s->in_use + s->queue.front()->footprint <= s->opt.mem_budget_bytes) {
+    Request* r = s->queue.front();
+    s->queue.erase(s->queue.begin());
+    int rc = admit(s, r);
+    if (rc) {
+      r->status = rc;
+      r->done = true;
+      r->t_done = std::chrono::steady_clock::now();
+      if (r->h) eig_destroy(r->h);
+      if (r->st) cudaStreamDestroy(r->st);
+      r->h = nullptr;
+      r->st = nullptr;
+      s->finished.push_back(r);
+      continue;
+    }
+    s->active.push_back(r);
+  }
+  // one iteration of every active solve
+  for (auto* r : s->active) {
+    int rc = r->stp.pre();
+    if (rc) {
+      r->stp.finished = true;
+      r->stp.status = rc;
+    }
+  }
+  std::vector<Request*> still;
+  for (auto* r : s->active) {
+    if (!r->stp.finished) {
+      cudaStreamSynchronize(r->st);
+      prof_flush(r->h);
+      r->stp.post();
+    }
+    if (r->stp.finished) {
+      retire(s, r);
+      s->finished.push_back(r);
+    } else {
+      still.push_back(r);
+    }
+  }
+  s->active.swap(still);
+  if (n_active) *n_active = int(s->active.size());
+  if (n_queued) *n_queued = int(s->queue.size());
+  return EIG_OK;
+}
+
+int eig_poll(eig_server* s, uint64_t ticket, eig_result* out, int* ready) {
+  if (!s || !out || !ready) return EIG_EINVAL;
+  Request* r = find_req(s, ticket);
+  if (!r) return EIG_EINVAL;
+  *ready = r->done ? 1 : 0;
+  std::memset(out, 0, sizeof(*out));
+  if (!r->done) return EIG_OK;
+  out->status = r->status;
+  out->iters = r->iters;
+  out->n_shrink = r->n_shrink;
+  out->n_expand = r->n_expand;
+  out->nev = r->nev;
+  out->lambda = r->lam.empty() ? nullptr : r->lam.data();
+  out->resid = r->resid.empty() ? nullptr : r->resid.data();
+  out->V = r->V.empty() ? nullptr : r->V.data();
+  out->history = r->history.empty() ? nullptr : r->history.data();
+  out->widths = r->widths.empty() ? nullptr : r->widths.data();
+  out->time_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  out->normA = r->opt.normA;
+  return EIG_OK;
+}
+
+int eig_release(eig_server* s, uint64_t ticket) {
+  if (!s) return EIG_EINVAL;
+  for (size_t i = 0; i < s->finished.size(); ++i)
+    if (s->finished[i]->ticket == ticket) {
+      delete s->finished[i];
+      s->finished.erase(s->finished.begin() + i);
+      return EIG_OK;
+    }
+  return EIG_EINVAL;
+}
+
+void eig_server_destroy(eig_server* s) { delete s; }
 
 }  // extern "C"

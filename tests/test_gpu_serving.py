@@ -1,0 +1,79 @@
+"""Serving loop: requests solved concurrently (continuous batching with
+memory admission) give the same results as the same requests solved alone."""
+import numpy as np
+import pytest
+
+from paper_2409_05572_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2409_05572_gb300 import _lib as L  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    L.load()
+
+
+def small_stream(count=6):
+    reqs = W.serving_stream(count=count, rate=200.0, seed=4, n_lo=400, n_hi=4000, nev_lo=4, nev_hi=12)
+    out = []
+    for r in reqs:
+        A = r.matrix()
+        normA = W.dirichlet_norm(r.dims) + float(r.diag_shift.max())
+        X0 = W.gaussian_block(A.n, r.k_max, r.seed)
+        out.append((r, A, normA, X0))
+    return out
+
+
+OPTS = dict(form="mixed", tol=5e-9, max_iter=800, j_warm=5, r_warm=1e-4)
+
+
+def run_alone(A, X0, nev, k, normA):
+    s = L.Solver(A, nev=nev, k_max=k, strategy="fix", X0=X0, normA=normA, **OPTS)
+    out = s.solve()
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("budget_gb,max_active", [(64.0, 8), (0.0, 2)])
+def test_results_same_alone_and_in_the_mix(budget_gb, max_active):
+    stream = small_stream()
+    fps = [L.footprint(A.n, A.nnz, r.nev, r.k_max, form="mixed") for r, A, _, _ in stream]
+    budget = int(budget_gb * 2**30) if budget_gb else int(max(fps) * 1.5)   # tight: one or two at a time
+    srv = L.Server(budget, max_active)
+    tickets = [srv.submit(A, X0, r.nev, r.k_max, "fix", normA=normA, **OPTS) for r, A, normA, X0 in stream]
+    peak_active = 0
+    for _ in range(20000):
+        a, q = srv.step()
+        peak_active = max(peak_active, a)
+        if a == 0 and q == 0:
+            break
+    if budget_gb == 0.0:
+        assert peak_active <= 2
+    else:
+        assert peak_active >= 2           # several solves advanced together
+    for (r, A, normA, X0), t in zip(stream, tickets):
+        got = srv.poll(t, n=A.n)
+        assert got is not None and got["status"] == 0
+        ref = run_alone(A, X0, r.nev, r.k_max, normA)
+        assert got["iters"] == ref["iters"]
+        assert np.array_equal(got["lam"], ref["lam"])        # deterministic kernels: bitwise
+        assert got["resid"].max() <= 1e-8
+        M = A.to_scipy()
+        ex = np.linalg.eigvalsh(M.toarray())[:r.nev]
+        assert np.max(np.abs(got["lam"] - ex) / ex) <= 1e-8
+        srv.release(t)
+    srv.close()
+
+
+def test_request_larger_than_budget_is_rejected():
+    r, A, normA, X0 = small_stream(1)[0]
+    srv = L.Server(1 << 20, 4)
+    with pytest.raises(L.EigError) as e:
+        srv.submit(A, X0, r.nev, r.k_max, "fix", normA=normA, **OPTS)
+    assert e.value.code == 8   # EIG_EREJECT
+    srv.close()
