@@ -168,6 +168,7 @@ typedef struct {
 
 #define EIG_LOBPCG 0   /* Algorithm 3                                         */
 #define EIG_CHEB_SI 1  /* Algorithm 1, Chebyshev filter for the solve         */
+#define EIG_SD 2       /* Algorithm 2 (steepest descent, no locking)          */
 
 #define EIG_FORM_DF64 0   /* blocks in double-float, FP32-pipe arithmetic      */
 #define EIG_FORM_F64 1    /* blocks in float64, native FP64 arithmetic          */
@@ -193,6 +194,8 @@ typedef struct {
   int x0_on_device;    /* 1: X0 is a device pointer                           */
   void *stream;        /* cudaStream_t the solve runs on                      */
   int profile;         /* 1: time every kernel class with CUDA events          */
+  int expand_powered;  /* EIG_CHEB_SI: 1 = "Powered X_drop" (Sec. 6.4): apply
+                          the filter to the saved columns every iteration     */
 } eig_options;
 
 /* kernel classes of the per-class statistics (eig_result.kstats) */

@@ -23,7 +23,11 @@ from .strategy import Strategy
 def chebsi(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none",
            tol: float = 1e-10, max_iter: int = 1000, normA: float = 1.0,
            degree: int = 12, upper: float | None = None,
-           keep_ritz: bool = False, **strategy_params) -> Result:
+           keep_ritz: bool = False, expand: str = "drop", **strategy_params) -> Result:
+    """``expand``: "drop" appends the columns dropped at the last shrink;
+    "powered" (Sec. 6.4, "Powered X_drop") also applies the iteration's
+    operator -- here the same Chebyshev filter -- to the saved columns every
+    iteration, without orthogonalising them."""
     n, nex = X0.shape
     assert nev <= nes < nex
     if upper is None:
@@ -47,7 +51,10 @@ def chebsi(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none",
             res.lam, res.X, res.converged, res.rho = lam[:nev].copy(), X[:, :nev].copy(), True, rho[:nev]
             break
         # X <- p_m(A) X replaces X <- (A - zeta I)^{-1} X.
-        X = B.cheb_filter(A, X, degree, float(lam[nnow - 1]), upper, float(lam[0]))
+        a, a0 = float(lam[nnow - 1]), float(lam[0])
+        X = B.cheb_filter(A, X, degree, a, upper, a0)
+        if expand == "powered" and Xdrop is not None:
+            Xdrop = B.cheb_filter(A, Xdrop, degree, a, upper, a0)
         if strat.ifexpand(j, nnow):
             X = np.hstack([X, Xdrop])
             nnow = nex

@@ -801,6 +801,32 @@ int cheb_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switc
       iy = inew;
       sigma = sn;
     }
+    // "Powered X_drop": the saved columns get the same filter (no
+    // orthogonalisation); temporaries are the two halves of the Wt buffer
+    if (h->opt.expand_powered && L.have_drop) {
+      const int hd = h->hdrop;
+      T* xb[3] = {static_cast<T*>(h->Sd), static_cast<T*>(h->Wt), static_cast<T*>(h->Wt) + hd};
+      const int64_t lds[3] = {hd, h->wtw, h->wtw};
+      double sg = e / (a0 - c);
+      {
+        Prof p(h, EIG_K_SPMM, 2.0 * double(h->nnz) * hd, o.spmm_bytes(hd, 2));
+        CK(eig::spmm<AU>(o.csr(), hd, xb[0], lds[0], xb[1], lds[1], sg / e, -sg * c / e, nullptr, 0, 0.0, h->st));
+      }
+      int jp = 0, jy = 1;
+      for (int d = 2; d <= h->opt.cheb_degree; ++d) {
+        const double sn = 1.0 / (tau - sg);
+        const int jn = 3 - jp - jy;
+        Prof p(h, EIG_K_SPMM, 2.0 * double(h->nnz) * hd, o.spmm_bytes(hd, 3));
+        CK(eig::spmm<AU>(o.csr(), hd, xb[jy], lds[jy], xb[jn], lds[jn], 2.0 * sn / e, -2.0 * sn * c / e, xb[jp],
+                         lds[jp], -sg * sn, h->st));
+        jp = jy;
+        jy = jn;
+        sg = sn;
+      }
+      if (jy != 0)
+        CK(cudaMemcpy2DAsync(h->Sd, sizeof(T) * hd, xb[jy], sizeof(T) * lds[jy], sizeof(T) * hd, h->n,
+                             cudaMemcpyDeviceToDevice, h->st));
+    }
     // expansion: X <- [Y, X_drop]
     Blk<T> Y = view<T>(bufs[iy], ld, 0, L.nnow);
     if (L.se.ifexpand(j, L.nnow)) {
@@ -836,13 +862,95 @@ int cheb_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switc
   return EIG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Steepest descent with shrink-and-expand (Algorithm 2): Rayleigh-Ritz on
+// S = [X, W], W = T R orthogonalised against X; no locking.  On expansion
+// X_drop is orthogonalised against X (Algorithm 2 appends it as is, but the
+// Rayleigh-Ritz step needs an orthonormal S).
+// ---------------------------------------------------------------------------
+template <Arith AU, Arith AG>
+int sd_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switched) {
+  using T = typename Pol<AU>::T;
+  Ops<AU, AG> o(h);
+  const int64_t ld = h->LDS;
+  const int k = h->kmax, nes = h->nes;
+  *done = false;
+  *switched = false;
+  int rc;
+  const int j = L.j + 1;
+  void* Sc = h->S[L.cur];
+  void* ASc = h->AS[L.cur];
+  T* X = static_cast<T*>(Sc);
+  T* Wslot = X + 2 * k;
+  ConvInfo ci = conv_test(h, L.nnow);
+  if (ci.breakdown) return EIG_EBREAKDOWN;
+  h->history.push_back(ci.r);
+  L.se.record(j, ci.r);
+  L.j = j;
+  h->iters = j;
+  if (ci.r <= h->opt.tol) {
+    *done = true;
+    return EIG_OK;
+  }
+  if (switch_r > 0.0 && ci.r <= switch_r) {
+    L.j = j - 1;
+    h->history.pop_back();
+    L.se.r.resize(j);
+    *switched = true;
+    return EIG_OK;
+  }
+  const int nw = L.nnow;  // W = T R has the width of X before any expansion
+  if (L.se.ifexpand(j, L.nnow)) {
+    if (!L.have_drop) return EIG_EINVAL;
+    const int hd = h->hdrop;
+    Blk<T> Q;
+    if (h->opt.deflate_ones) Q.add(FormData<AU>::u0(h), 1, 1);
+    Q = cat(Q, view<T>(Sc, ld, 0, L.nnow));
+    Blk<T> Dsrc = view<T>(h->Sd, hd, 0, hd);
+    Blk<T> Dmid = view<T>(h->Wt, h->wtw, 0, hd);
+    Blk<T> Ddst = view<T>(Sc, ld, L.nnow, hd);
+    if ((rc = o.orth(Q, Dsrc, Dmid, Ddst))) return rc;
+    if ((rc = o.spmm(X + L.nnow, ld, hd, static_cast<T*>(ASc) + L.nnow, ld))) return rc;
+    L.nnow += hd;
+    L.have_drop = false;
+  }
+  Blk<T> Xb = view<T>(Sc, ld, 0, L.nnow);
+  Blk<T> Q;
+  if (h->opt.deflate_ones) Q.add(FormData<AU>::u0(h), 1, 1);
+  Q = cat(Q, Xb);
+  Blk<T> Wb = view<T>(Sc, ld, 2 * k, nw);
+  Blk<T> Wmid = view<T>(h->Wt, h->wtw, 0, nw);
+  if ((rc = o.orth(Q, Wb, Wmid, Wb))) return rc;
+  if ((rc = o.spmm(Wslot, ld, nw, static_cast<T*>(ASc) + 2 * k, ld))) return rc;
+  Blk<T> Sb = cat(Xb, Wb);
+  Blk<T> ASb = cat(view<T>(ASc, ld, 0, L.nnow), view<T>(ASc, ld, 2 * k, nw));
+  const int s = Sb.width;
+  h->widths.push_back(L.nnow);
+  if ((rc = o.rr(Sb, ASb))) return rc;
+  const int nx = 1 - L.cur;
+  void* Sn = h->S[nx];
+  void* ASn = h->AS[nx];
+  if ((rc = o.upd(Sb, h->Z, s, L.nnow, 1.0, view<T>(Sn, ld, 0, L.nnow), 0.0))) return rc;
+  if ((rc = o.spmm(static_cast<T*>(Sn), ld, L.nnow, static_cast<T*>(ASn), ld))) return rc;
+  L.cur = nx;
+  if (L.se.ifshrink(j, L.nnow)) {
+    const int hd = h->hdrop;
+    CK(cudaMemcpy2DAsync(h->Sd, sizeof(T) * hd, static_cast<T*>(Sn) + nes, sizeof(T) * ld, sizeof(T) * hd, h->n,
+                         cudaMemcpyDeviceToDevice, h->st));
+    L.nnow = nes;
+    L.have_drop = true;
+  }
+  return EIG_OK;
+}
+
 // Convert the iterate of the float32 phase to double-float storage.
 // LOBPCG keeps X, P, AX, AP implicitly consistent, so after the conversion
 // [X, P] is re-orthonormalised (the float32 blocks are orthonormal only to
 // about 1e-7), AX and AP are recomputed by SpMM and a Rayleigh-Ritz step on X
 // restores Ritz vectors; without this the residual would stall near the
 // float32 level.
-int promote(eig_handle* h, LState& L, bool lobpcg) {
+int promote(eig_handle* h, LState& L, int algo) {
+  const bool lobpcg = algo == EIG_LOBPCG;
   using T = dd;
   const int64_t ld = h->LDS;
   const int k = h->kmax;
@@ -866,7 +974,7 @@ int promote(eig_handle* h, LState& L, bool lobpcg) {
     }
   }
   L.poff = 0;
-  if (!lobpcg) {
+  if (algo == EIG_CHEB_SI) {  // re-orthonormalised by the next CholeskyQR2 anyway
     L.cur = nx;
     return EIG_OK;
   }
@@ -929,7 +1037,8 @@ struct Stepper {
   eig_handle* h = nullptr;
   LState L;
   int phase = PH_DF64;
-  bool lob = true;
+  bool lob = true;  // LOBPCG (P block, HL trick); false for subspace iteration and SD
+  int algo = EIG_LOBPCG;
   bool finished = false;
   int status = EIG_OK;
 
@@ -952,7 +1061,8 @@ struct Stepper {
     finished = false;
     status = EIG_OK;
     CK(cudaMemsetAsync(h->flags, 0, sizeof(int) * NFLAGS, h->st));
-    lob = h->opt.algo == EIG_LOBPCG;
+    algo = h->opt.algo;
+    lob = algo == EIG_LOBPCG;
     phase = h->opt.form == EIG_FORM_F64 ? PH_F64 : (h->opt.form == EIG_FORM_MIXED ? PH_MIX32 : PH_DF64);
     switch (phase) {
       case PH_F64: return lob ? lobpcg_init<Arith::F64, Arith::F64>(h, L) : chebsi_init<Arith::F64, Arith::F64>(h, L);
@@ -960,11 +1070,13 @@ struct Stepper {
       default: return lob ? lobpcg_init<Arith::DF64, Arith::DF64>(h, L) : chebsi_init<Arith::DF64, Arith::DF64>(h, L);
     }
   }
+  // SD writes R into the W slot like LOBPCG, so it shares lob_pre
   int pre() {
+    const bool w = algo != EIG_CHEB_SI;
     switch (phase) {
-      case PH_F64: return lob ? lob_pre<Arith::F64, Arith::F64>(h, L) : cheb_pre<Arith::F64, Arith::F64>(h, L);
-      case PH_MIX32: return lob ? lob_pre<Arith::F32, Arith::C32>(h, L) : cheb_pre<Arith::F32, Arith::C32>(h, L);
-      default: return lob ? lob_pre<Arith::DF64, Arith::DF64>(h, L) : cheb_pre<Arith::DF64, Arith::DF64>(h, L);
+      case PH_F64: return w ? lob_pre<Arith::F64, Arith::F64>(h, L) : cheb_pre<Arith::F64, Arith::F64>(h, L);
+      case PH_MIX32: return w ? lob_pre<Arith::F32, Arith::C32>(h, L) : cheb_pre<Arith::F32, Arith::C32>(h, L);
+      default: return w ? lob_pre<Arith::DF64, Arith::DF64>(h, L) : cheb_pre<Arith::DF64, Arith::DF64>(h, L);
     }
   }
   int end(int st) {
@@ -981,16 +1093,19 @@ struct Stepper {
     const double sr = phase == PH_MIX32 ? h->opt.mixed_switch : 0.0;
     switch (phase) {
       case PH_F64:
-        rc = lob ? lob_post<Arith::F64, Arith::F64>(h, L, sr, &done, &sw)
-                 : cheb_post<Arith::F64, Arith::F64>(h, L, sr, &done, &sw);
+        rc = algo == EIG_LOBPCG ? lob_post<Arith::F64, Arith::F64>(h, L, sr, &done, &sw)
+             : algo == EIG_SD   ? sd_post<Arith::F64, Arith::F64>(h, L, sr, &done, &sw)
+                                : cheb_post<Arith::F64, Arith::F64>(h, L, sr, &done, &sw);
         break;
       case PH_MIX32:
-        rc = lob ? lob_post<Arith::F32, Arith::C32>(h, L, sr, &done, &sw)
-                 : cheb_post<Arith::F32, Arith::C32>(h, L, sr, &done, &sw);
+        rc = algo == EIG_LOBPCG ? lob_post<Arith::F32, Arith::C32>(h, L, sr, &done, &sw)
+             : algo == EIG_SD   ? sd_post<Arith::F32, Arith::C32>(h, L, sr, &done, &sw)
+                                : cheb_post<Arith::F32, Arith::C32>(h, L, sr, &done, &sw);
         break;
       default:
-        rc = lob ? lob_post<Arith::DF64, Arith::DF64>(h, L, sr, &done, &sw)
-                 : cheb_post<Arith::DF64, Arith::DF64>(h, L, sr, &done, &sw);
+        rc = algo == EIG_LOBPCG ? lob_post<Arith::DF64, Arith::DF64>(h, L, sr, &done, &sw)
+             : algo == EIG_SD   ? sd_post<Arith::DF64, Arith::DF64>(h, L, sr, &done, &sw)
+                                : cheb_post<Arith::DF64, Arith::DF64>(h, L, sr, &done, &sw);
     }
     if (rc) {
       finished = true;
@@ -1001,7 +1116,7 @@ struct Stepper {
     if (phase == PH_MIX32 && (sw || done || out_of_iters)) {
       // promote to double-float storage: the remaining iterations and the
       // final pass read double-float blocks
-      if ((rc = promote(h, L, lob))) {
+      if ((rc = promote(h, L, algo))) {
         finished = true;
         status = rc;
         return rc;
@@ -1167,7 +1282,7 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
   if (nev < 1 || nes < nev || nes >= k_max || k_max > A->n) return EIG_EINVAL;
   if (strategy < EIG_NONE || strategy > EIG_SLOPEK) return EIG_EINVAL;
   if (!opt->X0 || !(opt->normA > 0.0) || opt->max_iter < 1 || !(opt->tol > 0.0)) return EIG_EINVAL;
-  if (opt->algo != EIG_LOBPCG && opt->algo != EIG_CHEB_SI) return EIG_EINVAL;
+  if (opt->algo != EIG_LOBPCG && opt->algo != EIG_CHEB_SI && opt->algo != EIG_SD) return EIG_EINVAL;
   if (opt->form < EIG_FORM_DF64 || opt->form > EIG_FORM_MIXED) return EIG_EINVAL;
   if (opt->algo == EIG_CHEB_SI && opt->cheb_degree < 2) return EIG_EINVAL;
   if (opt->je < 1 || opt->js < 0 || opt->jp < 1) return EIG_EINVAL;

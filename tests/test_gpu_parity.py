@@ -415,3 +415,52 @@ def test_solver_reuse_gives_identical_results(c1):
     b = s.solve()
     assert np.array_equal(a["lam"], b["lam"]) and a["iters"] == b["iters"]
     s.close()
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 2 (SD) and the powered X_drop expansion of subspace iteration
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("form", ["df64", "mixed"])
+@pytest.mark.parametrize("strategy", ["none", "fix"])
+def test_sd_parity(form, strategy):
+    from oracle.sd import sd
+    A = W.laplacian_2d(16, 12)
+    ex = np.sort(np.add.outer(4 * np.sin(np.arange(1, 17) * np.pi / 34) ** 2,
+                              4 * np.sin(np.arange(1, 13) * np.pi / 26) ** 2).ravel())
+    X0 = W.gaussian_block(A.n, 12, 5)
+    kw = dict(j_warm=3, r_warm=1e-3, je=6, js=1, jp=3)
+    normA = W.dirichlet_norm((16, 12))
+    s = L.Solver(A, nev=6, k_max=12, strategy=strategy, X0=X0, normA=normA, tol=1e-10, algo="sd",
+                 form=form, max_iter=3000, nes=8, **kw)
+    out = s.solve()
+    ref = sd(A, X0, 6, 8, strategy, tol=1e-10, normA=normA, max_iter=3000, **kw)
+    assert out["status"] == 0 and ref.converged
+    tol = 1e-10 if form == "df64" else 1e-8
+    assert np.max(np.abs(out["lam"] - ex[:6]) / ex[:6]) <= tol
+    assert np.max(np.abs(out["lam"] - ref.lam) / ref.lam) <= tol
+    if form == "df64":
+        m = min(10, len(ref.history))
+        assert np.allclose(out["history"][:m], ref.history[:m], rtol=1e-6)
+    if strategy == "fix":
+        assert out["n_expand"] >= 1
+    s.close()
+
+
+def test_chebsi_powered_drop_parity():
+    A = W.anderson_3d(12, seed=2)
+    ev = np.linalg.eigvalsh(A.to_scipy().toarray())
+    X0 = W.gaussian_block(A.n, 32, 2)
+    ub = W.gershgorin_bound(A)
+    normA = float(np.abs(ev).max())
+    kw = dict(j_warm=2, r_warm=1e-2, je=4, js=1)
+    s = L.Solver(A, nev=16, k_max=32, strategy="fix", X0=X0, normA=normA, tol=1e-11, algo="chebsi",
+                 cheb_degree=10, cheb_upper=ub, max_iter=400, expand_powered=1, **kw)
+    out = s.solve()
+    ref = o_chebsi(A, X0, 16, 21, "fix", tol=1e-11, normA=normA, degree=10, upper=ub, max_iter=400,
+                   expand="powered", **kw)
+    assert out["status"] == 0 and ref.converged
+    assert np.max(np.abs(out["lam"] - ev[:16]) / np.abs(ev[:16])) <= 1e-10
+    assert np.max(np.abs(out["lam"] - ref.lam) / np.abs(ref.lam)) <= 1e-10
+    m = min(8, len(ref.history))
+    assert np.allclose(out["history"][:m], ref.history[:m], rtol=1e-6)
+    s.close()

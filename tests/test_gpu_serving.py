@@ -19,7 +19,8 @@ def _cuda():
 
 
 def small_stream(count=6):
-    reqs = W.serving_stream(count=count, rate=200.0, seed=4, n_lo=400, n_hi=4000, nev_lo=4, nev_hi=12)
+    # nev >= 6 keeps nes = nev + 5 below k_max = 2 nev
+    reqs = W.serving_stream(count=count, rate=200.0, seed=4, n_lo=400, n_hi=4000, nev_lo=6, nev_hi=12)
     out = []
     for r in reqs:
         A = r.matrix()

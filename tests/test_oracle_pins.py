@@ -474,3 +474,31 @@ def test_chebsi_c1_shrinks_and_matches():
     assert r.converged
     assert np.allclose(r.lam, ex[:10], rtol=1e-12)
     assert any(e == "shrink" for _, e in r.events)
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 2 (SD) and the powered X_drop expansion (Sec. 6.4)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("strategy", ["none", "fix", "slopek"])
+def test_sd_matches_closed_form(strategy):
+    from oracle.sd import sd
+    A = W.laplacian_2d(16, 12)
+    ex = dirichlet_spectrum((16, 12))
+    X0 = W.gaussian_block(A.n, 12, 5)
+    r = sd(A, X0, 6, 8, strategy, tol=1e-10, normA=W.dirichlet_norm((16, 12)), max_iter=3000,
+           j_warm=3, r_warm=1e-3, je=6, js=1, jp=3)
+    assert r.converged
+    assert np.allclose(r.lam, ex[:6], rtol=1e-11)
+    if strategy != "none":
+        assert any(e == "expand" for _, e in r.events)
+
+
+def test_chebsi_powered_drop_matches_and_expands():
+    A = W.anderson_3d(6, seed=2)
+    ev = np.linalg.eigvalsh(A.to_scipy().toarray())
+    X0 = W.gaussian_block(A.n, 16, 2)
+    kw = dict(tol=1e-11, normA=float(np.abs(ev).max()), degree=8, upper=W.gershgorin_bound(A),
+              j_warm=2, r_warm=1e-2, je=4, js=1)
+    r = chebsi(A, X0, 8, 11, "fix", expand="powered", **kw)
+    assert r.converged and np.allclose(r.lam, ev[:8], rtol=1e-10, atol=1e-12)
+    assert any(e == "expand" for _, e in r.events)
