@@ -59,6 +59,14 @@ extern "C" {
 #define EIG_ARITH_DF64 1  /* double-float blocks, FP32-pipe dd arithmetic    */
 #define EIG_ARITH_F32 2   /* float32 blocks, float32 arithmetic              */
 #define EIG_ARITH_C32 3   /* float32 blocks, compensated (Dot2) accumulation */
+/* eig_gram only: double-float blocks, product on the bf16 tensor cores by an
+ * exact integer splitting (Ozaki et al. 2012): each value is cut into six
+ * 8-bit slices against a power-of-two scale per 128-row chunk and column;
+ * the slice products of levels 0..5 are summed exactly and the rest dropped,
+ * an error of about 2^-48 (at most 20 * 2^-48) of max|u| max|v| over the
+ * chunk per row, i.e. normwise rather than componentwise double-float
+ * accuracy.  Chunk columns whose maximum is below 2^-100 count as zero. */
+#define EIG_ARITH_DF64_TC 4
 
 /* ---- conversions ------------------------------------------------------- */
 /* dst[i] = src[i] for i < count, converting between EIG_F64 / EIG_F32 /
@@ -83,7 +91,11 @@ int eig_spmm(int64_t n, const int32_t *rowptr, const int32_t *colind, const void
  * sym != 0 declares U^T V symmetric (U == V, or U^T A U with symmetric A):
  * only the upper tile triangle is computed and mirrored.  The reduction over
  * n is split across CTAs into float64 partial tiles held in temporary device
- * memory and summed in a fixed order (deterministic).  a, b <= 4096. */
+ * memory and summed in a fixed order (deterministic).  a, b <= 4096.
+ * arith EIG_ARITH_DF64_TC takes EIG_DF64 blocks (U, V 8-byte aligned, any
+ * leading dimension) and also holds the bf16 slices of U and V (12 bytes per
+ * element) in temporary device memory; U == V with equal ldu, ldv and a == b
+ * is sliced once. */
 int eig_gram(int64_t n, int a, int b, const void *U, int64_t ldu, const void *V, int64_t ldv,
              int arith, int sym, double *G, int64_t ldg, void *stream);
 
@@ -196,6 +208,11 @@ typedef struct {
   int profile;         /* 1: time every kernel class with CUDA events          */
   int expand_powered;  /* EIG_CHEB_SI: 1 = "Powered X_drop" (Sec. 6.4): apply
                           the filter to the saved columns every iteration     */
+  int gram_tc;         /* 1 (default): double-float Gram products on the
+                          tensor cores (EIG_ARITH_DF64_TC, normwise ~2^-48
+                          accuracy, 24 extra bytes per n x (3 k_max + 1)
+                          element pair of device memory); 0: FP32-pipe
+                          double-float Gram (componentwise ~2^-48)            */
 } eig_options;
 
 /* kernel classes of the per-class statistics (eig_result.kstats) */

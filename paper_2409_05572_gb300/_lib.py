@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "libeig_gb300.so")
 EIG_OK, EIG_EINVAL, EIG_ENOMEM, EIG_ENOTCONV, EIG_EBREAKDOWN, EIG_ECUDA, EIG_ETIMEOUT = range(7)
 EIG_F64, EIG_F32, EIG_DF64 = 0, 1, 2
 ARITH_F64, ARITH_DF64, ARITH_F32, ARITH_C32 = 0, 1, 2, 3
+ARITH_DF64_TC = 4  # eig_gram only: double-float blocks, tensor-core product
 STRATEGIES = {"none": 0, "fix": 1, "slope": 2, "slopek": 3}
 ALGOS = {"lobpcg": 0, "chebsi": 1, "sd": 2}
 FORMS = {"df64": 0, "f64": 1, "mixed": 2}
@@ -48,7 +49,7 @@ class eig_options(C.Structure):
                 ("cheb_upper", C.c_double), ("precond", C.c_int), ("deflate_ones", C.c_int),
                 ("normA", C.c_double), ("mixed_switch", C.c_double), ("X0", C.c_void_p),
                 ("x0_on_device", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int),
-                ("expand_powered", C.c_int)]
+                ("expand_powered", C.c_int), ("gram_tc", C.c_int)]
 
 
 class eig_server_opts(C.Structure):

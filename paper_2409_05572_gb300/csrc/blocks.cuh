@@ -36,6 +36,22 @@ cudaError_t gram_capped(int64_t n, const Blk<typename Pol<A>::T>& U, const Blk<t
                         bool sym, double* G, int64_t ldg, double* scratch, size_t max_scratch_elems,
                         cudaStream_t st);
 
+// G[i][j] = sum over z < nsplit of part[z][i][j] (a x b partial tiles) in
+// that fixed order; sym: the lower triangle mirrors the upper one.
+cudaError_t gram_reduce(int a, int b, int nsplit, bool sym, const double* part, double* G, int64_t ldg,
+                        cudaStream_t st, const int* gate = nullptr);
+
+// Tensor-core Gram for double-float blocks (k_gram_tc.cu): gram_tc_slice()
+// cuts an n x w block into exact bf16 integer slices (buffer of
+// gram_tc_slice_bytes(n, w) bytes, 16-byte aligned), gram_tc_product() forms
+// G = U^T V from the slices of U (n x a) and V (n x b) with split-K partial
+// tiles in scratch (gram_tc_scratch_elems() float64 elements).
+size_t gram_tc_slice_bytes(int64_t n, int w);
+size_t gram_tc_scratch_elems(int64_t n, int a, int b, bool sym);
+cudaError_t gram_tc_slice(int64_t n, const Blk<dd>& U, void* slices, cudaStream_t st, const int* gate = nullptr);
+cudaError_t gram_tc_product(int64_t n, int a, int b, const void* slu, const void* slv, bool sym, double* G,
+                            int64_t ldg, double* scratch, cudaStream_t st, const int* gate = nullptr);
+
 // Cs[i][j] (leading dimension ldo) = staged(scale * C[i][j]) for an s x c
 // float64 matrix.
 template <Arith A>

@@ -42,6 +42,23 @@ int gram_t(int64_t n, int a, int b, const void* U, int64_t ldu, const void* V, i
                              static_cast<double*>(scr.p), st));
 }
 
+// double-float blocks, product on the tensor cores (k_gram_tc.cu)
+int gram_tc_t(int64_t n, int a, int b, const void* U, int64_t ldu, const void* V, int64_t ldv, int sym, double* G,
+              int64_t ldg, cudaStream_t st) {
+  const bool same = U == V && ldu == ldv && a == b;
+  const size_t su = (gram_tc_slice_bytes(n, a) + 255) / 256 * 256;
+  const size_t sv = same ? 0 : gram_tc_slice_bytes(n, b);
+  Tmp sl(st), scr(st);
+  if (sl.alloc(su + sv) != cudaSuccess) return EIG_ENOMEM;
+  if (scr.alloc(sizeof(double) * gram_tc_scratch_elems(n, a, b, sym != 0)) != cudaSuccess) return EIG_ENOMEM;
+  char* pu = static_cast<char*>(sl.p);
+  char* pv = same ? pu : pu + su;
+  cudaError_t e = gram_tc_slice(n, one<dd>(U, ldu, a), pu, st);
+  if (e == cudaSuccess && !same) e = gram_tc_slice(n, one<dd>(V, ldv, b), pv, st);
+  if (e == cudaSuccess) e = gram_tc_product(n, a, b, pu, pv, sym != 0, G, ldg, static_cast<double*>(scr.p), st);
+  return cuda_status(e);
+}
+
 template <Arith A>
 int update_t(int64_t n, int s, int c, const void* U, int64_t ldu, const double* C, int64_t ldc, void* Y,
              int64_t ldy, double beta, cudaStream_t st) {
@@ -150,12 +167,13 @@ int eig_spmm(int64_t n, const int32_t* rowptr, const int32_t* colind, const void
 int eig_gram(int64_t n, int a, int b, const void* U, int64_t ldu, const void* V, int64_t ldv, int arith, int sym,
              double* G, int64_t ldg, void* stream) {
   if (n < 0 || a < 0 || b < 0 || a > 4096 || b > 4096 || ldu < a || ldv < b || ldg < b) return EIG_EINVAL;
-  if (!arith_ok(arith) || (sym && a != b)) return EIG_EINVAL;
+  if ((!arith_ok(arith) && arith != EIG_ARITH_DF64_TC) || (sym && a != b)) return EIG_EINVAL;
   if (a == 0 || b == 0) return EIG_OK;
   if (!U || !V || !G) return EIG_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (n == 0) return cuda_status(cudaMemset2DAsync(G, sizeof(double) * ldg, 0, sizeof(double) * b, a, st));
   switch (arith) {
+    case EIG_ARITH_DF64_TC: return gram_tc_t(n, a, b, U, ldu, V, ldv, sym, G, ldg, st);
     case EIG_ARITH_F64: return gram_t<Arith::F64>(n, a, b, U, ldu, V, ldv, sym, G, ldg, st);
     case EIG_ARITH_DF64: return gram_t<Arith::DF64>(n, a, b, U, ldu, V, ldv, sym, G, ldg, st);
     case EIG_ARITH_F32: return gram_t<Arith::F32>(n, a, b, U, ldu, V, ldv, sym, G, ldg, st);

@@ -364,6 +364,15 @@ __global__ void gram_reduce_kernel(int a, int b, int nsplit, bool sym, const dou
   G[int64_t(i) * ldg + j] = s;
 }
 
+cudaError_t gram_reduce(int a, int b, int nsplit, bool sym, const double* part, double* G, int64_t ldg,
+                        cudaStream_t st, const int* gate) {
+  const int64_t tot = int64_t(a) * b;
+  if (tot <= 0) return cudaSuccess;
+  gram_reduce_kernel<<<(unsigned)cdiv(tot, 256), 256, 0, st>>>(a, b, nsplit, sym, part, G, ldg, gate);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 static int gram_nsplit(int64_t n, int a, int b, bool sym) {
   const int ta = (a + GT - 1) / GT, tb = (b + GT - 1) / GT;
   int tiles = sym ? (ta * (ta + 1)) / 2 : ta * tb;

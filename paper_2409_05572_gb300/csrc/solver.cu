@@ -139,6 +139,9 @@ struct eig_handle {
   void* AS[2] = {nullptr, nullptr};
   void* Wt = nullptr;
   void* Sd = nullptr;
+  // bf16 slices of the two Gram operands (opt.gram_tc, double-float blocks)
+  void* tcU = nullptr;
+  void* tcV = nullptr;
   // small float64 work
   int smax = 0;
   double *Gp = nullptr, *Rinv = nullptr, *cholw = nullptr, *Z = nullptr, *lamd = nullptr, *CP = nullptr;
@@ -258,6 +261,17 @@ Blk<T> cat(const Blk<T>& a, const Blk<T>& b) {
   return r;
 }
 
+template <typename T>
+bool same_blk(const Blk<T>& a, const Blk<T>& b) {
+  if (a.nseg != b.nseg || a.width != b.width) return false;
+  for (int t = 0; t < a.nseg; ++t)
+    if (a.ptr[t] != b.ptr[t] || a.ld[t] != b.ld[t] || a.start[t + 1] != b.start[t + 1]) return false;
+  return true;
+}
+
+// the double-float Gram products run on the tensor cores (slice buffers)
+bool uses_gram_tc(const eig_options& o) { return o.gram_tc != 0 && o.form != EIG_FORM_F64; }
+
 template <Arith A> struct FormData;
 template <> struct FormData<Arith::DF64> {
   static const dd* val(eig_handle* h) { return h->valdd; }
@@ -304,6 +318,16 @@ struct Ops {
     const double nn = double(h->n), a = U.width, b = V.width;
     const bool same = U.ptr[0] == V.ptr[0];
     Prof p(h, EIG_K_GRAM, sym ? nn * a * (b + 1) : 2.0 * nn * a * b, E * nn * (same ? a : a + b));
+    if constexpr (AG == Arith::DF64) {
+      if (h->tcU) {  // tensor-core product on exact bf16 slices
+        const bool one = same_blk(U, V);
+        CK(gram_tc_slice(h->n, U, h->tcU, st(), gate));
+        if (!one) CK(gram_tc_slice(h->n, V, h->tcV, st(), gate));
+        CK(gram_tc_product(h->n, U.width, V.width, h->tcU, one ? h->tcU : h->tcV, sym, h->Gp, V.width, h->gscr,
+                           st(), gate));
+        return EIG_OK;
+      }
+    }
     CK(eig::gram<AG>(h->n, U, V, sym, h->Gp, V.width, h->gscr, st(), gate));
     return EIG_OK;
   }
@@ -1172,6 +1196,8 @@ void free_all(eig_handle* h) {
   F(h->AS[1]);
   F(h->Wt);
   F(h->Sd);
+  F(h->tcU);
+  F(h->tcV);
   F(h->Gp);
   F(h->Rinv);
   F(h->cholw);
@@ -1209,7 +1235,7 @@ __global__ void fill_kernel(int64_t n, double v, double* x) {
 
 // Device bytes eig_create allocates (same formulas as its allocations).
 size_t footprint_bytes(int64_t n, int64_t nnz, int nev, int k_max, int nes, int form, int precond,
-                       int deflate, int on_device) {
+                       int deflate, int on_device, int gram_tc) {
   const size_t LDS = size_t((3 * k_max + 3) / 4 * 4);
   const size_t hd = size_t(k_max - nes);
   const size_t wtw = std::max(size_t(k_max), 2 * hd);
@@ -1228,6 +1254,7 @@ size_t footprint_bytes(int64_t n, int64_t nnz, int nev, int k_max, int nes, int 
   b += 8 * (size_t(2) * num_sms() * 4 * 64 * 64 + smax * smax + 4096);
   b += 8 * residual_scratch_elems(n, k_max);
   b += syev_work_bytes(int(smax)) + hl_work_bytes(int(smax), k_max, 0) + 8 * smax * smax;
+  if (gram_tc && form != EIG_FORM_F64) b += 2 * gram_tc_slice_bytes(n, int(smax));
   return b + b / 16 + (size_t(32) << 20);        // allocator rounding and slack
 }
 
@@ -1271,6 +1298,7 @@ int eig_options_default(eig_options* o) {
   o->deflate_ones = 0;
   o->normA = 0.0;
   o->mixed_switch = 1e-5;
+  o->gram_tc = 1;
   return EIG_OK;
 }
 
@@ -1361,6 +1389,10 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
   AL(h->Wt, sizeof(double) * size_t(n) * std::max(h->wtw, nev));
   // S_drop and Wt are swapped when the mixed form promotes; same size
   AL(h->Sd, sizeof(double) * size_t(n) * std::max(h->wtw, nev));
+  if (uses_gram_tc(h->opt)) {
+    AL(h->tcU, gram_tc_slice_bytes(n, 3 * k_max + 1));
+    AL(h->tcV, gram_tc_slice_bytes(n, 3 * k_max + 1));
+  }
   // small
   const int smax = 3 * k_max + 1;
   h->smax = smax;
@@ -1553,7 +1585,7 @@ size_t eig_footprint(int64_t n, int64_t nnz, int nev, int k_max, const eig_optio
   eig_options_default(&d);
   const eig_options* o = opt ? opt : &d;
   const int nes = o->nes > 0 ? o->nes : nev + 5;
-  return footprint_bytes(n, nnz, nev, k_max, nes, o->form, o->precond, o->deflate_ones, 0);
+  return footprint_bytes(n, nnz, nev, k_max, nes, o->form, o->precond, o->deflate_ones, 0, o->gram_tc);
 }
 
 int eig_server_create(const eig_server_opts* opts, eig_server** out) {
@@ -1581,7 +1613,8 @@ int eig_submit(eig_server* s, const eig_csr* A, int nev, int k_max, int strategy
   r->k_max = k_max;
   r->strategy = strategy;
   r->opt = *opt;
-  r->footprint = footprint_bytes(A->n, A->nnz, nev, k_max, nes, opt->form, opt->precond, opt->deflate_ones, 0);
+  r->footprint = footprint_bytes(A->n, A->nnz, nev, k_max, nes, opt->form, opt->precond, opt->deflate_ones, 0,
+                                 opt->gram_tc);
   r->t_submit = std::chrono::steady_clock::now();
   if (r->footprint > s->opt.mem_budget_bytes) {
     delete r;

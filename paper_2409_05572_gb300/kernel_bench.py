@@ -26,7 +26,8 @@ def main(argv=None):
     ap.add_argument("--b", type=int, default=384)
     ap.add_argument("--sym", action="store_true")
     ap.add_argument("--grid", type=int, default=128, help="3D Laplacian grid side for --kernel spmm")
-    ap.add_argument("--arith", default="df64", choices=["df64", "f64", "f32", "c32"])
+    ap.add_argument("--arith", default="df64", choices=["df64", "df64_tc", "f64", "f32", "c32"],
+                    help="df64_tc: double-float blocks, Gram on the tensor cores (--kernel gram)")
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--reps", type=int, default=5)
     args = ap.parse_args(argv)
@@ -37,12 +38,15 @@ def main(argv=None):
     from . import workloads as W
 
     L.load()
-    ar = {"df64": L.ARITH_DF64, "f64": L.ARITH_F64, "f32": L.ARITH_F32, "c32": L.ARITH_C32}[args.arith]
+    ar = {"df64": L.ARITH_DF64, "df64_tc": L.ARITH_DF64_TC, "f64": L.ARITH_F64, "f32": L.ARITH_F32,
+          "c32": L.ARITH_C32}[args.arith]
+    if args.arith == "df64_tc" and args.kernel != "gram":
+        ap.error("df64_tc applies to --kernel gram only")
     g = torch.Generator(device="cuda").manual_seed(1234)
 
     def block(rows, cols):
         x = torch.randn(rows, cols, generator=g, device="cuda", dtype=torch.float64)
-        if args.arith == "df64":
+        if args.arith in ("df64", "df64_tc"):
             return L.to_df64(x)
         if args.arith == "f64":
             return x

@@ -85,3 +85,36 @@ def test_options_default_values(libpath):
     assert lib.eig_options_default(ctypes.byref(o)) == 0
     assert (o.tol, o.max_iter, o.je, o.js, o.jp, o.j_warm) == (1e-10, 1000, 12, 2, 10, 5)
     assert (o.mu, o.r_warm, o.cheb_degree) == (1.1, 1e-4, 12)
+    assert (o.expand_powered, o.gram_tc) == (0, 1)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of the C structs have the header's field offsets
+    and sizes (compiled with the host C compiler)."""
+    import shutil
+    import subprocess
+    from paper_2409_05572_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = [_lib.eig_csr, _lib.eig_options, _lib.eig_result, _lib.eig_server_opts]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "eig_gb300.h"', "int main(void) {"]
+    for S in structs:
+        name = S.__name__
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f in S._fields_:
+            cname = f[0].rstrip("_")   # Python keywords carry a trailing underscore
+            lines.append(f'printf("{name}.{f[0]} %zu\\n", offsetof({name}, {cname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                               text=True).stdout.splitlines())
+    for S in structs:
+        name = S.__name__
+        assert int(out[name]) == ctypes.sizeof(S), name
+        for f in S._fields_:
+            assert int(out[f"{name}.{f[0]}"]) == getattr(S, f[0]).offset, (name, f[0])

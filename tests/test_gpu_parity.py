@@ -155,6 +155,116 @@ def test_gram_deterministic_and_empty():
 
 
 # ---------------------------------------------------------------------------
+# a4 / a5 / a8: Gram on the tensor cores (EIG_ARITH_DF64_TC)
+# Error model of the exact slicing: per row at most about 24.4 * 2^-48 of
+# M_u M_v (M = the column's max |x| over the row's 128-row chunk) from the
+# six-slice representation and the dropped levels, plus the double-float
+# accumulation (the DF64 tolerance above).  The test allows 32 * 2^-48.
+# ---------------------------------------------------------------------------
+def chunk_max(X, rows=128):
+    n = X.shape[0]
+    nch = -(-n // rows)
+    P = np.zeros((nch * rows, X.shape[1]))
+    P[:n] = np.abs(X)
+    cnt = np.full(nch, rows, dtype=np.float64)
+    cnt[-1] = n - (nch - 1) * rows
+    return P.reshape(nch, rows, -1).max(axis=1), cnt
+
+
+def tc_bound(U, V):
+    Mu, cnt = chunk_max(U)
+    Mv, _ = chunk_max(V)
+    return RTOL["df64"] * (np.abs(U).T @ np.abs(V)) + 32 * 2.0 ** -48 * ((Mu * cnt[:, None]).T @ Mv)
+
+
+def tc_gram(U, V, sym, ldu_pad=0, ldv_pad=0):
+    n, a = U.shape
+    b = V.shape[1]
+    Up = np.zeros((n, a + ldu_pad))
+    Up[:, :a] = U
+    Ud = L.to_df64(dev(Up))
+    if V is U and ldv_pad == ldu_pad:
+        Vd = Ud
+    else:
+        Vp = np.zeros((n, b + ldv_pad))
+        Vp[:, :b] = V
+        Vd = L.to_df64(dev(Vp))
+    G = torch.full((a, b + 2), 9.0, dtype=torch.float64, device="cuda")
+    L.eig_gram(n, a, b, Ud, a + ldu_pad, Vd, b + ldv_pad, L.ARITH_DF64_TC, sym, G, b + 2)
+    assert torch.all(G[:, b:] == 9.0)
+    return G[:, :b].cpu().numpy()
+
+
+@pytest.mark.parametrize("n,a,b,sym", [(5017, 7, 5, False), (5017, 64, 64, True), (5017, 130, 70, False),
+                                       (5017, 150, 150, True), (1, 3, 2, False), (127, 1, 1, True),
+                                       (129, 65, 129, False), (3000, 385, 385, True)])
+def test_gram_tc_parity(n, a, b, sym):
+    rng = np.random.default_rng(n + a * 7 + b)
+    U = rng.standard_normal((n, a))
+    V = U if sym else rng.standard_normal((n, b))
+    got = tc_gram(U, V, sym, ldu_pad=3 * (not sym))
+    ref = B.gram(U, V)
+    err = np.abs(got - ref)
+    assert np.all(err <= tc_bound(U, V)), np.max(err / tc_bound(U, V))
+    if sym:
+        assert np.array_equal(got, got.T)
+
+
+def test_gram_tc_wide_range_and_structure():
+    """Columns scaled by 2^-60 .. 2^60, localized columns (exponential decay
+    over thousands of rows, like Anderson eigenvectors), a column with one
+    nonzero, a zero column, entries at powers of two with lo of both signs,
+    values just below a power of two, and a sign-alternating column."""
+    n, a = 4100, 40
+    rng = np.random.default_rng(11)
+    U = rng.standard_normal((n, a))
+    r = np.arange(n)
+    for j in range(8):
+        U[:, j] = rng.standard_normal(n) * np.exp(-np.abs(r - 500 * j) / 60.0)
+    U[:, 8] = 0.0
+    U[:, 9] = 0.0
+    U[1234, 9] = -3.75
+    U[:, 10] = 2.0 ** rng.integers(-20, 20, n) * (1 + 2.0 ** -30 * rng.choice([-1, 1], n))
+    U[:, 11] = np.nextafter(2.0 ** rng.integers(-5, 5, n), 0) * rng.choice([-1.0, 1.0], n)
+    U[:, 12] = (-1.0) ** r * (1 + 1e-9 * r)
+    for j in range(13, a):
+        U[:, j] *= 2.0 ** rng.integers(-60, 60)
+    V = rng.standard_normal((n, 24)) * 2.0 ** rng.integers(-30, 30, 24)
+    for sym, (X, Y) in ((True, (U, U)), (False, (U, V))):
+        got = tc_gram(X, Y, sym)
+        ref = B.gram(X, Y)
+        err = np.abs(got - ref)
+        bound = tc_bound(X, Y)
+        assert np.all(err <= bound), np.max(err / np.maximum(bound, 1e-300))
+    assert np.all(got[8] == 0.0)
+
+
+def test_gram_tc_tiny_chunks_are_zero_and_deterministic():
+    n, a = 3000, 20
+    rng = np.random.default_rng(5)
+    U = rng.standard_normal((n, a))
+    U[:, 3] = 1e-35 * rng.standard_normal(n)   # every chunk maximum below 2^-100
+    g1 = tc_gram(U, U, True)
+    g2 = tc_gram(U, U, True)
+    assert np.array_equal(g1, g2)
+    assert np.all(g1[3] == 0.0) and np.all(g1[:, 3] == 0.0)
+
+
+def test_gram_tc_matches_cuda_core_gram_in_solve_accuracy():
+    """Same C-ABI product through both DF64 arithmetics on orthonormal
+    columns (the CholeskyQR Gram of a converged block): both within 1e-13
+    of the identity's exact Gram."""
+    n, a = 20000, 96
+    Q, _ = np.linalg.qr(np.random.default_rng(9).standard_normal((n, a)))
+    Qd = L.to_df64(dev(Q))
+    for arith in (L.ARITH_DF64, L.ARITH_DF64_TC):
+        G = torch.empty(a, a, dtype=torch.float64, device="cuda")
+        L.eig_gram(n, a, a, Qd, a, Qd, a, arith, True, G, a)
+        ref = B.gram(Q, Q)
+        assert np.max(np.abs(G.cpu().numpy() - ref)) <= 1e-13
+
+
+# ---------------------------------------------------------------------------
 # a4 / a11: block update
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("arith", ["f64", "df64", "f32"])
@@ -342,6 +452,21 @@ def test_c1_lobpcg_parity(c1, form, strategy):
     Qv, _ = np.linalg.qr(V)
     Qo, _ = np.linalg.qr(ref.X)
     assert np.linalg.norm(Qv @ Qv.T - Qo @ Qo.T, 2) < 1e-8
+    s.close()
+
+
+def test_c1_lobpcg_cuda_core_gram(c1):
+    """The double-float form with its Gram products on the FP32 pipes
+    (gram_tc = 0) instead of the tensor cores."""
+    A, normA, X0, ex = c1
+    s = L.Solver(A, nev=10, k_max=20, strategy="fix", X0=X0, normA=normA, tol=1e-10, gram_tc=0)
+    out = s.solve()
+    ref = o_lobpcg(A, X0, 10, 15, "fix", tol=1e-10, normA=normA)
+    assert out["status"] == 0
+    assert np.max(np.abs(out["lam"] - ref.lam) / ref.lam) <= 1e-10
+    assert out["resid"].max() <= 2e-10
+    m = min(12, len(ref.history), len(out["history"]))
+    assert np.allclose(out["history"][:m], ref.history[:m], rtol=1e-6)
     s.close()
 
 
