@@ -41,16 +41,25 @@ cudaError_t gram_capped(int64_t n, const Blk<typename Pol<A>::T>& U, const Blk<t
 cudaError_t gram_reduce(int a, int b, int nsplit, bool sym, const double* part, double* G, int64_t ldg,
                         cudaStream_t st, const int* gate = nullptr);
 
-// Tensor-core Gram for double-float blocks (k_gram_tc.cu): gram_tc_slice()
-// cuts an n x w block into exact bf16 integer slices (buffer of
-// gram_tc_slice_bytes(n, w) bytes, 16-byte aligned), gram_tc_product() forms
-// G = U^T V from the slices of U (n x a) and V (n x b) with split-K partial
-// tiles in scratch (gram_tc_scratch_elems() float64 elements).
-size_t gram_tc_slice_bytes(int64_t n, int w);
+// Tensor-core products of double-float blocks (k_tc.cu).  A slice buffer
+// holds the exact bf16 integer slices of an operand with contraction length
+// K and M operand rows: tc_slice_bytes(K, M) bytes, 16-byte aligned.
+//  - Gram G = U^T V (n x a, n x b): tc_slice_cols() of U and V (K = n,
+//    M = width), gram_tc_product() with split-K partial tiles in scratch
+//    (gram_tc_scratch_elems() float64 elements).
+//  - Update Y = U (scale C) + beta Y (U: n x s, C: s x c float64): tc_slice_rows()
+//    of U (K = s, M = n), tc_slice_coef() of C (K = s, M = c),
+//    update_tc_product().  Y must not overlap U.
+size_t tc_slice_bytes(int64_t K, int64_t M);
 size_t gram_tc_scratch_elems(int64_t n, int a, int b, bool sym);
-cudaError_t gram_tc_slice(int64_t n, const Blk<dd>& U, void* slices, cudaStream_t st, const int* gate = nullptr);
+cudaError_t tc_slice_cols(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t st, const int* gate = nullptr);
+cudaError_t tc_slice_rows(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t st, const int* gate = nullptr);
+cudaError_t tc_slice_coef(int s, int c, const double* C, int64_t ldc, double scale, void* buf, cudaStream_t st,
+                          const int* gate = nullptr);
 cudaError_t gram_tc_product(int64_t n, int a, int b, const void* slu, const void* slv, bool sym, double* G,
                             int64_t ldg, double* scratch, cudaStream_t st, const int* gate = nullptr);
+cudaError_t update_tc_product(int64_t n, int s, int c, const void* slu, const void* slc, const Blk<dd>& Y,
+                              double beta, cudaStream_t st, const int* gate = nullptr);
 
 // Cs[i][j] (leading dimension ldo) = staged(scale * C[i][j]) for an s x c
 // float64 matrix.

@@ -42,23 +42,6 @@ int gram_t(int64_t n, int a, int b, const void* U, int64_t ldu, const void* V, i
                              static_cast<double*>(scr.p), st));
 }
 
-// double-float blocks, product on the tensor cores (k_gram_tc.cu)
-int gram_tc_t(int64_t n, int a, int b, const void* U, int64_t ldu, const void* V, int64_t ldv, int sym, double* G,
-              int64_t ldg, cudaStream_t st) {
-  const bool same = U == V && ldu == ldv && a == b;
-  const size_t su = (gram_tc_slice_bytes(n, a) + 255) / 256 * 256;
-  const size_t sv = same ? 0 : gram_tc_slice_bytes(n, b);
-  Tmp sl(st), scr(st);
-  if (sl.alloc(su + sv) != cudaSuccess) return EIG_ENOMEM;
-  if (scr.alloc(sizeof(double) * gram_tc_scratch_elems(n, a, b, sym != 0)) != cudaSuccess) return EIG_ENOMEM;
-  char* pu = static_cast<char*>(sl.p);
-  char* pv = same ? pu : pu + su;
-  cudaError_t e = gram_tc_slice(n, one<dd>(U, ldu, a), pu, st);
-  if (e == cudaSuccess && !same) e = gram_tc_slice(n, one<dd>(V, ldv, b), pv, st);
-  if (e == cudaSuccess) e = gram_tc_product(n, a, b, pu, pv, sym != 0, G, ldg, static_cast<double*>(scr.p), st);
-  return cuda_status(e);
-}
-
 template <Arith A>
 int update_t(int64_t n, int s, int c, const void* U, int64_t ldu, const double* C, int64_t ldc, void* Y,
              int64_t ldy, double beta, cudaStream_t st) {
@@ -70,6 +53,38 @@ int update_t(int64_t n, int s, int c, const void* U, int64_t ldu, const double* 
   if (e != cudaSuccess) return EIG_ECUDA;
   return cuda_status(update<A>(n, one<T>(U, ldu, s), static_cast<S*>(cs.p), c, one<T>(Y, ldy, c), beta, st));
 }
+
+// double-float blocks, product on the tensor cores (k_tc.cu)
+int gram_tc_t(int64_t n, int a, int b, const void* U, int64_t ldu, const void* V, int64_t ldv, int sym, double* G,
+              int64_t ldg, cudaStream_t st) {
+  const bool same = U == V && ldu == ldv && a == b;
+  const size_t su = (tc_slice_bytes(n, a) + 255) / 256 * 256;
+  const size_t sv = same ? 0 : tc_slice_bytes(n, b);
+  Tmp sl(st), scr(st);
+  if (sl.alloc(su + sv) != cudaSuccess) return EIG_ENOMEM;
+  if (scr.alloc(sizeof(double) * gram_tc_scratch_elems(n, a, b, sym != 0)) != cudaSuccess) return EIG_ENOMEM;
+  char* pu = static_cast<char*>(sl.p);
+  char* pv = same ? pu : pu + su;
+  cudaError_t e = tc_slice_cols(n, one<dd>(U, ldu, a), pu, st);
+  if (e == cudaSuccess && !same) e = tc_slice_cols(n, one<dd>(V, ldv, b), pv, st);
+  if (e == cudaSuccess) e = gram_tc_product(n, a, b, pu, pv, sym != 0, G, ldg, static_cast<double*>(scr.p), st);
+  return cuda_status(e);
+}
+
+int update_tc_t(int64_t n, int s, int c, const void* U, int64_t ldu, const double* C, int64_t ldc, void* Y,
+                int64_t ldy, double beta, cudaStream_t st) {
+  if (s == 0) return update_t<Arith::DF64>(n, s, c, U, ldu, C, ldc, Y, ldy, beta, st);
+  const size_t su = (tc_slice_bytes(s, n) + 255) / 256 * 256;
+  Tmp sl(st);
+  if (sl.alloc(su + tc_slice_bytes(s, c)) != cudaSuccess) return EIG_ENOMEM;
+  char* pu = static_cast<char*>(sl.p);
+  char* pc = pu + su;
+  cudaError_t e = tc_slice_coef(s, c, C, ldc, 1.0, pc, st);
+  if (e == cudaSuccess) e = tc_slice_rows(n, one<dd>(U, ldu, s), pu, st);
+  if (e == cudaSuccess) e = update_tc_product(n, s, c, pu, pc, one<dd>(Y, ldy, c), beta, st);
+  return cuda_status(e);
+}
+
 
 template <Arith A>
 int residual_t(int64_t n, int w, const void* X, int64_t ldx, const void* AX, int64_t ldax, const double* lam,
@@ -183,11 +198,13 @@ int eig_gram(int64_t n, int a, int b, const void* U, int64_t ldu, const void* V,
 
 int eig_block_update(int64_t n, int s, int c, const void* U, int64_t ldu, const double* C, int64_t ldc, void* Y,
                      int64_t ldy, double beta, int arith, void* stream) {
-  if (n < 0 || s < 0 || c < 0 || ldu < s || ldc < c || ldy < c || !arith_ok(arith)) return EIG_EINVAL;
+  if (n < 0 || s < 0 || c < 0 || ldu < s || ldc < c || ldy < c || (!arith_ok(arith) && arith != EIG_ARITH_DF64_TC))
+    return EIG_EINVAL;
   if (n == 0 || c == 0) return EIG_OK;
   if (!Y || (s > 0 && (!U || !C))) return EIG_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   switch (arith) {
+    case EIG_ARITH_DF64_TC: return update_tc_t(n, s, c, U, ldu, C, ldc, Y, ldy, beta, st);
     case EIG_ARITH_F64: return update_t<Arith::F64>(n, s, c, U, ldu, C, ldc, Y, ldy, beta, st);
     case EIG_ARITH_DF64: return update_t<Arith::DF64>(n, s, c, U, ldu, C, ldc, Y, ldy, beta, st);
     case EIG_ARITH_F32: return update_t<Arith::F32>(n, s, c, U, ldu, C, ldc, Y, ldy, beta, st);

@@ -1,0 +1,641 @@
+// Double-float block products on the tensor cores: the Gram products
+// G = U^T V and the block updates Y = U C + beta Y of the Rayleigh-Ritz,
+// orthogonalisation and update steps of arXiv:2409.05572 (Algorithms 1-3),
+// the two contractions that dominate every iteration.
+//
+// Exact splitting, a fixed-point form of Ozaki, Ogita, Oishi and Rump
+// (Numer. Algorithms 59, 2012).  Both operands of a product P = A B^T
+// (A: M x K, B: N x K, contraction over K) are cut into six integer slices
+// against a power of two shared by one CHUNK of 64 consecutive K indices of
+// one row of A (or B): with e the exponent of the chunk's largest |x|
+// (max < 2^e),
+//   x 2^(7 - e) = s_0 + s_1 2^-8 + ... + s_5 2^-40 + r,  |s_i| <= 128,
+//   |r| <= 2^-41, i.e. r is below 2^-47 of the chunk's max.
+// Integers of magnitude <= 256 are exact in bf16, every product s_i t_j
+// (<= 2^14) is exact in the fp32 accumulators of mma.sync, and for every level
+// l = i + j <= 5 the sum over one chunk (64 K indices) of its at most six
+// products per index stays below 6 * 64 * 2^14 < 2^23, so each level
+// accumulates EXACTLY in its own fp32 accumulator, whatever order the tensor
+// core adds in.  After every chunk the six level sums are combined into a
+// double-float (TwoSum), scaled by 2^(e_a + e_b - 14) and added to a
+// double-float accumulator.  The levels l >= 6 are dropped: per K index that
+// is at most 20 * 2^-48 of max|a| max|b| over the chunk, and about 2^-48 of
+// it on average.  The result is accurate normwise (to the chunk maxima)
+// rather than componentwise like the FP32-pipe double-float kernels.
+//
+//  Gram G = U^T V:   A = U^T, B = V^T, K = the n rows; chunks are 64 rows of
+//                    one column (tc_slice_cols).
+//  Update U C:       A = U, B = C^T, K = the s columns of U; chunks are 64
+//                    columns of one row of U (tc_slice_rows) and 64 rows of one
+//                    column of C (tc_slice_coef, from float64 C).
+//
+// Slice buffers hold [slice][32-K block][M][32] bf16, then one int exponent
+// per (chunk, row of the operand).  The product kernel streams 32-K blocks of
+// both operands into shared memory with cp.async (three stages), loads
+// m16n8k16 fragments with ldmatrix and issues 21 MMAs per fragment pair and
+// k-step (all slice pairs with i + j <= 5).  Gram: split-K partial tiles,
+// summed in a fixed order by the same reduction as the CUDA-core Gram.
+// Update: persistent CTAs walk the 64 x 64 output tiles, N fastest, and
+// write Y = P + beta Y in double-float.
+//
+// Range: chunks whose maximum is below 2^-100 are treated as 0 (their
+// products are below 2^-100 times the other operand, far under the rounding
+// of any entry that matters); double-float itself has the float32 exponent
+// range.
+#include <cuda_bf16.h>
+
+#include "blocks.cuh"
+
+namespace eig {
+
+namespace {
+
+constexpr int TC_S = 6;        // slices per value
+constexpr int TC_KB = 32;      // K indices per block (one pipeline stage)
+constexpr int TC_CH = 64;      // K indices per chunk (one exponent, one exact-level flush)
+constexpr int TC_KBC = TC_CH / TC_KB;
+constexpr int TC_T = 64;       // CTA tile: 64 rows of A x 64 rows of B
+constexpr int TC_KP = 40;      // padded pitch (bf16) of one row's 32 K values in shared memory
+constexpr int TC_NST = 3;      // pipeline stages
+constexpr int TC_OPND = TC_S * TC_T * TC_KP;  // bf16 elements per operand and stage
+constexpr int TC_STAGE = 2 * TC_OPND;
+constexpr size_t TC_SHM = size_t(TC_NST) * TC_STAGE * sizeof(__nv_bfloat16);
+constexpr int TC_ZERO = -1000;  // exponent mark of an all-zero chunk
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+
+// slices of one double-float value, scaled by `scale` (a power of two)
+__device__ __forceinline__ void cut(float hv, float lv, float scale, float* s) {
+  hv *= scale;
+  lv *= scale;
+#pragma unroll
+  for (int q = 0; q < TC_S; ++q) {
+    const float r = rintf(hv);
+    s[q] = r;
+    float nh, nl;
+    two_sum(hv - r, lv, nh, nl);  // hv - r is exact (Sterbenz)
+    hv = nh * 256.f;
+    lv = nl * 256.f;
+  }
+}
+
+__device__ __forceinline__ int chunk_exp(float mx) {
+  int e = TC_ZERO;
+  if (mx >= 0x1p-100f) frexpf(mx, &e);  // 2^(e-1) <= mx < 2^e
+  return e;
+}
+
+__device__ __forceinline__ float exp_scale(int e) { return e == TC_ZERO ? 0.f : ldexpf(1.0f, 7 - e); }
+
+// 16 slices values of one slice (two rows of 8) -> 2 x 16 bytes
+__device__ __forceinline__ void store16(__nv_bfloat16* dst, const float (*v)[TC_S], int q) {
+  uint32_t p[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * i][q], v[2 * i + 1][q]);
+    p[i] = *reinterpret_cast<const uint32_t*>(&b);
+  }
+  uint4* d = reinterpret_cast<uint4*>(dst);
+  d[0] = make_uint4(p[0], p[1], p[2], p[3]);
+  d[1] = make_uint4(p[4], p[5], p[6], p[7]);
+}
+
+// ---------------------------------------------------------------------------
+// Slicing.  CTA = one 64 x 64 square of the block (one chunk x 64 operand
+// rows), 256 threads; staged through shared memory so that both the read of
+// the row-major block and the write of the slice layout are coalesced.
+// ---------------------------------------------------------------------------
+struct SliceOut {
+  __nv_bfloat16* sl;  // [TC_S][nkb][M][32]
+  int* ex;            // [nkc][M]
+  int64_t nkb;
+  int64_t M;
+};
+
+__device__ __forceinline__ void col_lookup(const Blk<dd>& U, int c, const dd*& p, int64_t& ld) {
+  int s = 0;
+  while (s + 1 < U.nseg && c >= U.start[s + 1]) ++s;
+  p = U.ptr[s] + (c - U.start[s]);
+  ld = U.ld[s];
+}
+
+// Gram operand: K = rows of U, operand rows = columns of U
+__global__ void __launch_bounds__(256) tc_slice_cols_kernel(int64_t n, Blk<dd> U, SliceOut o, const int* gate) {
+  if (gate && *gate == 0) return;
+  const int w = U.width;
+  const int c0 = blockIdx.x * 64;
+  const int64_t kc = blockIdx.y;
+  const int64_t r0 = kc * TC_CH;
+  __shared__ float shi[TC_CH][65];
+  __shared__ float slo[TC_CH][65];
+  __shared__ float pmax[4][64];
+  __shared__ int sexp[64];
+  const int t = threadIdx.x;
+  {
+    const int lc = t & 63, lr = t >> 6;
+    const int c = c0 + lc;
+    const dd* colp = nullptr;
+    int64_t cld = 0;
+    if (c < w) col_lookup(U, c, colp, cld);
+    float m = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < TC_CH / 4; ++i) {
+      const int rr = lr + 4 * i;
+      const int64_t r = r0 + rr;
+      dd x = {0.f, 0.f};
+      if (colp && r < n) x = colp[r * cld];
+      shi[rr][lc] = x.hi;
+      slo[rr][lc] = x.lo;
+      m = fmaxf(m, fabsf(x.hi));
+    }
+    pmax[lr][lc] = m;
+  }
+  __syncthreads();
+  if (t < 64) {
+    const float mm = fmaxf(fmaxf(pmax[0][t], pmax[1][t]), fmaxf(pmax[2][t], pmax[3][t]));
+    const int e = chunk_exp(mm);
+    sexp[t] = e;
+    if (c0 + t < w) o.ex[kc * o.M + c0 + t] = e == TC_ZERO ? 0 : e;
+  }
+  __syncthreads();
+  // thread -> (K block kbl, operand row col, K values k0 .. k0 + 15)
+  const int kbl = t >> 7, col = (t & 127) >> 1, k0 = (t & 1) * 16;
+  const int c = c0 + col;
+  if (c >= w) return;
+  const float scale = exp_scale(sexp[col]);
+  float v[16][TC_S];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) cut(shi[kbl * TC_KB + k0 + i][col], slo[kbl * TC_KB + k0 + i][col], scale, v[i]);
+  const int64_t kb = kc * TC_KBC + kbl;
+#pragma unroll
+  for (int q = 0; q < TC_S; ++q) store16(o.sl + ((q * o.nkb + kb) * o.M + c) * TC_KB + k0, v, q);
+}
+
+// Update operand A: K = columns of U, operand rows = rows of U
+__global__ void __launch_bounds__(256) tc_slice_rows_kernel(int64_t n, Blk<dd> U, SliceOut o, const int* gate) {
+  if (gate && *gate == 0) return;
+  const int w = U.width;
+  const int64_t r0 = int64_t(blockIdx.x) * 64;
+  const int kc = blockIdx.y;
+  const int k00 = kc * TC_CH;
+  __shared__ float shi[64][65];
+  __shared__ float slo[64][65];
+  __shared__ int sexp[64];
+  const int t = threadIdx.x;
+  {
+    const int lc = t & 63, lr = t >> 6;
+    const int c = k00 + lc;
+    const dd* colp = nullptr;
+    int64_t cld = 0;
+    if (c < w) col_lookup(U, c, colp, cld);
+#pragma unroll 4
+    for (int i = 0; i < 16; ++i) {
+      const int rr = lr + 4 * i;
+      const int64_t r = r0 + rr;
+      dd x = {0.f, 0.f};
+      if (colp && r < n) x = colp[r * cld];
+      shi[rr][lc] = x.hi;
+      slo[rr][lc] = x.lo;
+    }
+  }
+  __syncthreads();
+  {
+    // row maxima: 4 threads per row, 16 columns each
+    const int row = t >> 2, part = t & 3;
+    float m = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) m = fmaxf(m, fabsf(shi[row][part * 16 + i]));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    if (part == 0) {
+      const int e = chunk_exp(m);
+      sexp[row] = e;
+      if (r0 + row < n) o.ex[int64_t(kc) * o.M + r0 + row] = e == TC_ZERO ? 0 : e;
+    }
+  }
+  __syncthreads();
+  const int kbl = t >> 7, row = (t & 127) >> 1, k0 = (t & 1) * 16;
+  const int64_t r = r0 + row;
+  if (r >= n) return;
+  const float scale = exp_scale(sexp[row]);
+  float v[16][TC_S];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) cut(shi[row][kbl * TC_KB + k0 + i], slo[row][kbl * TC_KB + k0 + i], scale, v[i]);
+  const int64_t kb = int64_t(kc) * TC_KBC + kbl;
+#pragma unroll
+  for (int q = 0; q < TC_S; ++q) store16(o.sl + ((q * o.nkb + kb) * o.M + r) * TC_KB + k0, v, q);
+}
+
+// Update operand B from float64 C (s x c, ldc) times scale: K = rows of C,
+// operand rows = columns of C.  Cut in float64 (exact: each step removes the
+// integer part of a value with at most 53 significant bits).
+__global__ void __launch_bounds__(256) tc_slice_coef_kernel(int s, int c, const double* __restrict__ C, int64_t ldc,
+                                                            double scale, SliceOut o, const int* gate) {
+  if (gate && *gate == 0) return;
+  const int j0 = blockIdx.x * 64;
+  const int kc = blockIdx.y;
+  const int k00 = kc * TC_CH;
+  __shared__ double sc[TC_CH][65];
+  __shared__ double pmax[4][64];
+  __shared__ int sexp[64];
+  const int t = threadIdx.x;
+  {
+    const int lj = t & 63, lk = t >> 6;
+    const int j = j0 + lj;
+    double m = 0.0;
+    for (int i = 0; i < TC_CH / 4; ++i) {
+      const int kk = lk + 4 * i;
+      const int k = k00 + kk;
+      const double x = (j < c && k < s) ? scale * C[int64_t(k) * ldc + j] : 0.0;
+      sc[kk][lj] = x;
+      m = fmax(m, fabs(x));
+    }
+    pmax[lk][lj] = m;
+  }
+  __syncthreads();
+  if (t < 64) {
+    const double mm = fmax(fmax(pmax[0][t], pmax[1][t]), fmax(pmax[2][t], pmax[3][t]));
+    int e = TC_ZERO;
+    if (mm >= 0x1p-100) frexp(mm, &e);
+    sexp[t] = e;
+    if (j0 + t < c) o.ex[int64_t(kc) * o.M + j0 + t] = e == TC_ZERO ? 0 : e;
+  }
+  __syncthreads();
+  const int kbl = t >> 7, col = (t & 127) >> 1, k0 = (t & 1) * 16;
+  const int j = j0 + col;
+  if (j >= c) return;
+  const int e = sexp[col];
+  float v[16][TC_S];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    double x = e == TC_ZERO ? 0.0 : ldexp(sc[kbl * TC_KB + k0 + i][col], 7 - e);
+#pragma unroll
+    for (int q = 0; q < TC_S; ++q) {
+      const double r = rint(x);
+      v[i][q] = float(r);
+      x = (x - r) * 256.0;
+    }
+  }
+  const int64_t kb = int64_t(kc) * TC_KBC + kbl;
+#pragma unroll
+  for (int q = 0; q < TC_S; ++q) store16(o.sl + ((q * o.nkb + kb) * o.M + j) * TC_KB + k0, v, q);
+}
+
+// ---------------------------------------------------------------------------
+// product kernel
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(s));
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const int nb = pred ? 16 : 0;  // 0: zero-fill, nothing read
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(nb));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+struct Opnd {
+  const __nv_bfloat16* sl;  // [TC_S][nkb][M][32]
+  const int* ex;            // [nkc][M]
+  int64_t M;
+};
+
+struct GramOut {
+  double* part;  // [split][M_A][M_B]
+  bool sym;
+};
+
+struct UpdOut {
+  Blk<dd> Y;
+  dd beta;
+  bool has_beta;
+};
+
+// MODE 0: Gram (one item per CTA: tile (blockIdx.y, blockIdx.x), K blocks
+// [z * kb_per, (z + 1) * kb_per) of split z = blockIdx.z).
+// MODE 1: update (persistent: items t = blockIdx.x + i * gridDim.x over the
+// tiles_m x tiles_n output tiles, N fastest, all K blocks).
+template <int MODE>
+__global__ void __launch_bounds__(512, 1) tc_product_kernel(Opnd A, Opnd B, int nkb, int kb_per, int tiles_n,
+                                                            int nitems, GramOut go, UpdOut uo, const int* gate) {
+  if (gate && *gate == 0) return;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __nv_bfloat16* sm = reinterpret_cast<__nv_bfloat16*>(smraw);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int am = (warp >> 2) * 16;  // warp's 16 A rows within the tile
+  const int bn = (warp & 3) * 16;   // warp's 16 B rows within the tile
+  const int g = lane >> 2, tq = lane & 3;
+
+  // this CTA's sequence of (item, K block) positions
+  int item0, item_step, nitem_cta, kb0, nkb_item;
+  if (MODE == 0) {
+    if (go.sym && blockIdx.y > blockIdx.x) return;
+    item0 = int(blockIdx.y) * tiles_n + int(blockIdx.x);
+    item_step = 1;
+    nitem_cta = 1;
+    kb0 = int(blockIdx.z) * kb_per;
+    const int kb1 = min(kb0 + kb_per, nkb);
+    nkb_item = kb1 > kb0 ? kb1 - kb0 : 0;
+  } else {
+    item0 = blockIdx.x;
+    item_step = gridDim.x;
+    nitem_cta = item0 < nitems ? (nitems - 1 - item0) / item_step + 1 : 0;
+    kb0 = 0;
+    nkb_item = nkb;
+  }
+  if (nkb_item == 0) nitem_cta = MODE == 0 ? nitem_cta : 0;
+
+  auto load_stage = [&](int it, int kbi, int buf) {
+    const int item = item0 + it * item_step;
+    const int64_t kb = kb0 + kbi;
+    const int64_t m0 = int64_t(item / tiles_n) * TC_T, n0 = int64_t(item % tiles_n) * TC_T;
+    __nv_bfloat16* dst = sm + buf * TC_STAGE;
+#pragma unroll
+    for (int i = 0; i < (TC_S * TC_T * 4) / 512; ++i) {
+      const int id = t + 512 * i;
+      const int q = id / (TC_T * 4);
+      const int rem = id % (TC_T * 4);
+      const int col = rem >> 2, piece = rem & 3;
+      const int64_t ra = m0 + col, rb = n0 + col;
+      const __nv_bfloat16* ga = A.sl + ((q * int64_t(nkb) + kb) * A.M + (ra < A.M ? ra : 0)) * TC_KB + piece * 8;
+      const __nv_bfloat16* gb = B.sl + ((q * int64_t(nkb) + kb) * B.M + (rb < B.M ? rb : 0)) * TC_KB + piece * 8;
+      cp_async16(dst + (q * TC_T + col) * TC_KP + piece * 8, ga, ra < A.M);
+      cp_async16(dst + TC_OPND + (q * TC_T + col) * TC_KP + piece * 8, gb, rb < B.M);
+    }
+  };
+
+  // ldmatrix row addresses (element offsets within a stage)
+  const int lm = lane >> 3, lr = lane & 7;
+  const int a_off = (am + lr + (lm & 1) * 8) * TC_KP + (lm >> 1) * 8;
+  const int b_off = TC_OPND + (bn + (lm >> 1) * 8 + lr) * TC_KP + (lm & 1) * 8;
+
+  float acc[2][6][4];
+  dd master[2][4];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int f = 0; f < 4; ++f) master[j][f] = {0.f, 0.f};
+
+  // load position (ld_it, ld_k) runs TC_NST - 1 stages ahead of compute
+  int ld_it = 0, ld_k = 0, ld_buf = 0;
+#pragma unroll
+  for (int s = 0; s < TC_NST - 1; ++s) {
+    if (ld_it < nitem_cta && nkb_item > 0) {
+      load_stage(ld_it, ld_k, ld_buf);
+      if (++ld_k == nkb_item) {
+        ld_k = 0;
+        ++ld_it;
+      }
+      ld_buf = ld_buf + 1 == TC_NST ? 0 : ld_buf + 1;
+    }
+    cp_async_commit();
+  }
+  int buf = 0;
+  for (int it = 0; it < nitem_cta; ++it) {
+    const int item = item0 + it * item_step;
+    const int64_t m0 = int64_t(item / tiles_n) * TC_T, n0 = int64_t(item % tiles_n) * TC_T;
+    const int64_t rl = m0 + am + g, rh = rl + 8;
+    for (int kbi = 0; kbi < nkb_item; ++kbi) {
+      const int kb = kb0 + kbi;
+      if (kb % TC_KBC == 0 || kbi == 0) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+          for (int l = 0; l < 6; ++l)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) acc[j][l][f] = 0.f;
+      }
+      cp_async_wait<TC_NST - 2>();
+      __syncthreads();
+      if (ld_it < nitem_cta) {
+        load_stage(ld_it, ld_k, ld_buf);
+        if (++ld_k == nkb_item) {
+          ld_k = 0;
+          ++ld_it;
+        }
+        ld_buf = ld_buf + 1 == TC_NST ? 0 : ld_buf + 1;
+      }
+      cp_async_commit();
+      const __nv_bfloat16* stg = sm + buf * TC_STAGE;
+      buf = buf + 1 == TC_NST ? 0 : buf + 1;
+#pragma unroll
+      for (int ks = 0; ks < TC_KB; ks += 16) {
+        uint32_t bf[TC_S][4];
+#pragma unroll
+        for (int q = 0; q < TC_S; ++q) ldsm_x4(bf[q], stg + b_off + q * TC_T * TC_KP + ks);
+#pragma unroll
+        for (int qi = 0; qi < TC_S; ++qi) {
+          uint32_t af[4];
+          ldsm_x4(af, stg + a_off + qi * TC_T * TC_KP + ks);
+#pragma unroll
+          for (int qj = 0; qj < TC_S - qi; ++qj) {
+            mma_bf16(acc[0][qi + qj], af, bf[qj][0], bf[qj][1]);
+            mma_bf16(acc[1][qi + qj], af, bf[qj][2], bf[qj][3]);
+          }
+        }
+      }
+      const bool last = kbi + 1 == nkb_item;
+      if (kb % TC_KBC == TC_KBC - 1 || last) {
+        // chunk done: value = sum_l acc_l 2^(-8 l) (exact integers per
+        // level), times 2^(e_a + e_b - 14), added to the double-float master
+        const int64_t kc = kb / TC_KBC;
+        const int eal = rl < A.M ? A.ex[kc * A.M + rl] : 0;
+        const int eah = rh < A.M ? A.ex[kc * A.M + rh] : 0;
+        int ebc[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const int64_t cb = n0 + bn + 8 * (f >> 1) + 2 * tq + (f & 1);
+          ebc[f] = cb < B.M ? B.ex[kc * B.M + cb] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+          for (int f = 0; f < 4; ++f) {
+            float hi = acc[j][5][f], lo = 0.f;
+#pragma unroll
+            for (int l = 4; l >= 0; --l) {
+              hi *= 0x1p-8f;
+              lo *= 0x1p-8f;
+              float s, e;
+              two_sum(acc[j][l][f], hi, s, e);
+              lo += e;
+              hi = s;
+            }
+            const int sc = (f >= 2 ? eah : eal) + ebc[2 * j + (f & 1)] - 14;
+            hi = ldexpf(hi, sc);
+            lo = ldexpf(lo, sc);
+            float s, e;
+            two_sum(master[j][f].hi, hi, s, e);
+            e += master[j][f].lo + lo;
+            master[j][f].hi = s + e;
+            master[j][f].lo = e - (master[j][f].hi - s);
+          }
+      }
+    }
+    // item done: write it out
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const int64_t r = f >= 2 ? rh : rl;
+        const int64_t c = n0 + bn + 8 * j + 2 * tq + (f & 1);
+        if (r < A.M && c < B.M) {
+          if (MODE == 0) {
+            go.part[int64_t(blockIdx.z) * A.M * B.M + r * B.M + c] =
+                double(master[j][f].hi) + double(master[j][f].lo);
+          } else {
+            dd* yp = uo.Y.at(r, int(c));
+            dd v = master[j][f];
+            if (uo.has_beta) dd_mac(v, *yp, uo.beta);
+            dd_renorm(v);
+            *yp = v;
+          }
+        }
+        master[j][f] = {0.f, 0.f};
+      }
+  }
+  cp_async_wait<0>();
+}
+
+int64_t nkb_of(int64_t K) { return cdiv(K, TC_CH) * TC_KBC; }
+
+SliceOut slice_out(void* buf, int64_t K, int64_t M) {
+  SliceOut o;
+  o.nkb = nkb_of(K);
+  o.M = M;
+  o.sl = static_cast<__nv_bfloat16*>(buf);
+  o.ex = reinterpret_cast<int*>(o.sl + size_t(TC_S) * size_t(o.nkb) * size_t(M) * TC_KB);
+  return o;
+}
+
+Opnd opnd(const void* buf, int64_t K, int64_t M) {
+  SliceOut s = slice_out(const_cast<void*>(buf), K, M);
+  return Opnd{s.sl, s.ex, M};
+}
+
+int gram_tc_nsplit(int64_t n, int a, int b, bool sym) {
+  const int ta = (a + TC_T - 1) / TC_T, tb = (b + TC_T - 1) / TC_T;
+  const int tiles = (sym && ta == tb) ? ta * (ta + 1) / 2 : ta * tb;
+  int ns = num_sms() / tiles;  // one CTA per SM, one wave
+  const int64_t nch = cdiv(n, TC_CH);
+  if (ns > nch) ns = int(nch);
+  if (ns < 1) ns = 1;
+  return ns;
+}
+
+template <int MODE>
+cudaError_t set_smem() {
+  static thread_local int done_dev = -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (done_dev != dev) {
+    e = cudaFuncSetAttribute(tc_product_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TC_SHM));
+    if (e != cudaSuccess) return e;
+    done_dev = dev;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+size_t tc_slice_bytes(int64_t K, int64_t M) {
+  const size_t sb = sizeof(__nv_bfloat16) * size_t(TC_S) * size_t(nkb_of(K)) * size_t(M) * TC_KB;
+  return sb + sizeof(int) * size_t(cdiv(K, TC_CH)) * size_t(M);
+}
+
+size_t gram_tc_scratch_elems(int64_t n, int a, int b, bool sym) {
+  return size_t(gram_tc_nsplit(n, a, b, sym)) * size_t(a) * size_t(b);
+}
+
+cudaError_t tc_slice_cols(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t st, const int* gate) {
+  const int w = U.width;
+  if (w <= 0 || n <= 0) return cudaSuccess;
+  dim3 grid((w + 63) / 64, (unsigned)cdiv(n, TC_CH));
+  tc_slice_cols_kernel<<<grid, 256, 0, st>>>(n, U, slice_out(buf, n, w), gate);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_slice_rows(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t st, const int* gate) {
+  const int w = U.width;
+  if (w <= 0 || n <= 0) return cudaSuccess;
+  dim3 grid((unsigned)cdiv(n, 64), (unsigned)cdiv(w, TC_CH));
+  tc_slice_rows_kernel<<<grid, 256, 0, st>>>(n, U, slice_out(buf, w, n), gate);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_slice_coef(int s, int c, const double* C, int64_t ldc, double scale, void* buf, cudaStream_t st,
+                          const int* gate) {
+  if (s <= 0 || c <= 0) return cudaSuccess;
+  dim3 grid((c + 63) / 64, (unsigned)cdiv(s, TC_CH));
+  tc_slice_coef_kernel<<<grid, 256, 0, st>>>(s, c, C, ldc, scale, slice_out(buf, s, c), gate);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t gram_tc_product(int64_t n, int a, int b, const void* slu, const void* slv, bool sym, double* G,
+                            int64_t ldg, double* scratch, cudaStream_t st, const int* gate) {
+  if (a <= 0 || b <= 0 || n <= 0) return cudaSuccess;
+  cudaError_t e = set_smem<0>();
+  if (e != cudaSuccess) return e;
+  const int64_t nkb = nkb_of(n);
+  const int ns = gram_tc_nsplit(n, a, b, sym);
+  const int64_t kb_per = cdiv(cdiv(n, TC_CH), ns) * TC_KBC;
+  const int tm = (a + TC_T - 1) / TC_T, tn = (b + TC_T - 1) / TC_T;
+  GramOut go{scratch, sym};
+  UpdOut uo{};
+  dim3 grid(tn, tm, ns);
+  tc_product_kernel<0><<<grid, 512, TC_SHM, st>>>(opnd(slu, n, a), opnd(slv, n, b), int(nkb), int(kb_per), tn,
+                                                  tm * tn, go, uo, gate);
+  count_launches(1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return gram_reduce(a, b, ns, sym, scratch, G, ldg, st, gate);
+}
+
+cudaError_t update_tc_product(int64_t n, int s, int c, const void* slu, const void* slc, const Blk<dd>& Y,
+                              double beta, cudaStream_t st, const int* gate) {
+  if (n <= 0 || c <= 0) return cudaSuccess;
+  cudaError_t e = set_smem<1>();
+  if (e != cudaSuccess) return e;
+  const int64_t nkb = nkb_of(s);
+  const int64_t tm = cdiv(n, TC_T);
+  const int tn = (c + TC_T - 1) / TC_T;
+  const int64_t items = tm * tn;
+  int64_t grid = num_sms();
+  if (grid > items) grid = items;
+  GramOut go{};
+  UpdOut uo;
+  uo.Y = Y;
+  const float bh = float(beta);
+  uo.beta = dd{bh, float(beta - double(bh))};
+  uo.has_beta = beta != 0.0;
+  tc_product_kernel<1><<<(unsigned)grid, 512, TC_SHM, st>>>(opnd(slu, s, n), opnd(slc, s, c), int(nkb), int(nkb),
+                                                            tn, int(items), go, uo, gate);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace eig

@@ -142,6 +142,7 @@ struct eig_handle {
   // bf16 slices of the two Gram operands (opt.gram_tc, double-float blocks)
   void* tcU = nullptr;
   void* tcV = nullptr;
+  void* tcC = nullptr;  // slices of the update coefficients
   // small float64 work
   int smax = 0;
   double *Gp = nullptr, *Rinv = nullptr, *cholw = nullptr, *Z = nullptr, *lamd = nullptr, *CP = nullptr;
@@ -269,8 +270,13 @@ bool same_blk(const Blk<T>& a, const Blk<T>& b) {
   return true;
 }
 
-// the double-float Gram products run on the tensor cores (slice buffers)
+// the double-float Gram products and updates run on the tensor cores (slice
+// buffers)
 bool uses_gram_tc(const eig_options& o) { return o.gram_tc != 0 && o.form != EIG_FORM_F64; }
+
+// one slice buffer: a Gram operand (K = n, up to w columns) or an update's
+// left operand (K = up to w columns, n rows)
+size_t tc_operand_bytes(int64_t n, int w) { return std::max(tc_slice_bytes(n, w), tc_slice_bytes(w, n)); }
 
 template <Arith A> struct FormData;
 template <> struct FormData<Arith::DF64> {
@@ -321,8 +327,8 @@ struct Ops {
     if constexpr (AG == Arith::DF64) {
       if (h->tcU) {  // tensor-core product on exact bf16 slices
         const bool one = same_blk(U, V);
-        CK(gram_tc_slice(h->n, U, h->tcU, st(), gate));
-        if (!one) CK(gram_tc_slice(h->n, V, h->tcV, st(), gate));
+        CK(tc_slice_cols(h->n, U, h->tcU, st(), gate));
+        if (!one) CK(tc_slice_cols(h->n, V, h->tcV, st(), gate));
         CK(gram_tc_product(h->n, U.width, V.width, h->tcU, one ? h->tcU : h->tcV, sym, h->Gp, V.width, h->gscr,
                            st(), gate));
         return EIG_OK;
@@ -334,6 +340,19 @@ struct Ops {
   // Y = U (scale * C) + beta Y with C float64 (s x c, ldc)
   int upd(const Blk<T>& U, const double* C, int64_t ldc, int c, double scale, const Blk<T>& Y, double beta,
           const int* gate = nullptr) {
+    if constexpr (AU == Arith::DF64) {
+      if (h->tcU && U.width > 0 && c > 0) {  // tensor-core product on exact bf16 slices
+        {
+          Prof p(h, EIG_K_OTHER, 0.0, 0.0);
+          CK(tc_slice_coef(U.width, c, C, ldc, scale, h->tcC, st(), gate));
+        }
+        const double nn = double(h->n);
+        Prof p(h, EIG_K_UPDATE, 2.0 * nn * U.width * c, E * nn * (U.width + c * (beta != 0.0 ? 2.0 : 1.0)));
+        CK(tc_slice_rows(h->n, U, h->tcU, st(), gate));
+        CK(update_tc_product(h->n, U.width, c, h->tcU, h->tcC, Y, beta, st(), gate));
+        return EIG_OK;
+      }
+    }
     {
       Prof p(h, EIG_K_OTHER, 0.0, 0.0);
       CK(stage_coef<AU>(U.width, c, C, ldc, static_cast<SU*>(h->Cs), c, scale, st(), gate));
@@ -1198,6 +1217,7 @@ void free_all(eig_handle* h) {
   F(h->Sd);
   F(h->tcU);
   F(h->tcV);
+  F(h->tcC);
   F(h->Gp);
   F(h->Rinv);
   F(h->cholw);
@@ -1254,7 +1274,8 @@ size_t footprint_bytes(int64_t n, int64_t nnz, int nev, int k_max, int nes, int 
   b += 8 * (size_t(2) * num_sms() * 4 * 64 * 64 + smax * smax + 4096);
   b += 8 * residual_scratch_elems(n, k_max);
   b += syev_work_bytes(int(smax)) + hl_work_bytes(int(smax), k_max, 0) + 8 * smax * smax;
-  if (gram_tc && form != EIG_FORM_F64) b += 2 * gram_tc_slice_bytes(n, int(smax));
+  if (gram_tc && form != EIG_FORM_F64)
+    b += 2 * tc_operand_bytes(n, int(smax)) + tc_slice_bytes(int64_t(smax), 2 * k_max + 1);
   return b + b / 16 + (size_t(32) << 20);        // allocator rounding and slack
 }
 
@@ -1390,8 +1411,9 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
   // S_drop and Wt are swapped when the mixed form promotes; same size
   AL(h->Sd, sizeof(double) * size_t(n) * std::max(h->wtw, nev));
   if (uses_gram_tc(h->opt)) {
-    AL(h->tcU, gram_tc_slice_bytes(n, 3 * k_max + 1));
-    AL(h->tcV, gram_tc_slice_bytes(n, 3 * k_max + 1));
+    AL(h->tcU, tc_operand_bytes(n, 3 * k_max + 1));
+    AL(h->tcV, tc_operand_bytes(n, 3 * k_max + 1));
+    AL(h->tcC, tc_slice_bytes(3 * k_max + 1, 2 * k_max + 1));
   }
   // small
   const int smax = 3 * k_max + 1;

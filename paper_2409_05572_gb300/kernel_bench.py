@@ -27,7 +27,7 @@ def main(argv=None):
     ap.add_argument("--sym", action="store_true")
     ap.add_argument("--grid", type=int, default=128, help="3D Laplacian grid side for --kernel spmm")
     ap.add_argument("--arith", default="df64", choices=["df64", "df64_tc", "f64", "f32", "c32"],
-                    help="df64_tc: double-float blocks, Gram on the tensor cores (--kernel gram)")
+                    help="df64_tc: double-float blocks, product on the tensor cores (gram, update)")
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--reps", type=int, default=5)
     args = ap.parse_args(argv)
@@ -40,8 +40,8 @@ def main(argv=None):
     L.load()
     ar = {"df64": L.ARITH_DF64, "df64_tc": L.ARITH_DF64_TC, "f64": L.ARITH_F64, "f32": L.ARITH_F32,
           "c32": L.ARITH_C32}[args.arith]
-    if args.arith == "df64_tc" and args.kernel != "gram":
-        ap.error("df64_tc applies to --kernel gram only")
+    if args.arith == "df64_tc" and args.kernel not in ("gram", "update"):
+        ap.error("df64_tc applies to --kernel gram and --kernel update")
     g = torch.Generator(device="cuda").manual_seed(1234)
 
     def block(rows, cols):

@@ -287,6 +287,63 @@ def test_update_parity(arith, s, c, beta):
     assert np.all(np.abs(got - ref) <= tol * scale + 1e-300)
 
 
+def row_chunk_max(X, cols=64):
+    """max |x| over each row's chunks of 64 columns: (rows, chunks), counts."""
+    m, k = X.shape
+    nch = -(-k // cols)
+    P = np.zeros((m, nch * cols))
+    P[:, :k] = np.abs(X)
+    cnt = np.full(nch, cols, dtype=np.float64)
+    cnt[-1] = k - (nch - 1) * cols
+    return P.reshape(m, nch, cols).max(axis=2), cnt
+
+
+@pytest.mark.parametrize("n,s,c,beta", [(5017, 7, 5, 0.0), (5017, 64, 64, 1.0), (5017, 130, 70, -0.37),
+                                        (3001, 385, 257, 0.0), (1, 3, 2, 2.5), (65, 1, 129, -1.0)])
+def test_update_tc_parity(n, s, c, beta):
+    """Y = U C + beta Y on the tensor cores (EIG_ARITH_DF64_TC): per output
+    at most about 24.4 * 2^-48 * sum over 64-column chunks k of
+    64 * max|U(row, k)| * max|C(k, col)|, plus double-float accumulation."""
+    rng = np.random.default_rng(n + s * 3 + c)
+    U = rng.standard_normal((n, s)) * 2.0 ** rng.integers(-20, 20, s)
+    Cm = rng.standard_normal((s, c))
+    Y0 = rng.standard_normal((n, c))
+    Ud = L.to_df64(dev(U))
+    Yd = L.to_df64(dev(Y0))
+    L.eig_block_update(n, s, c, Ud, s, dev(Cm), c, Yd, c, beta, L.ARITH_DF64_TC)
+    got = L.from_df64(Yd).cpu().numpy()
+    ref = U @ Cm + beta * Y0
+    Mu, cnt = row_chunk_max(U)
+    Mc, _ = row_chunk_max(Cm.T)
+    bound = RTOL["df64"] * (np.abs(U) @ np.abs(Cm) + abs(beta) * np.abs(Y0)) + \
+        32 * 2.0 ** -48 * ((Mu * cnt) @ Mc.T)
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), np.max(err / bound)
+
+
+def test_update_tc_zero_width_and_padding():
+    """s = 0 gives beta Y; the leading dimensions larger than the widths are
+    neither read nor written."""
+    n, s, c = 300, 40, 20
+    rng = np.random.default_rng(4)
+    U = np.zeros((n, s + 5))
+    U[:, :s] = rng.standard_normal((n, s))
+    U[:, s:] = np.nan
+    Cm = np.zeros((s, c + 3))
+    Cm[:, :c] = rng.standard_normal((s, c))
+    Cm[:, c:] = np.nan
+    Y0 = rng.standard_normal((n, c + 2))
+    Yd = L.to_df64(dev(Y0))
+    L.eig_block_update(n, s, c, L.to_df64(dev(U)), s + 5, dev(Cm), c + 3, Yd, c + 2, 0.5, L.ARITH_DF64_TC)
+    got = L.from_df64(Yd).cpu().numpy()
+    ref = U[:, :s] @ Cm[:, :c] + 0.5 * Y0[:, :c]
+    assert np.all(np.abs(got[:, :c] - ref) <= 1e-12 * (np.abs(U[:, :s]) @ np.abs(Cm[:, :c]) + np.abs(Y0[:, :c])))
+    assert np.array_equal(got[:, c:], L.from_df64(L.to_df64(dev(Y0[:, c:].copy()))).cpu().numpy())
+    Yd = L.to_df64(dev(Y0))
+    L.eig_block_update(n, 0, c, L.to_df64(dev(U)), s + 5, dev(Cm), c + 3, Yd, c + 2, -2.0, L.ARITH_DF64_TC)
+    assert np.allclose(L.from_df64(Yd).cpu().numpy()[:, :c], -2.0 * Y0[:, :c], rtol=1e-14)
+
+
 # ---------------------------------------------------------------------------
 # a1 / a2: residual, norms, Jacobi preconditioning
 # ---------------------------------------------------------------------------
