@@ -17,10 +17,12 @@
 // products per index stays below 6 * 64 * 2^14 < 2^23, so each level
 // accumulates EXACTLY in its own fp32 accumulator, whatever order the tensor
 // core adds in.  After every chunk the six level sums are combined into a
-// double-float (TwoSum), scaled by 2^(e_a + e_b - 14) and added to a
-// double-float accumulator.  The levels l >= 6 are dropped: per K index that
-// is at most 20 * 2^-48 of max|a| max|b| over the chunk, and about 2^-48 of
-// it on average.  The result is accurate normwise (to the chunk maxima)
+// double-float (two TwoSums, the small levels added into the low part: about
+// 2^-44 of the largest possible chunk sum), scaled by 2^(e_a - 7) 2^(e_b - 7)
+// (each factor a normal float for the exponents -99 .. 128 a chunk can have)
+// and added to a double-float accumulator.  The levels l >= 6 are dropped:
+// per K index that is at most 20 * 2^-48 of max|a| max|b| over the chunk,
+// and about 2^-48 of it on average.  The result is accurate normwise (to the chunk maxima)
 // rather than componentwise like the FP32-pipe double-float kernels.
 //
 //  Gram G = U^T V:   A = U^T, B = V^T, K = the n rows; chunks are 64 rows of
@@ -81,6 +83,27 @@ __device__ __forceinline__ void cut(float hv, float lv, float scale, float* s) {
     hv = nh * 256.f;
     lv = nl * 256.f;
   }
+}
+
+// (hi, lo) = sum_l a_l 2^(-8 l) for exact integer level sums |a_l| < 2^23:
+// the two leading terms error-free (TwoSum), the rest into lo.  With
+// |a_0| <= 2^20 (one product per K index), |lo| < 2^-1 and the four roundings
+// of lo stay below 2^-24, i.e. 2^-44 of the largest possible chunk sum.
+__device__ __forceinline__ void combine_levels(float a0, float a1, float a2, float a3, float a4, float a5,
+                                               float& hi, float& lo) {
+  float h, e1, e2;
+  two_sum(a0, a1 * 0x1p-8f, h, e1);
+  two_sum(h, a2 * 0x1p-16f, hi, e2);
+  lo = e1 + e2;
+  lo = fmaf(a3, 0x1p-24f, lo);
+  lo = fmaf(a4, 0x1p-32f, lo);
+  lo = fmaf(a5, 0x1p-40f, lo);
+}
+
+// 2^k by its bit pattern; k > 127 (a float64 coefficient beyond the float
+// range) gives +inf, k < -126 gives 0
+__device__ __forceinline__ float pow2(int k) {
+  return k > 127 ? __int_as_float(0x7f800000) : (k < -126 ? 0.f : __int_as_float((k + 127) << 23));
 }
 
 __device__ __forceinline__ int chunk_exp(float mx) {
@@ -459,34 +482,25 @@ __global__ void __launch_bounds__(512, 1) tc_product_kernel(Opnd A, Opnd B, int 
         // chunk done: value = sum_l acc_l 2^(-8 l) (exact integers per
         // level), times 2^(e_a + e_b - 14), added to the double-float master
         const int64_t kc = kb / TC_KBC;
-        const int eal = rl < A.M ? A.ex[kc * A.M + rl] : 0;
-        const int eah = rh < A.M ? A.ex[kc * A.M + rh] : 0;
-        int ebc[4];
+        const float fal = pow2(rl < A.M ? A.ex[kc * A.M + rl] - 7 : 0);
+        const float fah = pow2(rh < A.M ? A.ex[kc * A.M + rh] - 7 : 0);
+        float fbc[4];
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
           const int64_t cb = n0 + bn + 8 * (f >> 1) + 2 * tq + (f & 1);
-          ebc[f] = cb < B.M ? B.ex[kc * B.M + cb] : 0;
+          fbc[f] = pow2(cb < B.M ? B.ex[kc * B.M + cb] - 7 : 0);
         }
 #pragma unroll
         for (int j = 0; j < 2; ++j)
 #pragma unroll
           for (int f = 0; f < 4; ++f) {
-            float hi = acc[j][5][f], lo = 0.f;
-#pragma unroll
-            for (int l = 4; l >= 0; --l) {
-              hi *= 0x1p-8f;
-              lo *= 0x1p-8f;
-              float s, e;
-              two_sum(acc[j][l][f], hi, s, e);
-              lo += e;
-              hi = s;
-            }
-            const int sc = (f >= 2 ? eah : eal) + ebc[2 * j + (f & 1)] - 14;
-            hi = ldexpf(hi, sc);
-            lo = ldexpf(lo, sc);
+            float hi, lo;
+            combine_levels(acc[j][0][f], acc[j][1][f], acc[j][2][f], acc[j][3][f], acc[j][4][f], acc[j][5][f], hi,
+                           lo);
+            const float sc = (f >= 2 ? fah : fal) * fbc[2 * j + (f & 1)];
             float s, e;
-            two_sum(master[j][f].hi, hi, s, e);
-            e += master[j][f].lo + lo;
+            two_sum(master[j][f].hi, hi * sc, s, e);
+            e += master[j][f].lo + lo * sc;
             master[j][f].hi = s + e;
             master[j][f].lo = e - (master[j][f].hi - s);
           }
