@@ -99,6 +99,16 @@ int eig_spmm(int64_t n, const int32_t *rowptr, const int32_t *colind, const void
 int eig_gram(int64_t n, int a, int b, const void *U, int64_t ldu, const void *V, int64_t ldv,
              int arith, int sym, double *G, int64_t ldg, void *stream);
 
+/* ---- device status of the tensor-core products (no counterpart in the
+ * paper) ----------------------------------------------------------------
+ * The tcgen05 product kernels behind EIG_ARITH_DF64_TC bound every wait on
+ * their shared-memory barriers; a wait that runs out ends the kernel early
+ * (its results are then wrong) and records the fact on the device.  Returns
+ * EIG_ETIMEOUT if that happened since the last call (and clears the record),
+ * EIG_ECUDA if the record cannot be read, else EIG_OK.  Synchronises the
+ * current device.  eig_solve() checks it itself. */
+int eig_device_status(void);
+
 /* ---- allocation-free Gram product (no counterpart in the paper) ---------
  * Same product, arguments and result as eig_gram, for callers that cannot
  * allocate device memory while they run: a serving process that gave all of

@@ -28,7 +28,7 @@ FORMS = {"df64": 0, "f64": 1, "mixed": 2}
 EXPORTS = ("eig_convert", "eig_spmm", "eig_gram", "eig_gram_noalloc", "eig_block_update", "eig_residual",
            "eig_cholqr2", "eig_syev", "eig_hl_trick", "eig_options_default", "eig_create", "eig_solve",
            "eig_query", "eig_destroy", "eig_strerror", "eig_footprint", "eig_server_create", "eig_submit",
-           "eig_server_step", "eig_poll", "eig_release", "eig_server_destroy")
+           "eig_server_step", "eig_poll", "eig_release", "eig_server_destroy", "eig_device_status")
 
 
 class EigError(RuntimeError):
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH):
         "eig_spmm": [i64, p, p, p, i32, i32, p, i64, p, i64, d, d, p, i64, d, p],
         "eig_gram": [i64, i32, i32, p, i64, p, i64, i32, i32, p, i64, p],
         "eig_gram_noalloc": [i64, i32, i32, p, i64, p, i64, i32, i32, p, i64, p],
+        "eig_device_status": [],
         "eig_block_update": [i64, i32, i32, p, i64, p, i64, p, i64, d, i32, p],
         "eig_residual": [i64, i32, p, i64, p, i64, p, p, p, i64, p, p, i32, p],
         "eig_cholqr2": [i64, i32, p, i64, i32, C.POINTER(C.c_int), p],
@@ -183,6 +184,12 @@ def eig_spmm(n, rowptr, colind, val, dtype, w, V, ldv, Y, ldy, alpha=1.0, beta=0
 def eig_gram(n, a, b, U, ldu, V, ldv, arith, sym, G, ldg, stream=None):
     return _check("eig_gram", load().eig_gram(n, a, b, _ptr(U), ldu, _ptr(V), ldv, arith, int(sym), _ptr(G), ldg,
                                               _stream(stream)))
+
+
+def device_status():
+    """EIG_ETIMEOUT if a bounded wait inside a tensor-core product ran out
+    since the last call (clears it), else 0; synchronises the device."""
+    return int(load().eig_device_status())
 
 
 def eig_gram_noalloc(n, a, b, U, ldu, V, ldv, arith, sym, G, ldg, stream=None):

@@ -5,6 +5,7 @@
 
 #include "blocks.cuh"
 #include "small.cuh"
+#include "tc.cuh"
 
 using namespace eig;
 
@@ -177,6 +178,12 @@ int eig_spmm(int64_t n, const int32_t* rowptr, const int32_t* colind, const void
     case EIG_F32: return spmm_t<Arith::F32>(n, rowptr, colind, val, w, V, ldv, Y, ldy, alpha, beta, U, ldu, gamma, st);
     default: return EIG_EINVAL;
   }
+}
+
+int eig_device_status(void) {
+  if (cudaDeviceSynchronize() != cudaSuccess) return EIG_ECUDA;
+  const int v = tc::tc5_take_error();
+  return v < 0 ? EIG_ECUDA : (v ? EIG_ETIMEOUT : EIG_OK);
 }
 
 int eig_gram(int64_t n, int a, int b, const void* U, int64_t ldu, const void* V, int64_t ldv, int arith, int sym,

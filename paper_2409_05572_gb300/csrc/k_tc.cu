@@ -31,51 +31,45 @@
 //                    columns of one row of U (tc_slice_rows) and 64 rows of one
 //                    column of C (tc_slice_coef, from float64 C).
 //
-// Slice buffers hold [slice][32-K block][M][32] bf16, then one int exponent
-// per (chunk, row of the operand).  The product kernel streams 32-K blocks of
-// both operands into shared memory with cp.async (three stages), loads
-// m16n8k16 fragments with ldmatrix and issues 21 MMAs per fragment pair and
-// k-step (all slice pairs with i + j <= 5).  Gram: split-K partial tiles,
-// summed in a fixed order by the same reduction as the CUDA-core Gram.
-// Update: persistent CTAs walk the 64 x 64 output tiles, N fastest, and
-// write Y = P + beta Y in double-float.
+// The slice layout is described in tc.cuh.  Two product kernels read it:
+// the tcgen05 kernel of k_tc5.cu (default) and, in this file, an mma.sync
+// kernel (EIG_TC_KERNEL=mma selects it): it streams 32-K blocks of both
+// operands into shared memory with cp.async (three stages), loads m16n8k16
+// fragments with ldmatrix and issues 21 MMAs per fragment pair and k-step
+// (all slice pairs with i + j <= 5).  Gram: split-K partial tiles, summed in
+// a fixed order by the same reduction as the CUDA-core Gram.  Update:
+// persistent CTAs walk the 64 x 64 output tiles, N fastest, and write
+// Y = P + beta Y in double-float.
 //
 // Range: chunks whose maximum is below 2^-100 are treated as 0 (their
 // products are below 2^-100 times the other operand, far under the rounding
 // of any entry that matters); double-float itself has the float32 exponent
 // range.
-#include <cuda_bf16.h>
+#include <cstdlib>
+#include <cstring>
 
 #include "blocks.cuh"
+#include "tc.cuh"
 
 namespace eig {
 
+using namespace tc;
+
 namespace {
 
-constexpr int TC_S = 6;        // slices per value
-constexpr int TC_KB = 32;      // K indices per block (one pipeline stage)
-constexpr int TC_CH = 64;      // K indices per chunk (one exponent, one exact-level flush)
-constexpr int TC_KBC = TC_CH / TC_KB;
-constexpr int TC_T = 64;       // CTA tile: 64 rows of A x 64 rows of B
+constexpr int TC_T = 64;       // mma.sync CTA tile: 64 rows of A x 64 rows of B
 constexpr int TC_KP = 40;      // padded pitch (bf16) of one row's 32 K values in shared memory
 constexpr int TC_NST = 3;      // pipeline stages
-constexpr int TC_OPND = TC_S * TC_T * TC_KP;  // bf16 elements per operand and stage
+constexpr int TC_OPND = S * TC_T * TC_KP;  // bf16 elements per operand and stage
 constexpr int TC_STAGE = 2 * TC_OPND;
 constexpr size_t TC_SHM = size_t(TC_NST) * TC_STAGE * sizeof(__nv_bfloat16);
-constexpr int TC_ZERO = -1000;  // exponent mark of an all-zero chunk
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float z = s - a;
-  e = (a - (s - z)) + (b - z);
-}
 
 // slices of one double-float value, scaled by `scale` (a power of two)
 __device__ __forceinline__ void cut(float hv, float lv, float scale, float* s) {
   hv *= scale;
   lv *= scale;
 #pragma unroll
-  for (int q = 0; q < TC_S; ++q) {
+  for (int q = 0; q < S; ++q) {
     const float r = rintf(hv);
     s[q] = r;
     float nh, nl;
@@ -85,60 +79,33 @@ __device__ __forceinline__ void cut(float hv, float lv, float scale, float* s) {
   }
 }
 
-// (hi, lo) = sum_l a_l 2^(-8 l) for exact integer level sums |a_l| < 2^23:
-// the two leading terms error-free (TwoSum), the rest into lo.  With
-// |a_0| <= 2^20 (one product per K index), |lo| < 2^-1 and the four roundings
-// of lo stay below 2^-24, i.e. 2^-44 of the largest possible chunk sum.
-__device__ __forceinline__ void combine_levels(float a0, float a1, float a2, float a3, float a4, float a5,
-                                               float& hi, float& lo) {
-  float h, e1, e2;
-  two_sum(a0, a1 * 0x1p-8f, h, e1);
-  two_sum(h, a2 * 0x1p-16f, hi, e2);
-  lo = e1 + e2;
-  lo = fmaf(a3, 0x1p-24f, lo);
-  lo = fmaf(a4, 0x1p-32f, lo);
-  lo = fmaf(a5, 0x1p-40f, lo);
-}
-
-// 2^k by its bit pattern; k > 127 (a float64 coefficient beyond the float
-// range) gives +inf, k < -126 gives 0
-__device__ __forceinline__ float pow2(int k) {
-  return k > 127 ? __int_as_float(0x7f800000) : (k < -126 ? 0.f : __int_as_float((k + 127) << 23));
-}
-
 __device__ __forceinline__ int chunk_exp(float mx) {
-  int e = TC_ZERO;
+  int e = ZERO_EXP;
   if (mx >= 0x1p-100f) frexpf(mx, &e);  // 2^(e-1) <= mx < 2^e
   return e;
 }
 
-__device__ __forceinline__ float exp_scale(int e) { return e == TC_ZERO ? 0.f : ldexpf(1.0f, 7 - e); }
+__device__ __forceinline__ float exp_scale(int e) { return e == ZERO_EXP ? 0.f : ldexpf(1.0f, 7 - e); }
 
-// 16 slices values of one slice (two rows of 8) -> 2 x 16 bytes
-__device__ __forceinline__ void store16(__nv_bfloat16* dst, const float (*v)[TC_S], int q) {
+// the 16 values v[0..15][q] of one row, K indices k0 .. k0 + 15 (k0 a
+// multiple of 16) of one block -> two 16-byte core-matrix rows
+__device__ __forceinline__ void store16(__nv_bfloat16* blk, int64_t r, int k0, const float (*v)[S], int q) {
   uint32_t p[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * i][q], v[2 * i + 1][q]);
     p[i] = *reinterpret_cast<const uint32_t*>(&b);
   }
-  uint4* d = reinterpret_cast<uint4*>(dst);
-  d[0] = make_uint4(p[0], p[1], p[2], p[3]);
-  d[1] = make_uint4(p[4], p[5], p[6], p[7]);
+  *reinterpret_cast<uint4*>(blk + in_block(r, k0)) = make_uint4(p[0], p[1], p[2], p[3]);
+  *reinterpret_cast<uint4*>(blk + in_block(r, k0 + 8)) = make_uint4(p[4], p[5], p[6], p[7]);
 }
 
 // ---------------------------------------------------------------------------
-// Slicing.  CTA = one 64 x 64 square of the block (one chunk x 64 operand
-// rows), 256 threads; staged through shared memory so that both the read of
-// the row-major block and the write of the slice layout are coalesced.
+// Slicing.  CTA = one 64 x 64 square (one chunk x 64 operand rows), 256
+// threads; staged through shared memory so that both the read of the
+// row-major block and the write of the slice layout are coalesced.  The
+// grids cover the padded operand rows, which get zero slices.
 // ---------------------------------------------------------------------------
-struct SliceOut {
-  __nv_bfloat16* sl;  // [TC_S][nkb][M][32]
-  int* ex;            // [nkc][M]
-  int64_t nkb;
-  int64_t M;
-};
-
 __device__ __forceinline__ void col_lookup(const Blk<dd>& U, int c, const dd*& p, int64_t& ld) {
   int s = 0;
   while (s + 1 < U.nseg && c >= U.start[s + 1]) ++s;
@@ -147,14 +114,14 @@ __device__ __forceinline__ void col_lookup(const Blk<dd>& U, int c, const dd*& p
 }
 
 // Gram operand: K = rows of U, operand rows = columns of U
-__global__ void __launch_bounds__(256) tc_slice_cols_kernel(int64_t n, Blk<dd> U, SliceOut o, const int* gate) {
+__global__ void __launch_bounds__(256) tc_slice_cols_kernel(int64_t n, Blk<dd> U, Layout o, const int* gate) {
   if (gate && *gate == 0) return;
   const int w = U.width;
   const int c0 = blockIdx.x * 64;
   const int64_t kc = blockIdx.y;
-  const int64_t r0 = kc * TC_CH;
-  __shared__ float shi[TC_CH][65];
-  __shared__ float slo[TC_CH][65];
+  const int64_t r0 = kc * CH;
+  __shared__ float shi[CH][65];
+  __shared__ float slo[CH][65];
   __shared__ float pmax[4][64];
   __shared__ int sexp[64];
   const int t = threadIdx.x;
@@ -166,7 +133,7 @@ __global__ void __launch_bounds__(256) tc_slice_cols_kernel(int64_t n, Blk<dd> U
     if (c < w) col_lookup(U, c, colp, cld);
     float m = 0.f;
 #pragma unroll 4
-    for (int i = 0; i < TC_CH / 4; ++i) {
+    for (int i = 0; i < CH / 4; ++i) {
       const int rr = lr + 4 * i;
       const int64_t r = r0 + rr;
       dd x = {0.f, 0.f};
@@ -182,29 +149,28 @@ __global__ void __launch_bounds__(256) tc_slice_cols_kernel(int64_t n, Blk<dd> U
     const float mm = fmaxf(fmaxf(pmax[0][t], pmax[1][t]), fmaxf(pmax[2][t], pmax[3][t]));
     const int e = chunk_exp(mm);
     sexp[t] = e;
-    if (c0 + t < w) o.ex[kc * o.M + c0 + t] = e == TC_ZERO ? 0 : e;
+    o.ex[kc * o.Mp + c0 + t] = e == ZERO_EXP ? 0 : e;
   }
   __syncthreads();
   // thread -> (K block kbl, operand row col, K values k0 .. k0 + 15)
   const int kbl = t >> 7, col = (t & 127) >> 1, k0 = (t & 1) * 16;
   const int c = c0 + col;
-  if (c >= w) return;
   const float scale = exp_scale(sexp[col]);
-  float v[16][TC_S];
+  float v[16][S];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) cut(shi[kbl * TC_KB + k0 + i][col], slo[kbl * TC_KB + k0 + i][col], scale, v[i]);
-  const int64_t kb = kc * TC_KBC + kbl;
+  for (int i = 0; i < 16; ++i) cut(shi[kbl * KB + k0 + i][col], slo[kbl * KB + k0 + i][col], scale, v[i]);
+  const int64_t kb = kc * KBC + kbl;
 #pragma unroll
-  for (int q = 0; q < TC_S; ++q) store16(o.sl + ((q * o.nkb + kb) * o.M + c) * TC_KB + k0, v, q);
+  for (int q = 0; q < S; ++q) store16(o.sl + o.block(q, kb), c, k0, v, q);
 }
 
 // Update operand A: K = columns of U, operand rows = rows of U
-__global__ void __launch_bounds__(256) tc_slice_rows_kernel(int64_t n, Blk<dd> U, SliceOut o, const int* gate) {
+__global__ void __launch_bounds__(256) tc_slice_rows_kernel(int64_t n, Blk<dd> U, Layout o, const int* gate) {
   if (gate && *gate == 0) return;
   const int w = U.width;
   const int64_t r0 = int64_t(blockIdx.x) * 64;
   const int kc = blockIdx.y;
-  const int k00 = kc * TC_CH;
+  const int k00 = kc * CH;
   __shared__ float shi[64][65];
   __shared__ float slo[64][65];
   __shared__ int sexp[64];
@@ -237,32 +203,31 @@ __global__ void __launch_bounds__(256) tc_slice_rows_kernel(int64_t n, Blk<dd> U
     if (part == 0) {
       const int e = chunk_exp(m);
       sexp[row] = e;
-      if (r0 + row < n) o.ex[int64_t(kc) * o.M + r0 + row] = e == TC_ZERO ? 0 : e;
+      o.ex[int64_t(kc) * o.Mp + r0 + row] = e == ZERO_EXP ? 0 : e;
     }
   }
   __syncthreads();
   const int kbl = t >> 7, row = (t & 127) >> 1, k0 = (t & 1) * 16;
   const int64_t r = r0 + row;
-  if (r >= n) return;
   const float scale = exp_scale(sexp[row]);
-  float v[16][TC_S];
+  float v[16][S];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) cut(shi[row][kbl * TC_KB + k0 + i], slo[row][kbl * TC_KB + k0 + i], scale, v[i]);
-  const int64_t kb = int64_t(kc) * TC_KBC + kbl;
+  for (int i = 0; i < 16; ++i) cut(shi[row][kbl * KB + k0 + i], slo[row][kbl * KB + k0 + i], scale, v[i]);
+  const int64_t kb = int64_t(kc) * KBC + kbl;
 #pragma unroll
-  for (int q = 0; q < TC_S; ++q) store16(o.sl + ((q * o.nkb + kb) * o.M + r) * TC_KB + k0, v, q);
+  for (int q = 0; q < S; ++q) store16(o.sl + o.block(q, kb), r, k0, v, q);
 }
 
 // Update operand B from float64 C (s x c, ldc) times scale: K = rows of C,
 // operand rows = columns of C.  Cut in float64 (exact: each step removes the
 // integer part of a value with at most 53 significant bits).
 __global__ void __launch_bounds__(256) tc_slice_coef_kernel(int s, int c, const double* __restrict__ C, int64_t ldc,
-                                                            double scale, SliceOut o, const int* gate) {
+                                                            double scale, Layout o, const int* gate) {
   if (gate && *gate == 0) return;
   const int j0 = blockIdx.x * 64;
   const int kc = blockIdx.y;
-  const int k00 = kc * TC_CH;
-  __shared__ double sc[TC_CH][65];
+  const int k00 = kc * CH;
+  __shared__ double sc[CH][65];
   __shared__ double pmax[4][64];
   __shared__ int sexp[64];
   const int t = threadIdx.x;
@@ -270,7 +235,7 @@ __global__ void __launch_bounds__(256) tc_slice_coef_kernel(int s, int c, const 
     const int lj = t & 63, lk = t >> 6;
     const int j = j0 + lj;
     double m = 0.0;
-    for (int i = 0; i < TC_CH / 4; ++i) {
+    for (int i = 0; i < CH / 4; ++i) {
       const int kk = lk + 4 * i;
       const int k = k00 + kk;
       const double x = (j < c && k < s) ? scale * C[int64_t(k) * ldc + j] : 0.0;
@@ -282,34 +247,33 @@ __global__ void __launch_bounds__(256) tc_slice_coef_kernel(int s, int c, const 
   __syncthreads();
   if (t < 64) {
     const double mm = fmax(fmax(pmax[0][t], pmax[1][t]), fmax(pmax[2][t], pmax[3][t]));
-    int e = TC_ZERO;
+    int e = ZERO_EXP;
     if (mm >= 0x1p-100) frexp(mm, &e);
     sexp[t] = e;
-    if (j0 + t < c) o.ex[int64_t(kc) * o.M + j0 + t] = e == TC_ZERO ? 0 : e;
+    o.ex[int64_t(kc) * o.Mp + j0 + t] = e == ZERO_EXP ? 0 : e;
   }
   __syncthreads();
   const int kbl = t >> 7, col = (t & 127) >> 1, k0 = (t & 1) * 16;
   const int j = j0 + col;
-  if (j >= c) return;
   const int e = sexp[col];
-  float v[16][TC_S];
+  float v[16][S];
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
-    double x = e == TC_ZERO ? 0.0 : ldexp(sc[kbl * TC_KB + k0 + i][col], 7 - e);
+    double x = e == ZERO_EXP ? 0.0 : ldexp(sc[kbl * KB + k0 + i][col], 7 - e);
 #pragma unroll
-    for (int q = 0; q < TC_S; ++q) {
+    for (int q = 0; q < S; ++q) {
       const double r = rint(x);
       v[i][q] = float(r);
       x = (x - r) * 256.0;
     }
   }
-  const int64_t kb = int64_t(kc) * TC_KBC + kbl;
+  const int64_t kb = int64_t(kc) * KBC + kbl;
 #pragma unroll
-  for (int q = 0; q < TC_S; ++q) store16(o.sl + ((q * o.nkb + kb) * o.M + j) * TC_KB + k0, v, q);
+  for (int q = 0; q < S; ++q) store16(o.sl + o.block(q, kb), j, k0, v, q);
 }
 
 // ---------------------------------------------------------------------------
-// product kernel
+// mma.sync product kernel
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
   asm volatile(
@@ -326,33 +290,15 @@ __device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
                : "r"(s));
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  const int nb = pred ? 16 : 0;  // 0: zero-fill, nothing read
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(nb));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
-
-struct Opnd {
-  const __nv_bfloat16* sl;  // [TC_S][nkb][M][32]
-  const int* ex;            // [nkc][M]
-  int64_t M;
-};
-
-struct GramOut {
-  double* part;  // [split][M_A][M_B]
-  bool sym;
-};
-
-struct UpdOut {
-  Blk<dd> Y;
-  dd beta;
-  bool has_beta;
-};
 
 // MODE 0: Gram (one item per CTA: tile (blockIdx.y, blockIdx.x), K blocks
 // [z * kb_per, (z + 1) * kb_per) of split z = blockIdx.z).
@@ -386,24 +332,25 @@ __global__ void __launch_bounds__(512, 1) tc_product_kernel(Opnd A, Opnd B, int 
     kb0 = 0;
     nkb_item = nkb;
   }
-  if (nkb_item == 0) nitem_cta = MODE == 0 ? nitem_cta : 0;
+  if (nkb_item == 0 && MODE == 1) nitem_cta = 0;
 
+  // operand rows are padded to a multiple of 128 with zero slices, so every
+  // 64-row tile is in bounds
   auto load_stage = [&](int it, int kbi, int buf) {
     const int item = item0 + it * item_step;
     const int64_t kb = kb0 + kbi;
     const int64_t m0 = int64_t(item / tiles_n) * TC_T, n0 = int64_t(item % tiles_n) * TC_T;
     __nv_bfloat16* dst = sm + buf * TC_STAGE;
 #pragma unroll
-    for (int i = 0; i < (TC_S * TC_T * 4) / 512; ++i) {
+    for (int i = 0; i < (S * TC_T * 4) / 512; ++i) {
       const int id = t + 512 * i;
       const int q = id / (TC_T * 4);
       const int rem = id % (TC_T * 4);
       const int col = rem >> 2, piece = rem & 3;
-      const int64_t ra = m0 + col, rb = n0 + col;
-      const __nv_bfloat16* ga = A.sl + ((q * int64_t(nkb) + kb) * A.M + (ra < A.M ? ra : 0)) * TC_KB + piece * 8;
-      const __nv_bfloat16* gb = B.sl + ((q * int64_t(nkb) + kb) * B.M + (rb < B.M ? rb : 0)) * TC_KB + piece * 8;
-      cp_async16(dst + (q * TC_T + col) * TC_KP + piece * 8, ga, ra < A.M);
-      cp_async16(dst + TC_OPND + (q * TC_T + col) * TC_KP + piece * 8, gb, rb < B.M);
+      const __nv_bfloat16* ga = A.sl + (int64_t(q) * nkb + kb) * A.Mp * KB + in_block(m0 + col, piece * 8);
+      const __nv_bfloat16* gb = B.sl + (int64_t(q) * nkb + kb) * B.Mp * KB + in_block(n0 + col, piece * 8);
+      cp_async16(dst + (q * TC_T + col) * TC_KP + piece * 8, ga);
+      cp_async16(dst + TC_OPND + (q * TC_T + col) * TC_KP + piece * 8, gb);
     }
   };
 
@@ -440,7 +387,7 @@ __global__ void __launch_bounds__(512, 1) tc_product_kernel(Opnd A, Opnd B, int 
     const int64_t rl = m0 + am + g, rh = rl + 8;
     for (int kbi = 0; kbi < nkb_item; ++kbi) {
       const int kb = kb0 + kbi;
-      if (kb % TC_KBC == 0 || kbi == 0) {
+      if (kb % KBC == 0 || kbi == 0) {
 #pragma unroll
         for (int j = 0; j < 2; ++j)
 #pragma unroll
@@ -462,34 +409,31 @@ __global__ void __launch_bounds__(512, 1) tc_product_kernel(Opnd A, Opnd B, int 
       const __nv_bfloat16* stg = sm + buf * TC_STAGE;
       buf = buf + 1 == TC_NST ? 0 : buf + 1;
 #pragma unroll
-      for (int ks = 0; ks < TC_KB; ks += 16) {
-        uint32_t bf[TC_S][4];
+      for (int ks = 0; ks < KB; ks += 16) {
+        uint32_t bf[S][4];
 #pragma unroll
-        for (int q = 0; q < TC_S; ++q) ldsm_x4(bf[q], stg + b_off + q * TC_T * TC_KP + ks);
+        for (int q = 0; q < S; ++q) ldsm_x4(bf[q], stg + b_off + q * TC_T * TC_KP + ks);
 #pragma unroll
-        for (int qi = 0; qi < TC_S; ++qi) {
+        for (int qi = 0; qi < S; ++qi) {
           uint32_t af[4];
           ldsm_x4(af, stg + a_off + qi * TC_T * TC_KP + ks);
 #pragma unroll
-          for (int qj = 0; qj < TC_S - qi; ++qj) {
+          for (int qj = 0; qj < S - qi; ++qj) {
             mma_bf16(acc[0][qi + qj], af, bf[qj][0], bf[qj][1]);
             mma_bf16(acc[1][qi + qj], af, bf[qj][2], bf[qj][3]);
           }
         }
       }
       const bool last = kbi + 1 == nkb_item;
-      if (kb % TC_KBC == TC_KBC - 1 || last) {
+      if (kb % KBC == KBC - 1 || last) {
         // chunk done: value = sum_l acc_l 2^(-8 l) (exact integers per
-        // level), times 2^(e_a + e_b - 14), added to the double-float master
-        const int64_t kc = kb / TC_KBC;
-        const float fal = pow2(rl < A.M ? A.ex[kc * A.M + rl] - 7 : 0);
-        const float fah = pow2(rh < A.M ? A.ex[kc * A.M + rh] - 7 : 0);
+        // level), times 2^(e_a - 7) 2^(e_b - 7), into the double-float master
+        const int64_t kc = kb / KBC;
+        const float fal = pow2(A.ex[kc * A.Mp + rl] - 7);
+        const float fah = pow2(A.ex[kc * A.Mp + rh] - 7);
         float fbc[4];
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          const int64_t cb = n0 + bn + 8 * (f >> 1) + 2 * tq + (f & 1);
-          fbc[f] = pow2(cb < B.M ? B.ex[kc * B.M + cb] - 7 : 0);
-        }
+        for (int f = 0; f < 4; ++f) fbc[f] = pow2(B.ex[kc * B.Mp + n0 + bn + 8 * (f >> 1) + 2 * tq + (f & 1)] - 7);
 #pragma unroll
         for (int j = 0; j < 2; ++j)
 #pragma unroll
@@ -497,12 +441,7 @@ __global__ void __launch_bounds__(512, 1) tc_product_kernel(Opnd A, Opnd B, int 
             float hi, lo;
             combine_levels(acc[j][0][f], acc[j][1][f], acc[j][2][f], acc[j][3][f], acc[j][4][f], acc[j][5][f], hi,
                            lo);
-            const float sc = (f >= 2 ? fah : fal) * fbc[2 * j + (f & 1)];
-            float s, e;
-            two_sum(master[j][f].hi, hi * sc, s, e);
-            e += master[j][f].lo + lo * sc;
-            master[j][f].hi = s + e;
-            master[j][f].lo = e - (master[j][f].hi - s);
+            add_scaled(master[j][f], hi, lo, (f >= 2 ? fah : fal) * fbc[2 * j + (f & 1)]);
           }
       }
     }
@@ -531,27 +470,11 @@ __global__ void __launch_bounds__(512, 1) tc_product_kernel(Opnd A, Opnd B, int 
   cp_async_wait<0>();
 }
 
-int64_t nkb_of(int64_t K) { return cdiv(K, TC_CH) * TC_KBC; }
-
-SliceOut slice_out(void* buf, int64_t K, int64_t M) {
-  SliceOut o;
-  o.nkb = nkb_of(K);
-  o.M = M;
-  o.sl = static_cast<__nv_bfloat16*>(buf);
-  o.ex = reinterpret_cast<int*>(o.sl + size_t(TC_S) * size_t(o.nkb) * size_t(M) * TC_KB);
-  return o;
-}
-
-Opnd opnd(const void* buf, int64_t K, int64_t M) {
-  SliceOut s = slice_out(const_cast<void*>(buf), K, M);
-  return Opnd{s.sl, s.ex, M};
-}
-
 int gram_tc_nsplit(int64_t n, int a, int b, bool sym) {
   const int ta = (a + TC_T - 1) / TC_T, tb = (b + TC_T - 1) / TC_T;
   const int tiles = (sym && ta == tb) ? ta * (ta + 1) / 2 : ta * tb;
   int ns = num_sms() / tiles;  // one CTA per SM, one wave
-  const int64_t nch = cdiv(n, TC_CH);
+  const int64_t nch = cdiv(n, CH);
   if (ns > nch) ns = int(nch);
   if (ns < 1) ns = 1;
   return ns;
@@ -571,22 +494,43 @@ cudaError_t set_smem() {
   return cudaSuccess;
 }
 
+// EIG_TC_KERNEL=mma selects the mma.sync product kernel
+bool use_mma_sync() {
+  static const bool v = [] {
+    const char* e = std::getenv("EIG_TC_KERNEL");
+    return e && std::strcmp(e, "mma") == 0;
+  }();
+  return v;
+}
+
+UpdOut upd_out(const Blk<dd>& Y, double beta) {
+  UpdOut uo;
+  uo.Y = Y;
+  const float bh = float(beta);
+  uo.beta = dd{bh, float(beta - double(bh))};
+  uo.has_beta = beta != 0.0;
+  return uo;
+}
+
 }  // namespace
 
 size_t tc_slice_bytes(int64_t K, int64_t M) {
-  const size_t sb = sizeof(__nv_bfloat16) * size_t(TC_S) * size_t(nkb_of(K)) * size_t(M) * TC_KB;
-  return sb + sizeof(int) * size_t(cdiv(K, TC_CH)) * size_t(M);
+  const size_t mp = size_t(mpad_of(M));
+  const size_t sb = sizeof(__nv_bfloat16) * size_t(S) * size_t(nkb_of(K)) * mp * KB;
+  return sb + sizeof(int) * size_t(cdiv(K, CH)) * mp;
 }
 
 size_t gram_tc_scratch_elems(int64_t n, int a, int b, bool sym) {
-  return size_t(gram_tc_nsplit(n, a, b, sym)) * size_t(a) * size_t(b);
+  const int ns = std::max(gram_tc_nsplit(n, a, b, sym), tc5_gram_nsplit(n, a, b, sym));
+  return size_t(ns) * size_t(a) * size_t(b);
 }
 
 cudaError_t tc_slice_cols(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t st, const int* gate) {
   const int w = U.width;
   if (w <= 0 || n <= 0) return cudaSuccess;
-  dim3 grid((w + 63) / 64, (unsigned)cdiv(n, TC_CH));
-  tc_slice_cols_kernel<<<grid, 256, 0, st>>>(n, U, slice_out(buf, n, w), gate);
+  const Layout o = layout(buf, n, w);
+  dim3 grid((unsigned)(o.Mp / 64), (unsigned)cdiv(n, CH));
+  tc_slice_cols_kernel<<<grid, 256, 0, st>>>(n, U, o, gate);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -594,8 +538,9 @@ cudaError_t tc_slice_cols(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t s
 cudaError_t tc_slice_rows(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t st, const int* gate) {
   const int w = U.width;
   if (w <= 0 || n <= 0) return cudaSuccess;
-  dim3 grid((unsigned)cdiv(n, 64), (unsigned)cdiv(w, TC_CH));
-  tc_slice_rows_kernel<<<grid, 256, 0, st>>>(n, U, slice_out(buf, w, n), gate);
+  const Layout o = layout(buf, w, n);
+  dim3 grid((unsigned)(o.Mp / 64), (unsigned)cdiv(w, CH));
+  tc_slice_rows_kernel<<<grid, 256, 0, st>>>(n, U, o, gate);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -603,8 +548,9 @@ cudaError_t tc_slice_rows(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t s
 cudaError_t tc_slice_coef(int s, int c, const double* C, int64_t ldc, double scale, void* buf, cudaStream_t st,
                           const int* gate) {
   if (s <= 0 || c <= 0) return cudaSuccess;
-  dim3 grid((c + 63) / 64, (unsigned)cdiv(s, TC_CH));
-  tc_slice_coef_kernel<<<grid, 256, 0, st>>>(s, c, C, ldc, scale, slice_out(buf, s, c), gate);
+  const Layout o = layout(buf, s, c);
+  dim3 grid((unsigned)(o.Mp / 64), (unsigned)cdiv(s, CH));
+  tc_slice_coef_kernel<<<grid, 256, 0, st>>>(s, c, C, ldc, scale, o, gate);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -612,26 +558,34 @@ cudaError_t tc_slice_coef(int s, int c, const double* C, int64_t ldc, double sca
 cudaError_t gram_tc_product(int64_t n, int a, int b, const void* slu, const void* slv, bool sym, double* G,
                             int64_t ldg, double* scratch, cudaStream_t st, const int* gate) {
   if (a <= 0 || b <= 0 || n <= 0) return cudaSuccess;
-  cudaError_t e = set_smem<0>();
-  if (e != cudaSuccess) return e;
-  const int64_t nkb = nkb_of(n);
-  const int ns = gram_tc_nsplit(n, a, b, sym);
-  const int64_t kb_per = cdiv(cdiv(n, TC_CH), ns) * TC_KBC;
-  const int tm = (a + TC_T - 1) / TC_T, tn = (b + TC_T - 1) / TC_T;
-  GramOut go{scratch, sym};
-  UpdOut uo{};
-  dim3 grid(tn, tm, ns);
-  tc_product_kernel<0><<<grid, 512, TC_SHM, st>>>(opnd(slu, n, a), opnd(slv, n, b), int(nkb), int(kb_per), tn,
-                                                  tm * tn, go, uo, gate);
-  count_launches(1);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  int ns;
+  if (use_mma_sync()) {
+    cudaError_t e = set_smem<0>();
+    if (e != cudaSuccess) return e;
+    const int64_t nkb = nkb_of(n);
+    ns = gram_tc_nsplit(n, a, b, sym);
+    const int64_t kb_per = cdiv(cdiv(n, CH), ns) * KBC;
+    const int tm = (a + TC_T - 1) / TC_T, tn = (b + TC_T - 1) / TC_T;
+    GramOut go{scratch, sym};
+    UpdOut uo{};
+    dim3 grid(tn, tm, ns);
+    tc_product_kernel<0><<<grid, 512, TC_SHM, st>>>(opnd(slu, n, a), opnd(slv, n, b), int(nkb), int(kb_per), tn,
+                                                    tm * tn, go, uo, gate);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  } else {
+    ns = tc5_gram_nsplit(n, a, b, sym);
+    cudaError_t e = tc5_gram(n, a, b, slu, slv, sym, scratch, ns, st, gate);
+    if (e != cudaSuccess) return e;
+  }
   return gram_reduce(a, b, ns, sym, scratch, G, ldg, st, gate);
 }
 
 cudaError_t update_tc_product(int64_t n, int s, int c, const void* slu, const void* slc, const Blk<dd>& Y,
                               double beta, cudaStream_t st, const int* gate) {
   if (n <= 0 || c <= 0) return cudaSuccess;
+  if (!use_mma_sync()) return tc5_update(n, s, c, slu, slc, Y, beta, st, gate);
   cudaError_t e = set_smem<1>();
   if (e != cudaSuccess) return e;
   const int64_t nkb = nkb_of(s);
@@ -641,13 +595,8 @@ cudaError_t update_tc_product(int64_t n, int s, int c, const void* slu, const vo
   int64_t grid = num_sms();
   if (grid > items) grid = items;
   GramOut go{};
-  UpdOut uo;
-  uo.Y = Y;
-  const float bh = float(beta);
-  uo.beta = dd{bh, float(beta - double(bh))};
-  uo.has_beta = beta != 0.0;
   tc_product_kernel<1><<<(unsigned)grid, 512, TC_SHM, st>>>(opnd(slu, s, n), opnd(slc, s, c), int(nkb), int(nkb),
-                                                            tn, int(items), go, uo, gate);
+                                                            tn, int(items), go, upd_out(Y, beta), gate);
   count_launches(1);
   return cudaGetLastError();
 }

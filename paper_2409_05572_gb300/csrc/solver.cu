@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "blocks.cuh"
+#include "tc.cuh"
 #include "small.cuh"
 
 using namespace eig;
@@ -1451,6 +1452,10 @@ int eig_solve(eig_handle* h) {
   const int64_t l0 = launches_total();
   int rc = solve_impl(h);
   cudaStreamSynchronize(h->st);
+  if (h->tcU) {  // a bounded wait of a tensor-core product ran out
+    const int v = tc::tc5_take_error();
+    if (v != 0 && rc == EIG_OK) rc = v > 0 ? EIG_ETIMEOUT : EIG_ECUDA;
+  }
   prof_flush(h);
   auto t1 = std::chrono::steady_clock::now();
   h->time_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();

@@ -191,6 +191,7 @@ def tc_gram(U, V, sym, ldu_pad=0, ldv_pad=0):
         Vd = L.to_df64(dev(Vp))
     G = torch.full((a, b + 2), 9.0, dtype=torch.float64, device="cuda")
     L.eig_gram(n, a, b, Ud, a + ldu_pad, Vd, b + ldv_pad, L.ARITH_DF64_TC, sym, G, b + 2)
+    assert L.device_status() == 0   # no bounded wait of the product kernel ran out
     assert torch.all(G[:, b:] == 9.0)
     return G[:, :b].cpu().numpy()
 
@@ -311,6 +312,7 @@ def test_update_tc_parity(n, s, c, beta):
     Ud = L.to_df64(dev(U))
     Yd = L.to_df64(dev(Y0))
     L.eig_block_update(n, s, c, Ud, s, dev(Cm), c, Yd, c, beta, L.ARITH_DF64_TC)
+    assert L.device_status() == 0
     got = L.from_df64(Yd).cpu().numpy()
     ref = U @ Cm + beta * Y0
     Mu, cnt = row_chunk_max(U)
