@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256) tc_slice_cols_kernel(int64_t n, Blk<dd> U
     int64_t cld = 0;
     if (c < w) col_lookup(U, c, colp, cld);
     float m = 0.f;
-#pragma unroll 4
+#pragma unroll
     for (int i = 0; i < CH / 4; ++i) {
       const int rr = lr + 4 * i;
       const int64_t r = r0 + rr;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) tc_slice_rows_kernel(int64_t n, Blk<dd> U
     const dd* colp = nullptr;
     int64_t cld = 0;
     if (c < w) col_lookup(U, c, colp, cld);
-#pragma unroll 4
+#pragma unroll
     for (int i = 0; i < 16; ++i) {
       const int rr = lr + 4 * i;
       const int64_t r = r0 + rr;

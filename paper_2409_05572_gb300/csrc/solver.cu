@@ -734,16 +734,28 @@ int lob_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switch
     void* ASn = h->AS[nx];
     {
       using SU = typename Pol<AU>::S;
-      SU* Cs = static_cast<SU*>(h->Cs);
       const int c = L.nnow + npn;
-      {
-        Prof p(h, EIG_K_OTHER, 0.0, 0.0);
-        CK(stage_coef<AU>(s, L.nnow, h->Z, s, Cs, c, 1.0, h->st));
-        CK(stage_coef<AU>(s, npn, h->CP, npn, Cs + L.nnow, c, 1.0, h->st));
-      }
       Blk<T> Yn = cat(view<T>(Sn, ld, 0, L.nnow), view<T>(Sn, ld, k, npn));
-      const double fl = 2.0 * double(h->n) * s * c, by = Ops<AU, AG>::E * double(h->n) * (s + c);
-      {
+      if (AU == Arith::DF64 && h->tcU) {
+        // tensor-core update: C = [Z(:, :nnow) | C_P] as one float64 s x c
+        // matrix (the staging buffer holds smax x (2 k_max + 1) 8-byte values)
+        double* Cm = static_cast<double*>(h->Cs);
+        {
+          Prof p(h, EIG_K_OTHER, 0.0, 0.0);
+          CK(cudaMemcpy2DAsync(Cm, sizeof(double) * c, h->Z, sizeof(double) * s, sizeof(double) * L.nnow, s,
+                               cudaMemcpyDeviceToDevice, h->st));
+          CK(cudaMemcpy2DAsync(Cm + L.nnow, sizeof(double) * c, h->CP, sizeof(double) * npn, sizeof(double) * npn, s,
+                               cudaMemcpyDeviceToDevice, h->st));
+        }
+        if ((rc = o.upd(Sb, Cm, c, c, 1.0, Yn, 0.0))) return rc;
+      } else {
+        SU* Cs = static_cast<SU*>(h->Cs);
+        {
+          Prof p(h, EIG_K_OTHER, 0.0, 0.0);
+          CK(stage_coef<AU>(s, L.nnow, h->Z, s, Cs, c, 1.0, h->st));
+          CK(stage_coef<AU>(s, npn, h->CP, npn, Cs + L.nnow, c, 1.0, h->st));
+        }
+        const double fl = 2.0 * double(h->n) * s * c, by = Ops<AU, AG>::E * double(h->n) * (s + c);
         Prof p(h, EIG_K_UPDATE, fl, by);
         CK(eig::update<AU>(h->n, Sb, Cs, c, Yn, 0.0, h->st));
       }
