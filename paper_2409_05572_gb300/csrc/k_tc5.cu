@@ -10,9 +10,9 @@
 //                        4 KB per slice) into a 3-stage ring; each stage
 //                        completes an mbarrier by transaction count.
 //   warp 1, one thread   MMA issuer: per K block and 16-index half, the 21
-//                        slice pairs (i, j), i + j <= 5, as tcgen05.mma
-//                        (M = 128, N = 64, K = 16, bf16 in, fp32 out) into
-//                        the TMEM accumulator of level i + j (6 x 64
+//                        slice pairs (i, j), i + j <= 5, as eight tcgen05.mma
+//                        (M = 128, N = 64 .. 256, K = 16, bf16 in, fp32 out)
+//                        into the TMEM accumulators of the levels i + j (6 x 64
 //                        columns); tcgen05.commit frees the stage and, after
 //                        the second K block of a 64-index chunk, hands the
 //                        six exact level sums to the flush warps.
@@ -55,7 +55,9 @@ constexpr int THREADS = 32 * (2 + FLUSH_WARPS);
 constexpr size_t SMEM = size_t(NST) * STAGE + 1024;  // + alignment slack
 constexpr uint32_t LBO = 128, SBO = 512;
 // instruction descriptor: D f32, A and B bf16, both K-major, N >> 3, M >> 4
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+__host__ __device__ constexpr uint32_t idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+}
 constexpr uint64_t WAIT_NS = 2000000000ull;  // a wait gives up after 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -126,12 +128,33 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+      "l"(a), "l"(b), "r"(id), "r"(accumulate)
       : "memory");
+}
+
+// All slice pairs (qi, qj), qi + qj <= 5, of one 16-index K step.  The B
+// slices lie in shared memory one after another with the same 512-byte
+// row-group stride, so B slices qj .. qj + m - 1 form one operand of
+// N = 64 m rows; with D at TMEM column 64 qi, the product of A slice qi with
+// B slice qj lands in the columns of level qi + qj.  Eight MMAs (N <= 256)
+// cover the 21 pairs.  first: the first K step of a chunk (overwrite).
+__device__ __forceinline__ void mma_kstep(uint32_t tmem, uint32_t sa, uint32_t sb, bool first) {
+  const uint32_t acc = first ? 0u : 1u;
+  // qi = 0: levels 0..3 and 4..5 (these two start every level of the chunk)
+  mma(tmem + 0 * BN, sdesc(sa + 0 * A_SLICE), sdesc(sb + 0 * B_SLICE), idesc(4 * BN), acc);
+  mma(tmem + 4 * BN, sdesc(sa + 0 * A_SLICE), sdesc(sb + 4 * B_SLICE), idesc(2 * BN), acc);
+  // qi = 1: levels 1..4 and 5
+  mma(tmem + 1 * BN, sdesc(sa + 1 * A_SLICE), sdesc(sb + 0 * B_SLICE), idesc(4 * BN), 1u);
+  mma(tmem + 5 * BN, sdesc(sa + 1 * A_SLICE), sdesc(sb + 4 * B_SLICE), idesc(1 * BN), 1u);
+  // qi = 2 .. 5: levels qi .. 5
+  mma(tmem + 2 * BN, sdesc(sa + 2 * A_SLICE), sdesc(sb), idesc(4 * BN), 1u);
+  mma(tmem + 3 * BN, sdesc(sa + 3 * A_SLICE), sdesc(sb), idesc(3 * BN), 1u);
+  mma(tmem + 4 * BN, sdesc(sa + 4 * A_SLICE), sdesc(sb), idesc(2 * BN), 1u);
+  mma(tmem + 5 * BN, sdesc(sa + 5 * A_SLICE), sdesc(sb), idesc(1 * BN), 1u);
 }
 __device__ __forceinline__ void commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -139,18 +162,25 @@ __device__ __forceinline__ void commit(uint32_t bar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 16 consecutive TMEM columns of this thread's lane, waited for
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// 16 consecutive TMEM columns of this thread's lane in each of the six
+// level accumulators (64 columns apart), one wait for all six loads
+__device__ __forceinline__ void tmem_ld_levels(uint32_t taddr, float (*v)[16]) {
+  uint32_t r[96];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%96];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%97];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47}, [%98];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%99];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%64,%65,%66,%67,%68,%69,%70,%71,%72,%73,%74,%75,%76,%77,%78,%79}, [%100];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%80,%81,%82,%83,%84,%85,%86,%87,%88,%89,%90,%91,%92,%93,%94,%95}, [%101];\n"
       "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63]), "=r"(r[64]), "=r"(r[65]), "=r"(r[66]), "=r"(r[67]), "=r"(r[68]), "=r"(r[69]), "=r"(r[70]), "=r"(r[71]), "=r"(r[72]), "=r"(r[73]), "=r"(r[74]), "=r"(r[75]), "=r"(r[76]), "=r"(r[77]), "=r"(r[78]), "=r"(r[79]), "=r"(r[80]), "=r"(r[81]), "=r"(r[82]), "=r"(r[83]), "=r"(r[84]), "=r"(r[85]), "=r"(r[86]), "=r"(r[87]), "=r"(r[88]), "=r"(r[89]), "=r"(r[90]), "=r"(r[91]), "=r"(r[92]), "=r"(r[93]), "=r"(r[94]), "=r"(r[95])
+      : "r"(taddr), "r"(taddr + 64u), "r"(taddr + 128u), "r"(taddr + 192u), "r"(taddr + 256u), "r"(taddr + 320u)
       : "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int l = 0; l < 6; ++l)
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[l][i] = __uint_as_float(r[16 * l + i]);
 }
 
 // MODE 0: Gram (tile (blockIdx.y, blockIdx.x) of 128 x 64, K blocks
@@ -258,14 +288,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb
             if (!(ok = mbar_wait(smem_u32(&bar_full[s]), uint32_t((p / NST) & 1), abort))) break;
             fence_after();
             const uint32_t sa = base + uint32_t(s) * STAGE, sb = sa + S * A_SLICE;
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks)
-#pragma unroll
-              for (int qi = 0; qi < S; ++qi)
-#pragma unroll
-                for (int qj = 0; qj < S - qi; ++qj)
-                  mma(tmem + uint32_t((qi + qj) * BN), sdesc(sa + qi * A_SLICE + ks * 256),
-                      sdesc(sb + qj * B_SLICE + ks * 256), (h | ks | qi) != 0 ? 1u : 0u);
+            mma_kstep(tmem, sa, sb, h == 0);
+            mma_kstep(tmem, sa + 256, sb + 256, false);
             commit(smem_u32(&bar_empty[s]));
           }
           if (ok) commit(smem_u32(&bar_accf));
@@ -299,8 +323,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb
 #pragma unroll
         for (int sub = 0; sub < 2; ++sub) {
           float v[6][16];
-#pragma unroll
-          for (int l = 0; l < 6; ++l) tmem_ld16(trow + uint32_t(l * BN + 32 * half + 16 * sub), v[l]);
+          tmem_ld_levels(trow + uint32_t(32 * half + 16 * sub), v);
           if (sub == 1) {  // TMEM read: the issuer may start the next chunk
             fence_before();
             __syncwarp();
