@@ -43,6 +43,9 @@ UNIT = "eigenpairs/s"
 # the small cases (profiles/gram_kernel_df64_n262144_384x384_sym.md and
 # profiles/update_kernel_df64_n262144_384x256.md); traffic grows with n.
 TRAFFIC_RATIO = {"gram": 1.387 / 0.805, "update": 1.447 / 1.342}
+# the same for the tensor-core classes (slicing + product kernels); empty
+# until the current kernels are captured
+TC_TRAFFIC_RATIO = {}
 
 
 def peaks():
@@ -51,6 +54,23 @@ def peaks():
         d = json.load(open(p))
         return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
     return 6800.0, 1900.0, "fallback"
+
+
+def bf16_sustained():
+    """Sustained bf16 tensor rate (TFLOP/s) for kernels timed inside a long
+    step: the measured seconds-long cuBLAS loop, else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        if "bf16_tflops_sustained" in d:
+            return d["bf16_tflops_sustained"], "measured (sustained cuBLAS bf16 GEMM)"
+    return 1700.0, "fallback (sustained)"
+
+
+# The tensor-core Gram and update cut each double-float operand into six
+# exact bf16 slices and form the 21 slice products of levels 0..5, i.e. 21
+# bf16 multiply-adds per double-float multiply-add.
+TC_MMA_PER_MAC = 21
 
 
 # FP32 issue rate measured on this pool's GB300 (152 SMs, FFMA, 72.6 TFLOP/s
@@ -311,6 +331,8 @@ def main():
     ap.add_argument("--requests", type=int, default=32, help="c5: requests replayed from the stream")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="c5: device memory for active solves")
     ap.add_argument("--max-active", type=int, default=64, help="c5: solves advanced per step")
+    ap.add_argument("--gram-tc", type=int, default=1, choices=[0, 1],
+                    help="1: double-float Gram and update on the tensor cores; 0: on the FP32 pipes")
     ap.add_argument("--max-iter", type=int, default=1000,
                     help="iteration cap per solve (profiling runs use a small cap)")
     ap.add_argument("--ref-iters", type=int, default=322,
@@ -344,7 +366,8 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     # stopping test of Eq. conv at tol/2 so that ||Av - lv|| / ||A|| <= tol holds
     algo = wl.get("algo", "lobpcg")
-    extra = wl.get("extra", {})
+    extra = dict(wl.get("extra", {}))
+    extra["gram_tc"] = args.gram_tc
     solver = L.Solver((rp, ci, va), nev=nev, k_max=k, strategy=args.strategy, X0=X0d, normA=normA,
                       tol=0.5 * tol, form=args.form, stream=stream, profile=1, max_iter=args.max_iter,
                       algo=algo, **extra)
@@ -389,6 +412,8 @@ def main():
             "vs_baseline": None, "dtype": args.form, "data": "synthetic",
             "config": {"workload": wl["desc"], "nev": nev, "k_max": k, "strategy": args.strategy,
                        "form": args.form, "tol": tol, "parallelism": f"replicas x{ws}",
+                       "products": "tensor cores (tcgen05, exact bf16 slices)" if (args.gram_tc and args.form != "f64")
+                       else "CUDA cores",
                        "l2": "inputs larger than L2 (each n x k block is 4.3 GB); no flush"},
             "converged": bool(ok), "iters": last["iters"], "n_shrink": last["n_shrink"],
             "n_expand": last["n_expand"], "max_resid": float(np.max(last["resid"])),
@@ -405,6 +430,18 @@ def main():
         ach = v["bytes"] / (v["ms"] / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "peak_source": src}
+    elif dom in ("gram", "update") and args.form != "f64" and extra.get("gram_tc", 1):
+        # tensor-core products: the bf16 MMA work the sliced method performs
+        # (21 slice products per double-float multiply-add) against the
+        # sustained bf16 peak; the class time includes the slicing passes
+        alg = v["flops"] / (v["ms"] / 1e3) / 1e12
+        ach = TC_MMA_PER_MAC * alg
+        pk, psrc = bf16_sustained()
+        roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk, "peak_source": psrc,
+                "df64_equivalent_tflops": alg,
+                "note": "achieved = 21 bf16 slice products per double-float multiply-add x algorithmic "
+                        "multiply-adds / class time (slicing passes included)"}
     else:
         ach = v["flops"] / (v["ms"] / 1e3) / 1e12
         pk = FP64_PEAK_TFLOPS if args.form == "f64" else DF64_PEAK_TFLOPS
@@ -414,12 +451,14 @@ def main():
                                "11.1 FP32 instructions per double-float multiply-add x 2"
                 if args.form != "f64" else "measured native FP64 FMA rate"}
     roof["avg_launch_ms"] = v["ms"] / max(v["launches"], 1)
-    if dom in TRAFFIC_RATIO and args.form == "df64":
+    tc_on = args.form != "f64" and extra.get("gram_tc", 1) != 0
+    ratios = TC_TRAFFIC_RATIO if tc_on else TRAFFIC_RATIO
+    if dom in ratios and args.form == "df64":
         # per launch, like achieved: algorithmic bytes of the class's average
         # launch x the DRAM/algorithmic ratio of the ncu capture
-        roof["traffic"] = TRAFFIC_RATIO[dom] * v["bytes"] / max(v["launches"], 1)
-        roof["traffic_source"] = (f"ncu dram__bytes_read+write of {dom}_kernel<DF64> at n=262144 "
-                                  f"(ratio {TRAFFIC_RATIO[dom]:.2f} to algorithmic bytes), scaled")
+        roof["traffic"] = ratios[dom] * v["bytes"] / max(v["launches"], 1)
+        roof["traffic_source"] = (f"ncu dram__bytes_read+write of the {dom} kernels at n=262144 "
+                                  f"(ratio {ratios[dom]:.2f} to algorithmic bytes), scaled")
     else:
         roof["traffic"] = None
     line["roofline"] = roof

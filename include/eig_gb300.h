@@ -168,8 +168,10 @@ int eig_syev(int s, const double *A, int64_t lda, double *lam, double *Z, int64_
 
 /* ---- a10: improved Hetmaniuk-Lehoucq basis selection (Algorithm 3) -----
  * Given all s eigenvectors Z (s x s, ascending), C_P = Z(:, nnow:s) Q with Q the
- * orthonormal Householder factor of Z(nlock:nnow, nnow:s)^T; CP is s x
- * (nnow - nlock) float64 row-major (device).  Requires s - nnow >= nnow - nlock. */
+ * orthonormal QR factor of Z(nlock:nnow, nnow:s)^T, computed by shifted
+ * CholeskyQR3 (Fukaya et al. 2020; for a full-rank block the Householder
+ * factor up to column signs); CP is s x (nnow - nlock) float64 row-major
+ * (device).  Requires s - nnow >= nnow - nlock. */
 int eig_hl_trick(int s, int nnow, int nlock, const double *Z, int64_t ldz, double *CP,
                  int64_t ldcp, void *stream);
 

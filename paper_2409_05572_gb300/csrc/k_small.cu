@@ -2,12 +2,16 @@
 // steps (arXiv:2409.05572, Algorithms 1 and 3):
 //   * Cholesky G = R^T R and R^{-1} for CholeskyQR (shifted variant of
 //     Fukaya et al. 2020 on breakdown),
-//   * the Householder QR and right-multiplication of the improved
-//     Hetmaniuk-Lehoucq basis selection.
+//   * the improved Hetmaniuk-Lehoucq basis selection (shifted CholeskyQR3 of
+//     a block of Z and the product with Z, built from the float64 Gram,
+//     Cholesky and update kernels).
 // These act on s x s matrices (s <= 3 k_max); they are latency / FP64-pipe
-// bound and run on a few SMs.
+// bound.
 #include <cstdio>
 
+#include <utility>
+
+#include "blocks.cuh"
 #include "small.cuh"
 
 namespace eig {
@@ -126,82 +130,53 @@ cudaError_t chol_rinv(int w, int64_t nrows, const double* G, int64_t ldg, double
 // ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // Improved Hetmaniuk-Lehoucq basis selection.
-// M = Z(nlock:nnow, nnow:s)^T  (m x q, m = s - nnow, q = nnow - nlock),
-// Householder QR M = Q R (one CTA), then CP = Z(:, nnow:s) H_0 ... H_{q-1}
-// restricted to its first q columns (one thread per row of Z).
+// Y = Z(nlock:nnow, nnow:s)^T  (m x q, m = s - nnow, q = nnow - nlock); its
+// orthonormal QR factor Q by shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa,
+// Yamamoto and Yanagisawa, SISC 2020): three passes of G = Y^T Y (float64
+// Gram), R^{-1} from the float64 Cholesky of G (shifted when G is not
+// numerically positive definite), Y <- Y R^{-1}.  For a full-rank Y the thin
+// Q factor is unique up to column signs, so this is the Householder Q of the
+// same block up to signs, and the passes are float64 kernels over all SMs
+// rather than q sequential reflector steps.  Then CP = Z(:, nnow:s) Q.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) hl_qr_kernel(int s, int nnow, int nlock, const double* __restrict__ Z,
-                                                    int64_t ldz, double* __restrict__ Mw,
-                                                    double* __restrict__ htau) {
-  const int m = s - nnow, q = nnow - nlock;
-  __shared__ double red[256];
-  const int t = threadIdx.x;
-  // Mw (m x q row-major): Mw[i][j] = Z[nlock + j][nnow + i]
-  for (int64_t idx = t; idx < int64_t(m) * q; idx += blockDim.x) {
-    const int i = int(idx / q), j = int(idx % q);
-    Mw[idx] = Z[int64_t(nlock + j) * ldz + nnow + i];
-  }
-  __syncthreads();
-  for (int k = 0; k < q; ++k) {
-    // reflector for column k, rows k..m-1
-    double part = 0.0;
-    for (int i = k + 1 + t; i < m; i += blockDim.x) part += Mw[int64_t(i) * q + k] * Mw[int64_t(i) * q + k];
-    red[t] = part;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (t < o) red[t] += red[t + o];
-      __syncthreads();
-    }
-    const double tail2 = red[0];
-    __syncthreads();
-    const double x0 = Mw[int64_t(k) * q + k];
-    double tk = 0.0;
-    if (tail2 != 0.0) {
-      const double nrm = sqrt(x0 * x0 + tail2);
-      const double alpha = x0 >= 0.0 ? -nrm : nrm;
-      const double v0 = x0 - alpha;
-      tk = 2.0 / (tail2 + v0 * v0);
-      __syncthreads();
-      if (t == 0) Mw[int64_t(k) * q + k] = v0;  // v stored in column k (rows k..), v0 at the top
-    }
-    if (t == 0) htau[k] = tk;
-    __syncthreads();
-    if (tk != 0.0) {
-      // apply H_k to columns k+1..q-1: col -= tk v (v^T col)
-      for (int j = k + 1 + t; j < q; j += blockDim.x) {
-        double dot = 0.0;
-        for (int i = k; i < m; ++i) dot += Mw[int64_t(i) * q + k] * Mw[int64_t(i) * q + j];
-        const double f = tk * dot;
-        for (int i = k; i < m; ++i) Mw[int64_t(i) * q + j] -= f * Mw[int64_t(i) * q + k];
-      }
-    }
-    __syncthreads();
-  }
+__global__ void hl_gather_kernel(int nnow, int nlock, int m, int q, const double* __restrict__ Z, int64_t ldz,
+                                 double* __restrict__ Y) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= int64_t(m) * q) return;
+  const int i = int(idx / q), j = int(idx % q);
+  Y[idx] = Z[int64_t(nlock + j) * ldz + nnow + i];
 }
 
-// CP[row][0:q] = (Z(row, nnow:s) H_0 ... H_{q-1})[0:q]
-__global__ void hl_apply_kernel(int s, int nnow, int nlock, const double* __restrict__ Z, int64_t ldz,
-                                const double* __restrict__ Mw, const double* __restrict__ htau,
-                                double* __restrict__ CP, int64_t ldcp, double* __restrict__ rowbuf) {
-  const int m = s - nnow, q = nnow - nlock;
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= s) return;
-  double* z = rowbuf + int64_t(row) * m;
-  for (int i = 0; i < m; ++i) z[i] = Z[int64_t(row) * ldz + nnow + i];
-  for (int k = 0; k < q; ++k) {
-    const double tk = htau[k];
-    if (tk == 0.0) continue;
-    double dot = 0.0;
-    for (int i = k; i < m; ++i) dot += z[i] * Mw[int64_t(i) * q + k];
-    const double f = tk * dot;
-    for (int i = k; i < m; ++i) z[i] -= f * Mw[int64_t(i) * q + k];
-  }
-  for (int j = 0; j < q; ++j) CP[int64_t(row) * ldcp + j] = z[j];
+namespace {
+struct HLWork {
+  double *Y, *Y2, *G, *Rinv, *cholw, *Cs, *scr;
+  int* status;
+};
+size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+HLWork hl_carve(void* work, int m, int q) {
+  char* c = static_cast<char*>(work);
+  HLWork w;
+  auto take = [&](size_t n) {
+    double* r = reinterpret_cast<double*>(c);
+    c += al256(n * sizeof(double));
+    return r;
+  };
+  w.Y = take(size_t(m) * q);
+  w.Y2 = take(size_t(m) * q);
+  w.G = take(size_t(q) * q);
+  w.Rinv = take(size_t(q) * q);
+  w.cholw = take(size_t(q) * q + q);
+  w.Cs = take(size_t(m) * q);
+  w.scr = take(gram_scratch_elems(m, q, q, true));
+  w.status = reinterpret_cast<int*>(c);
+  return w;
 }
+}  // namespace
 
 size_t hl_work_bytes(int s, int nnow, int nlock) {
   const size_t m = size_t(s - nnow), q = size_t(nnow - nlock);
-  return (m * q + q + size_t(s) * m) * sizeof(double) + 64;
+  return 3 * al256(m * q * sizeof(double)) + 2 * al256(q * q * sizeof(double)) + al256((q * q + q) * sizeof(double)) +
+         al256(gram_scratch_elems(int64_t(m), int(q), int(q), true) * sizeof(double)) + 256;
 }
 
 cudaError_t hl_trick(int s, int nnow, int nlock, const double* Z, int64_t ldz, double* CP, int64_t ldcp,
@@ -209,12 +184,30 @@ cudaError_t hl_trick(int s, int nnow, int nlock, const double* Z, int64_t ldz, d
   const int m = s - nnow, q = nnow - nlock;
   if (q <= 0) return cudaSuccess;
   if (m < q) return cudaErrorInvalidValue;
-  double* Mw = static_cast<double*>(work);
-  double* htau = Mw + size_t(m) * q;
-  double* rowbuf = htau + q;
-  hl_qr_kernel<<<1, 256, 0, st>>>(s, nnow, nlock, Z, ldz, Mw, htau); count_launches(1);
-  hl_apply_kernel<<<(unsigned)cdiv(s, 64), 64, 0, st>>>(s, nnow, nlock, Z, ldz, Mw, htau, CP, ldcp, rowbuf); count_launches(1);
-  return cudaGetLastError();
+  HLWork w = hl_carve(work, m, q);
+  hl_gather_kernel<<<(unsigned)cdiv(int64_t(m) * q, 256), 256, 0, st>>>(nnow, nlock, m, q, Z, ldz, w.Y);
+  count_launches(1);
+  cudaError_t e = cudaGetLastError();
+  double* y = w.Y;
+  double* y2 = w.Y2;
+  for (int pass = 0; pass < 3 && e == cudaSuccess; ++pass) {
+    Blk<double> Yb, Yo;
+    Yb.add(y, q, q);
+    Yo.add(y2, q, q);
+    e = gram<Arith::F64>(m, Yb, Yb, true, w.G, q, w.scr, st);
+    if (e == cudaSuccess) e = chol_rinv(q, m, w.G, q, w.Rinv, w.cholw, w.status, st, nullptr, 1.1102230246251565e-16);
+    if (e == cudaSuccess) e = stage_coef<Arith::F64>(q, q, w.Rinv, q, w.Cs, q, 1.0, st);
+    if (e == cudaSuccess) e = update<Arith::F64>(m, Yb, w.Cs, q, Yo, 0.0, st);
+    std::swap(y, y2);
+  }
+  if (e != cudaSuccess) return e;
+  // CP = Z(:, nnow:s) Q
+  Blk<double> Zr, Cb;
+  Zr.add(const_cast<double*>(Z) + nnow, ldz, m);
+  Cb.add(CP, ldcp, q);
+  e = stage_coef<Arith::F64>(m, q, y, q, w.Cs, q, 1.0, st);
+  if (e == cudaSuccess) e = update<Arith::F64>(s, Zr, w.Cs, q, Cb, 0.0, st);
+  return e;
 }
 
 }  // namespace eig

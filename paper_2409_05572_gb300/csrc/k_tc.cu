@@ -193,11 +193,13 @@ __global__ void __launch_bounds__(256) tc_slice_rows_kernel(int64_t n, Blk<dd> U
   }
   __syncthreads();
   {
-    // row maxima: 4 threads per row, 16 columns each
+    // row maxima: 4 threads per row, columns 8 part + i and 8 part + 32 + i
+    // (banks row + 8 part + i: distinct across the warp)
     const int row = t >> 2, part = t & 3;
     float m = 0.f;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) m = fmaxf(m, fabsf(shi[row][part * 16 + i]));
+    for (int i = 0; i < 8; ++i)
+      m = fmaxf(m, fmaxf(fabsf(shi[row][8 * part + i]), fabsf(shi[row][8 * part + 32 + i])));
     m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
     m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
     if (part == 0) {
@@ -514,6 +516,17 @@ UpdOut upd_out(const Blk<dd>& Y, double beta) {
 
 }  // namespace
 
+// the slicers use 33-35 KB of shared memory per 256-thread CTA: ask for the
+// largest shared-memory carveout so that six CTAs fit on an SM
+template <typename K>
+void max_carveout(K kernel) {
+  static thread_local int done_dev = -1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || done_dev == dev) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  done_dev = dev;
+}
+
 size_t tc_slice_bytes(int64_t K, int64_t M) {
   const size_t mp = size_t(mpad_of(M));
   const size_t sb = sizeof(__nv_bfloat16) * size_t(S) * size_t(nkb_of(K)) * mp * KB;
@@ -530,6 +543,7 @@ cudaError_t tc_slice_cols(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t s
   if (w <= 0 || n <= 0) return cudaSuccess;
   const Layout o = layout(buf, n, w);
   dim3 grid((unsigned)(o.Mp / 64), (unsigned)cdiv(n, CH));
+  max_carveout(tc_slice_cols_kernel);
   tc_slice_cols_kernel<<<grid, 256, 0, st>>>(n, U, o, gate);
   count_launches(1);
   return cudaGetLastError();
@@ -540,6 +554,7 @@ cudaError_t tc_slice_rows(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t s
   if (w <= 0 || n <= 0) return cudaSuccess;
   const Layout o = layout(buf, w, n);
   dim3 grid((unsigned)(o.Mp / 64), (unsigned)cdiv(w, CH));
+  max_carveout(tc_slice_rows_kernel);
   tc_slice_rows_kernel<<<grid, 256, 0, st>>>(n, U, o, gate);
   count_launches(1);
   return cudaGetLastError();
@@ -550,6 +565,7 @@ cudaError_t tc_slice_coef(int s, int c, const double* C, int64_t ldc, double sca
   if (s <= 0 || c <= 0) return cudaSuccess;
   const Layout o = layout(buf, s, c);
   dim3 grid((unsigned)(o.Mp / 64), (unsigned)cdiv(s, CH));
+  max_carveout(tc_slice_coef_kernel);
   tc_slice_coef_kernel<<<grid, 256, 0, st>>>(s, c, C, ldc, scale, o, gate);
   count_launches(1);
   return cudaGetLastError();

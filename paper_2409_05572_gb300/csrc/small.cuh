@@ -25,8 +25,9 @@ size_t syev_qr64_work_bytes(int s);
 cudaError_t syev_qr64(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
                       int* status_dev, cudaStream_t st);
 
-// improved Hetmaniuk-Lehoucq: CP = Z(:, nnow:s) Q, Q from Householder QR of
-// Z(nlock:nnow, nnow:s)^T; work of hl_work_bytes() bytes.
+// improved Hetmaniuk-Lehoucq: CP = Z(:, nnow:s) Q, Q the orthonormal QR
+// factor (shifted CholeskyQR3) of Z(nlock:nnow, nnow:s)^T; work of
+// hl_work_bytes() bytes.
 size_t hl_work_bytes(int s, int nnow, int nlock);
 cudaError_t hl_trick(int s, int nnow, int nlock, const double* Z, int64_t ldz, double* CP, int64_t ldcp,
                      void* work, cudaStream_t st);
