@@ -7,9 +7,11 @@
 //
 //  1. float32 decomposition: Householder tridiagonalisation (cooperative,
 //     grid-synchronised kernel, one warp per row of the trailing matrix),
-//     implicit QL with Wilkinson shifts on the tridiagonal (Bowdler, Martin,
-//     Reinsch and Wilkinson 1968) recording its Givens rotations, row-parallel
-//     accumulation of the rotations and a warp-per-vector back-transformation.
+//     eigenvalues of the tridiagonal by bisection and eigenvectors by inverse
+//     iteration with Gram-Schmidt inside clusters (all parallel; the
+//     sequential implicit QL with Wilkinson shifts of Bowdler, Martin, Reinsch
+//     and Wilkinson 1968 with row-parallel accumulation of its rotations is
+//     kept behind EIG_TRIDIAG=ql), and a warp-per-vector back-transformation.
 //  2. refinement to float64 accuracy with the iteration of Ogita and Aishima
 //     (Japan J. Indust. Appl. Math. 35, 2018): with R = I - X^T X and
 //     S = X^T A X, lambda_i = S_ii / (1 - R_ii) and X <- X (I + E),
@@ -25,6 +27,8 @@
 
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
+#include <type_traits>
 
 #include "blocks.cuh"
 #include "small.cuh"
@@ -253,6 +257,243 @@ __global__ void tql_kernel(int s, R* __restrict__ dg, R* __restrict__ eg, int* _
   }
 }
 
+// ---------------------------------------------------------------------------
+// Parallel tridiagonal eigenvectors (float32 stage, default): eigenvalues by
+// bisection on Sturm counts (one thread per eigenvalue), eigenvectors by
+// inverse iteration with the pivoted LU of T - sigma_j I (one thread per
+// vector; the method of LAPACK's stebz / stein, Dhillon 1998), two passes,
+// each followed by classical Gram-Schmidt with re-orthogonalisation inside
+// clusters of eigenvalues closer than 1e-3 ||T||_1 (one CTA per cluster).
+// No step is a sequential chain over all eigenvalues.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int sturm_count(int s, const float* d, const float* e2, float x, float pivmin) {
+  int cnt = 0;
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  cnt += q < 0.f;
+  for (int k = 1; k < s; ++k) {
+    q = (d[k] - x) - e2[k - 1] / q;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += q < 0.f;
+  }
+  return cnt;
+}
+
+// lam[i] = i-th smallest eigenvalue of T (d, e; e[k] = T[k+1][k])
+__global__ void __launch_bounds__(128) bisect_kernel(int s, const float* __restrict__ dg, const float* __restrict__ eg,
+                                                     float* __restrict__ lam) {
+  extern __shared__ float sh[];
+  float* d = sh;
+  float* e2 = sh + s;
+  __shared__ float bounds[4];
+  for (int k = threadIdx.x; k < s; k += blockDim.x) {
+    d[k] = dg[k];
+    e2[k] = k + 1 < s ? eg[k] * eg[k] : 0.f;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float gl = d[0], gu = d[0], emax = 0.f;
+    for (int k = 0; k < s; ++k) {
+      const float r = (k > 0 ? fabsf(eg[k - 1]) : 0.f) + (k + 1 < s ? fabsf(eg[k]) : 0.f);
+      gl = fminf(gl, d[k] - r);
+      gu = fmaxf(gu, d[k] + r);
+      emax = fmaxf(emax, e2[k]);
+    }
+    const float pivmin = 1.1754944e-38f * fmaxf(1.f, emax);
+    const float tn = fmaxf(fabsf(gl), fabsf(gu));
+    bounds[0] = gl - 2.f * 1.1920929e-07f * tn - 2.f * pivmin;
+    bounds[1] = gu + 2.f * 1.1920929e-07f * tn + 2.f * pivmin;
+    bounds[2] = pivmin;
+    bounds[3] = 1.1920929e-07f * tn;  // absolute accuracy eps ||T|| is all the refinement needs
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s) return;
+  float lo = bounds[0], hi = bounds[1];
+  const float pivmin = bounds[2], atol = bounds[3];
+  for (int it = 0; it < 100; ++it) {
+    const float mid = 0.5f * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (hi - lo <= 2.f * 1.1920929e-07f * fmaxf(fabsf(lo), fabsf(hi)) + atol) break;
+    if (sturm_count(s, d, e2, mid, pivmin) > i)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  lam[i] = 0.5f * (lo + hi);
+}
+
+// shifts separated by at least 10 eps ||T||_1, cluster starts (gap to the
+// previous eigenvalue at most 1e-3 ||T||_1), zero-pivot replacement
+__global__ void invit_prep_kernel(int s, const float* __restrict__ d, const float* __restrict__ e,
+                                  const float* __restrict__ lam, float* __restrict__ sig, int* __restrict__ cstart,
+                                  float* __restrict__ pert) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  float nrm = 0.f;
+  for (int k = 0; k < s; ++k)
+    nrm = fmaxf(nrm, fabsf(d[k]) + (k > 0 ? fabsf(e[k - 1]) : 0.f) + (k + 1 < s ? fabsf(e[k]) : 0.f));
+  const float eps1 = 10.f * 1.1920929e-07f * nrm, ortol = 1e-3f * nrm;
+  sig[0] = lam[0];
+  cstart[0] = 0;
+  for (int j = 1; j < s; ++j) {
+    sig[j] = fmaxf(lam[j], sig[j - 1] + eps1);
+    cstart[j] = (lam[j] - lam[j - 1] <= ortol) ? cstart[j - 1] : j;
+  }
+  *pert = fmaxf(1.1920929e-07f * nrm, 1.1754944e-38f);
+}
+
+// One inverse-iteration solve per thread j: (T - sig_j I) x = b, b a fixed
+// pseudo-random vector (pass 0, which also factors) or column j of ZT (later
+// passes); x normalised into column j of ZT (ZT[j s + i]).  Factor arrays are
+// [k][j] so that the threads of a warp touch consecutive words.
+__global__ void __launch_bounds__(128) invit_kernel(int s, const float* __restrict__ d, const float* __restrict__ e,
+                                                    const float* __restrict__ sig, const float* __restrict__ pertp,
+                                                    float* __restrict__ dl, float* __restrict__ dg,
+                                                    float* __restrict__ du, float* __restrict__ du2,
+                                                    unsigned char* __restrict__ piv, float* __restrict__ b,
+                                                    float* __restrict__ ZT, int pass) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= s) return;
+  const int64_t S = s;
+  const float pert = *pertp;
+#define AT(a, k) a[int64_t(k) * S + j]
+  if (pass == 0) {
+    const float sg = sig[j];
+    for (int k = 0; k < s; ++k) {
+      AT(dg, k) = d[k] - sg;
+      if (k + 1 < s) {
+        AT(dl, k) = e[k];
+        AT(du, k) = e[k];
+      }
+    }
+    for (int k = 0; k + 1 < s; ++k) {
+      const float a = AT(dg, k), l = AT(dl, k);
+      if (fabsf(a) >= fabsf(l)) {  // no interchange
+        const float a2 = a != 0.f ? a : pert;
+        const float f = l / a2;
+        AT(dl, k) = f;
+        AT(dg, k) = a2;
+        AT(dg, k + 1) -= f * AT(du, k);
+        if (k + 2 < s) AT(du2, k) = 0.f;
+        AT(piv, k) = 0;
+      } else {  // interchange rows k and k + 1
+        const float f = a / l;
+        const float dk1 = AT(dg, k + 1);
+        AT(dg, k) = l;
+        AT(dl, k) = f;
+        const float t = AT(du, k);
+        AT(du, k) = dk1;
+        AT(dg, k + 1) = t - f * dk1;
+        if (k + 2 < s) {
+          const float u1 = AT(du, k + 1);
+          AT(du2, k) = u1;
+          AT(du, k + 1) = -f * u1;
+        }
+        AT(piv, k) = 1;
+      }
+    }
+    for (int k = 0; k < s; ++k) {
+      const float a = AT(dg, k);
+      if (fabsf(a) < pert) AT(dg, k) = a < 0.f ? -pert : pert;
+    }
+    // fixed pseudo-random start (integer hash of (k, j)), entries in [-1, 1)
+    for (int k = 0; k < s; ++k) {
+      uint32_t h = uint32_t(k) * 0x9E3779B1u ^ (uint32_t(j) * 0x85EBCA77u + 0x27d4eb2fu);
+      h ^= h >> 15;
+      h *= 0x2C1B3C6Du;
+      h ^= h >> 12;
+      h *= 0x297A2D39u;
+      h ^= h >> 15;
+      AT(b, k) = float(int32_t(h)) * 4.656612873e-10f;
+    }
+  } else {
+    float mx = 0.f;
+    for (int k = 0; k < s; ++k) mx = fmaxf(mx, fabsf(ZT[int64_t(j) * S + k]));
+    const float sc = mx > 0.f ? 1.f / mx : 1.f;
+    for (int k = 0; k < s; ++k) AT(b, k) = ZT[int64_t(j) * S + k] * sc;
+  }
+  // forward: L with the interchanges
+  for (int k = 0; k + 1 < s; ++k) {
+    if (AT(piv, k) == 0) {
+      AT(b, k + 1) -= AT(dl, k) * AT(b, k);
+    } else {
+      const float t = AT(b, k);
+      const float bk1 = AT(b, k + 1);
+      AT(b, k) = bk1;
+      AT(b, k + 1) = t - AT(dl, k) * bk1;
+    }
+  }
+  // backward: U with two superdiagonals
+  float x2 = 0.f, x1 = 0.f, nrm = 0.f;
+  for (int k = s - 1; k >= 0; --k) {
+    float v = AT(b, k);
+    if (k + 1 < s) v -= AT(du, k) * x1;
+    if (k + 2 < s) v -= AT(du2, k) * x2;
+    v /= AT(dg, k);
+    AT(b, k) = v;
+    x2 = x1;
+    x1 = v;
+    nrm = fmaxf(nrm, fabsf(v));
+  }
+  // normalise (scaled 2-norm)
+  const float inv = nrm > 0.f ? 1.f / nrm : 1.f;
+  float ss = 0.f;
+  for (int k = 0; k < s; ++k) {
+    const float v = AT(b, k) * inv;
+    ss += v * v;
+  }
+  const float f = ss > 0.f ? inv / sqrtf(ss) : 0.f;
+  for (int k = 0; k < s; ++k) ZT[int64_t(j) * S + k] = AT(b, k) * f;
+#undef AT
+}
+
+// Classical Gram-Schmidt with re-orthogonalisation inside each cluster, in
+// ascending order: CTA b handles the cluster that starts at b.
+__global__ void __launch_bounds__(256) cluster_cgs_kernel(int s, const int* __restrict__ cstart,
+                                                          float* __restrict__ ZT) {
+  const int b = blockIdx.x;
+  if (cstart[b] != b) return;
+  int end = b + 1;
+  while (end < s && cstart[end] == b) ++end;
+  if (end - b == 1) return;
+  extern __shared__ float sh[];
+  float* x = sh;       // s
+  float* c = sh + s;   // cluster size
+  __shared__ float red[8];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int64_t S = s;
+  for (int j = b + 1; j < end; ++j) {
+    for (int r = t; r < s; r += blockDim.x) x[r] = ZT[int64_t(j) * S + r];
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i = b + warp; i < j; i += blockDim.x / 32) {
+        const float* q = ZT + int64_t(i) * S;
+        float acc = 0.f;
+        for (int r = lane; r < s; r += 32) acc += q[r] * x[r];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) c[i - b] = acc;
+      }
+      __syncthreads();
+      for (int r = t; r < s; r += blockDim.x) {
+        float acc = 0.f;
+        for (int i = b; i < j; ++i) acc += c[i - b] * ZT[int64_t(i) * S + r];
+        x[r] -= acc;
+      }
+      __syncthreads();
+    }
+    float part = 0.f;
+    for (int r = t; r < s; r += blockDim.x) part += x[r] * x[r];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) red[warp] = part;
+    __syncthreads();
+    float nn = 0.f;
+    for (int w = 0; w < 8; ++w) nn += red[w];
+    const float f = nn > 0.f ? rsqrtf(nn) : 0.f;
+    for (int r = t; r < s; r += blockDim.x) ZT[int64_t(j) * S + r] = x[r] * f;
+    __syncthreads();
+  }
+}
+
 // rank[c] = position of d[c] in ascending order (ties by index)
 template <typename R>
 __global__ void rank_kernel(int s, const R* __restrict__ d, int* __restrict__ rank, double* __restrict__ lam) {
@@ -388,6 +629,48 @@ QLWork<R> ql_carve(int s, Carver& cv) {
   return w;
 }
 
+// EIG_TRIDIAG=ql selects the sequential QL chain for the float32 stage
+static bool use_tql() {
+  static const bool v = [] {
+    const char* e = std::getenv("EIG_TRIDIAG");
+    return e && std::strcmp(e, "ql") == 0;
+  }();
+  return v;
+}
+
+// bisection + inverse iteration for the float32 stage: eigenvectors of T into
+// w.ZT (column j = eigenvector of the j-th smallest eigenvalue), ranks
+// (identity) and eigenvalues (float64, if lam)
+template <typename R>
+static cudaError_t tri_invit(int s, QLWork<R>& w, double* lam, cudaStream_t st) {
+  if constexpr (std::is_same<R, float>::value) {
+    const size_t ss = size_t(s) * s;
+    float* dl = w.rc;
+    float* dgv = w.rc + ss;
+    float* du = w.rc + 2 * ss;
+    float* du2 = w.rc + 3 * ss;
+    float* bv = w.rc + 4 * ss;
+    float* lamf = w.rs;
+    float* sig = w.rs + s;
+    float* pert = w.rs + 2 * s;
+    int* cstart = reinterpret_cast<int*>(w.rs + 2 * s + 64);
+    unsigned char* piv = reinterpret_cast<unsigned char*>(w.ri);
+    const unsigned nb = (unsigned)cdiv(s, 128);
+    bisect_kernel<<<nb, 128, 2 * size_t(s) * sizeof(float), st>>>(s, w.d, w.e, lamf); count_launches(1);
+    invit_prep_kernel<<<1, 32, 0, st>>>(s, w.d, w.e, lamf, sig, cstart, pert); count_launches(1);
+    cudaFuncSetAttribute(cluster_cgs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    for (int pass = 0; pass < 2; ++pass) {
+      invit_kernel<<<nb, 128, 0, st>>>(s, w.d, w.e, sig, pert, dl, dgv, du, du2, piv, bv, w.ZT, pass);
+      count_launches(1);
+      cluster_cgs_kernel<<<s, 256, 2 * size_t(s) * sizeof(float), st>>>(s, cstart, w.ZT); count_launches(1);
+    }
+    rank_kernel<float><<<nb, 128, 0, st>>>(s, lamf, w.rank, lam); count_launches(1);
+    return cudaGetLastError();
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
 // Stage 1 in precision R: eigenvalues (ascending) into lam (if non-null) and
 // eigenvectors (float64, columns in ascending order) into Zd.
 template <typename R>
@@ -411,16 +694,20 @@ cudaError_t ql_eig(int s, const double* A, int64_t lda, double* lam, double* Zd,
   } else {
     small_tridiag_kernel<R><<<1, 32, 0, st>>>(s, w.Wm, w.d, w.e, w.tau); count_launches(1);
   }
-  cudaFuncSetAttribute(tql_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-  tql_kernel<R><<<1, 32, 2 * size_t(s) * sizeof(R), st>>>(s, w.d, w.e, w.ri, w.rc, w.rs, w.cap, w.nrot,
-                                                          status_dev ? status_dev : w.status); count_launches(1);
-  rank_kernel<R><<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.d, w.rank, lam); count_launches(1);
-  int rpb = 32;
-  while (rpb > 1 && size_t(s) * rpb * sizeof(R) > 200 * 1024) rpb >>= 1;
-  cudaFuncSetAttribute(rot_accum_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
   cudaFuncSetAttribute(backtrans_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-  rot_accum_kernel<R><<<(unsigned)cdiv(s, rpb), 64, size_t(s) * rpb * sizeof(R), st>>>(s, rpb, w.ri, w.rc, w.rs,
-                                                                                       w.nrot, w.ZT); count_launches(1);
+  if (std::is_same<R, float>::value && !use_tql()) {
+    if (cudaError_t err = tri_invit(s, w, lam, st)) return err;
+  } else {
+    cudaFuncSetAttribute(tql_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    tql_kernel<R><<<1, 32, 2 * size_t(s) * sizeof(R), st>>>(s, w.d, w.e, w.ri, w.rc, w.rs, w.cap, w.nrot,
+                                                            status_dev ? status_dev : w.status); count_launches(1);
+    rank_kernel<R><<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.d, w.rank, lam); count_launches(1);
+    int rpb = 32;
+    while (rpb > 1 && size_t(s) * rpb * sizeof(R) > 200 * 1024) rpb >>= 1;
+    cudaFuncSetAttribute(rot_accum_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    rot_accum_kernel<R><<<(unsigned)cdiv(s, rpb), 64, size_t(s) * rpb * sizeof(R), st>>>(s, rpb, w.ri, w.rc, w.rs,
+                                                                                         w.nrot, w.ZT); count_launches(1);
+  }
   int wpb = 8;
   while (wpb > 1 && size_t(wpb) * s * sizeof(R) > 200 * 1024) --wpb;
   backtrans_kernel<R><<<(unsigned)cdiv(s, wpb), 32 * wpb, size_t(wpb) * s * sizeof(R), st>>>(
