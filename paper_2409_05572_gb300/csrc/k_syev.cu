@@ -423,13 +423,23 @@ __global__ void __launch_bounds__(128) invit_kernel(int s, const float* __restri
       AT(b, k + 1) = t - AT(dl, k) * bk1;
     }
   }
-  // backward: U with two superdiagonals
+  // backward: U with two superdiagonals.  A nearly reducible T (repeated
+  // eigenvalues) has several tiny pivots, each multiplying the solution by up
+  // to ||T|| / pert; the whole vector (solved part and remaining right-hand
+  // side alike, x = U^{-1} b being linear) is rescaled before it can overflow.
   float x2 = 0.f, x1 = 0.f, nrm = 0.f;
   for (int k = s - 1; k >= 0; --k) {
     float v = AT(b, k);
     if (k + 1 < s) v -= AT(du, k) * x1;
     if (k + 2 < s) v -= AT(du2, k) * x2;
     v /= AT(dg, k);
+    if (fabsf(v) > 1e20f) {
+      for (int q = 0; q < s; ++q) AT(b, q) *= 1e-20f;
+      v *= 1e-20f;
+      x1 *= 1e-20f;
+      x2 *= 1e-20f;
+      nrm *= 1e-20f;
+    }
     AT(b, k) = v;
     x2 = x1;
     x1 = v;
@@ -488,8 +498,10 @@ __global__ void __launch_bounds__(256) cluster_cgs_kernel(int s, const int* __re
     __syncthreads();
     float nn = 0.f;
     for (int w = 0; w < 8; ++w) nn += red[w];
-    const float f = nn > 0.f ? rsqrtf(nn) : 0.f;
-    for (int r = t; r < s; r += blockDim.x) ZT[int64_t(j) * S + r] = x[r] * f;
+    if (nn > 0.f) {
+      const float f = rsqrtf(nn);
+      for (int r = t; r < s; r += blockDim.x) ZT[int64_t(j) * S + r] = x[r] * f;
+    }  // else: the vector lay in the span of the earlier ones; keep it as it was
     __syncthreads();
   }
 }

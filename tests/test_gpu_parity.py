@@ -552,6 +552,24 @@ def test_lobpcg_3d_several_tiles_closed_form():
     s.close()
 
 
+@pytest.mark.parametrize("strategy", ["none", "fix"])
+def test_lobpcg_cube_repeated_eigenvalues(strategy):
+    """3D Dirichlet cube: eigenvalues of multiplicity 3 and 6 (permutations of
+    the grid indices), so the projected matrices have exactly repeated Ritz
+    values near convergence and nearly reducible tridiagonal forms."""
+    d = 14
+    A = W.laplacian_3d(d, d, d)   # n = 2744
+    ex = dirichlet_spectrum((d, d, d))
+    nev, k = 24, 48
+    X0 = W.gaussian_block(A.n, k, 7)
+    s = L.Solver(A, nev=nev, k_max=k, strategy=strategy, X0=X0, normA=W.dirichlet_norm((d, d, d)), tol=1e-10)
+    out = s.solve()
+    assert out["status"] == 0
+    assert np.max(np.abs(out["lam"] - ex[:nev]) / ex[:nev]) <= 1e-9
+    assert out["resid"].max() <= 2e-10
+    s.close()
+
+
 def test_lobpcg_graph_laplacian_jacobi_deflation():
     A = W.graph_laplacian(3000, seed=3)
     M = A.to_scipy()
