@@ -261,9 +261,9 @@ __global__ void tql_kernel(int s, R* __restrict__ dg, R* __restrict__ eg, int* _
 // Parallel tridiagonal eigenvectors (float32 stage, default): eigenvalues by
 // bisection on Sturm counts (one thread per eigenvalue), eigenvectors by
 // inverse iteration with the pivoted LU of T - sigma_j I (one thread per
-// vector; the method of LAPACK's stebz / stein, Dhillon 1998), two passes,
-// each followed by classical Gram-Schmidt with re-orthogonalisation inside
-// clusters of eigenvalues closer than 1e-3 ||T||_1 (one CTA per cluster).
+// vector; after LAPACK's stebz / stein), two passes, each followed by
+// classical Gram-Schmidt with re-orthogonalisation inside clusters of
+// eigenvalues closer than 1e-5 ||T||_1 (one CTA per cluster).
 // No step is a sequential chain over all eigenvalues.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int sturm_count(int s, const float* d, const float* e2, float x, float pivmin) {
@@ -323,8 +323,15 @@ __global__ void __launch_bounds__(128) bisect_kernel(int s, const float* __restr
   lam[i] = 0.5f * (lo + hi);
 }
 
-// shifts separated by at least 10 eps ||T||_1, cluster starts (gap to the
-// previous eigenvalue at most 1e-3 ||T||_1), zero-pivot replacement
+// Shifts equal to the eigenvalues: every vector starts from its own
+// pseudo-random vector, so the vectors of a repeated eigenvalue stay
+// independent without the shift separation of stein (which, at about
+// 10 eps ||T|| per member, would push the shifts of a large group of equal
+// eigenvalues toward the next distinct one).  Cluster starts: gap to the
+// previous eigenvalue at most 1e-5 ||T||_1 (closer pairs can mix in float32
+// inverse iteration and are orthogonalised together; farther pairs are
+// coupled by at most (eps ||T|| / gap)^2 after two passes, which the
+// refinement removes).  Zero-pivot replacement eps ||T||_1.
 __global__ void invit_prep_kernel(int s, const float* __restrict__ d, const float* __restrict__ e,
                                   const float* __restrict__ lam, float* __restrict__ sig, int* __restrict__ cstart,
                                   float* __restrict__ pert) {
@@ -332,11 +339,11 @@ __global__ void invit_prep_kernel(int s, const float* __restrict__ d, const floa
   float nrm = 0.f;
   for (int k = 0; k < s; ++k)
     nrm = fmaxf(nrm, fabsf(d[k]) + (k > 0 ? fabsf(e[k - 1]) : 0.f) + (k + 1 < s ? fabsf(e[k]) : 0.f));
-  const float eps1 = 10.f * 1.1920929e-07f * nrm, ortol = 1e-3f * nrm;
+  const float ortol = 1e-5f * nrm;
   sig[0] = lam[0];
   cstart[0] = 0;
   for (int j = 1; j < s; ++j) {
-    sig[j] = fmaxf(lam[j], sig[j - 1] + eps1);
+    sig[j] = lam[j];
     cstart[j] = (lam[j] - lam[j - 1] <= ortol) ? cstart[j - 1] : j;
   }
   *pert = fmaxf(1.1920929e-07f * nrm, 1.1754944e-38f);

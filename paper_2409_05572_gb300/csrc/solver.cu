@@ -406,7 +406,11 @@ struct Ops {
       }
     std::fprintf(stderr, "[eig]   syev check s=%d: max |dlam|/|A_p| = %.2e at %d (lam %.12f vs %.12f)\n", s,
                  worst / nrm, wi, l1[wi], l2[wi]);
-    if (worst / nrm > 1e-11 && std::getenv("EIG_DUMP_AP")) {
+    bool finite = true;
+    for (int i = 0; i < s; ++i) finite = finite && std::isfinite(l1[i]);
+    static bool dumped = false;  // the first projected matrix that disagrees
+    if ((!finite || !(worst / nrm <= 1e-11)) && std::getenv("EIG_DUMP_AP") && !dumped) {
+      dumped = true;
       FILE* f = std::fopen(std::getenv("EIG_DUMP_AP"), "wb");
       if (f) {
         std::fwrite(&s, sizeof(int), 1, f);
