@@ -43,9 +43,11 @@ UNIT = "eigenpairs/s"
 # the small cases (profiles/gram_kernel_df64_n262144_384x384_sym.md and
 # profiles/update_kernel_df64_n262144_384x256.md); traffic grows with n.
 TRAFFIC_RATIO = {"gram": 1.387 / 0.805, "update": 1.447 / 1.342}
-# the same for the tensor-core classes (slicing + product kernels); empty
-# until the current kernels are captured
-TC_TRAFFIC_RATIO = {}
+# the same for the tensor-core classes (slicing + product kernels), from ncu
+# captures at n = 262,144 (profiles/tc5_gram_*.md, profiles/tc5_update_*.md):
+# DRAM bytes of the class's kernels / the class's algorithmic bytes
+TC_TRAFFIC_RATIO = {"gram": (0.805 + 1.299 + 1.219 + 0.005) / 0.805,
+                    "update": (0.805 + 1.299 + 1.217 + 0.513) / 1.342}
 
 
 def peaks():
