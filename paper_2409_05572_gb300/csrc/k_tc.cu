@@ -113,111 +113,114 @@ __device__ __forceinline__ void col_lookup(const Blk<dd>& U, int c, const dd*& p
   ld = U.ld[s];
 }
 
-// Gram operand: K = rows of U, operand rows = columns of U
-__global__ void __launch_bounds__(256) tc_slice_cols_kernel(int64_t n, Blk<dd> U, Layout o, const int* gate) {
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, int nbytes) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(nbytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_s() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_s() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int SL_PITCH = 65;                       // float2 pitch of a 64 x 64 tile in shared memory
+constexpr size_t SL_SHM = size_t(2) * 64 * SL_PITCH * sizeof(float2);
+
+// Both slicers: persistent CTAs walk the 64 x 64 squares (row block a, column
+// block b) of U, item = a * nb + b; the next square's 8-byte loads are in
+// flight (cp.async, two shared-memory buffers) while the current one is cut.
+//  COLS (Gram operand): K = rows of U, operand rows = columns of U, one
+//       exponent per (64-row chunk a, column).
+//  ROWS (update operand): K = columns of U, operand rows = rows of U, one
+//       exponent per (row, 64-column chunk b).
+template <bool COLS>
+__global__ void __launch_bounds__(256) tc_slice_kernel(int64_t n, Blk<dd> U, Layout o, int64_t nb, int64_t items,
+                                                       const int* gate) {
   if (gate && *gate == 0) return;
-  const int w = U.width;
-  const int c0 = blockIdx.x * 64;
-  const int64_t kc = blockIdx.y;
-  const int64_t r0 = kc * CH;
-  __shared__ float shi[CH][65];
-  __shared__ float slo[CH][65];
+  extern __shared__ __align__(16) float2 sdraw[];
   __shared__ float pmax[4][64];
   __shared__ int sexp[64];
   const int t = threadIdx.x;
-  {
-    const int lc = t & 63, lr = t >> 6;
-    const int c = c0 + lc;
-    const dd* colp = nullptr;
-    int64_t cld = 0;
-    if (c < w) col_lookup(U, c, colp, cld);
-    float m = 0.f;
-#pragma unroll
-    for (int i = 0; i < CH / 4; ++i) {
-      const int rr = lr + 4 * i;
-      const int64_t r = r0 + rr;
-      dd x = {0.f, 0.f};
-      if (colp && r < n) x = colp[r * cld];
-      shi[rr][lc] = x.hi;
-      slo[rr][lc] = x.lo;
-      m = fmaxf(m, fabsf(x.hi));
-    }
-    pmax[lr][lc] = m;
-  }
-  __syncthreads();
-  if (t < 64) {
-    const float mm = fmaxf(fmaxf(pmax[0][t], pmax[1][t]), fmaxf(pmax[2][t], pmax[3][t]));
-    const int e = chunk_exp(mm);
-    sexp[t] = e;
-    o.ex[kc * o.Mp + c0 + t] = e == ZERO_EXP ? 0 : e;
-  }
-  __syncthreads();
-  // thread -> (K block kbl, operand row col, K values k0 .. k0 + 15)
-  const int kbl = t >> 7, col = (t & 127) >> 1, k0 = (t & 1) * 16;
-  const int c = c0 + col;
-  const float scale = exp_scale(sexp[col]);
-  float v[16][S];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) cut(shi[kbl * KB + k0 + i][col], slo[kbl * KB + k0 + i][col], scale, v[i]);
-  const int64_t kb = kc * KBC + kbl;
-#pragma unroll
-  for (int q = 0; q < S; ++q) store16(o.sl + o.block(q, kb), c, k0, v, q);
-}
-
-// Update operand A: K = columns of U, operand rows = rows of U
-__global__ void __launch_bounds__(256) tc_slice_rows_kernel(int64_t n, Blk<dd> U, Layout o, const int* gate) {
-  if (gate && *gate == 0) return;
   const int w = U.width;
-  const int64_t r0 = int64_t(blockIdx.x) * 64;
-  const int kc = blockIdx.y;
-  const int k00 = kc * CH;
-  __shared__ float shi[64][65];
-  __shared__ float slo[64][65];
-  __shared__ int sexp[64];
-  const int t = threadIdx.x;
-  {
+  int64_t item = blockIdx.x;
+  if (item >= items) return;
+  auto issue = [&](int64_t it, int buf) {
+    const int64_t r0 = (it / nb) * 64;
+    const int cb = int(it % nb) * 64;
     const int lc = t & 63, lr = t >> 6;
-    const int c = k00 + lc;
+    const int c = cb + lc;
     const dd* colp = nullptr;
     int64_t cld = 0;
     if (c < w) col_lookup(U, c, colp, cld);
+    float2* dst = sdraw + buf * (64 * SL_PITCH);
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const int rr = lr + 4 * i;
       const int64_t r = r0 + rr;
-      dd x = {0.f, 0.f};
-      if (colp && r < n) x = colp[r * cld];
-      shi[rr][lc] = x.hi;
-      slo[rr][lc] = x.lo;
+      const bool ok = colp && r < n;
+      cp_async8(dst + rr * SL_PITCH + lc, ok ? static_cast<const void*>(colp + r * cld) : static_cast<const void*>(U.ptr[0]),
+                ok ? 8 : 0);
     }
-  }
-  __syncthreads();
-  {
-    // row maxima: 4 threads per row, columns 8 part + i and 8 part + 32 + i
-    // (banks row + 8 part + i: distinct across the warp)
-    const int row = t >> 2, part = t & 3;
-    float m = 0.f;
+    cp_async_commit_s();
+  };
+  issue(item, 0);
+  int buf = 0;
+  for (; item < items; item += gridDim.x) {
+    const int64_t nxt = item + gridDim.x;
+    if (nxt < items)
+      issue(nxt, buf ^ 1);
+    else
+      cp_async_commit_s();
+    cp_async_wait_s<1>();
+    __syncthreads();
+    const float2* sd = sdraw + buf * (64 * SL_PITCH);
+    const int64_t a = item / nb, b = item % nb;
+    if (COLS) {
+      const int lc = t & 63, lr = t >> 6;
+      float m = 0.f;
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-      m = fmaxf(m, fmaxf(fabsf(shi[row][8 * part + i]), fabsf(shi[row][8 * part + 32 + i])));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-    if (part == 0) {
-      const int e = chunk_exp(m);
-      sexp[row] = e;
-      o.ex[int64_t(kc) * o.Mp + r0 + row] = e == ZERO_EXP ? 0 : e;
+      for (int i = 0; i < 16; ++i) m = fmaxf(m, fabsf(sd[(lr + 4 * i) * SL_PITCH + lc].x));
+      pmax[lr][lc] = m;
+      __syncthreads();
+      if (t < 64) {
+        const float mm = fmaxf(fmaxf(pmax[0][t], pmax[1][t]), fmaxf(pmax[2][t], pmax[3][t]));
+        const int e = chunk_exp(mm);
+        sexp[t] = e;
+        o.ex[a * o.Mp + b * 64 + t] = e == ZERO_EXP ? 0 : e;
+      }
+    } else {
+      // row maxima: 4 threads per row, columns 8 part + i and 8 part + 32 + i
+      const int row = t >> 2, part = t & 3;
+      float m = 0.f;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        m = fmaxf(m, fmaxf(fabsf(sd[row * SL_PITCH + 8 * part + i].x), fabsf(sd[row * SL_PITCH + 8 * part + 32 + i].x)));
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+      if (part == 0) {
+        const int e = chunk_exp(m);
+        sexp[row] = e;
+        o.ex[b * o.Mp + a * 64 + row] = e == ZERO_EXP ? 0 : e;
+      }
     }
+    __syncthreads();
+    // thread -> (K block kbl, operand row idx of the square, K values k0 .. k0 + 15)
+    const int kbl = t >> 7, idx = (t & 127) >> 1, k0 = (t & 1) * 16;
+    const float scale = exp_scale(sexp[idx]);
+    float v[16][S];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float2 x = COLS ? sd[(kbl * KB + k0 + i) * SL_PITCH + idx] : sd[idx * SL_PITCH + kbl * KB + k0 + i];
+      cut(x.x, x.y, scale, v[i]);
+    }
+    const int64_t kb = (COLS ? a : b) * KBC + kbl;
+    const int64_t orow = (COLS ? b : a) * 64 + idx;
+#pragma unroll
+    for (int q = 0; q < S; ++q) store16(o.sl + o.block(q, kb), orow, k0, v, q);
+    __syncthreads();  // the buffer is refilled by the next issue
+    buf ^= 1;
   }
-  __syncthreads();
-  const int kbl = t >> 7, row = (t & 127) >> 1, k0 = (t & 1) * 16;
-  const int64_t r = r0 + row;
-  const float scale = exp_scale(sexp[row]);
-  float v[16][S];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) cut(shi[row][kbl * KB + k0 + i], slo[row][kbl * KB + k0 + i], scale, v[i]);
-  const int64_t kb = int64_t(kc) * KBC + kbl;
-#pragma unroll
-  for (int q = 0; q < S; ++q) store16(o.sl + o.block(q, kb), r, k0, v, q);
+  cp_async_wait_s<0>();
 }
 
 // Update operand B from float64 C (s x c, ldc) times scale: K = rows of C,
@@ -538,26 +541,41 @@ size_t gram_tc_scratch_elems(int64_t n, int a, int b, bool sym) {
   return size_t(ns) * size_t(a) * size_t(b);
 }
 
+template <bool COLS>
+cudaError_t slice_launch(int64_t n, const Blk<dd>& U, const Layout& o, int64_t na, int64_t nb, cudaStream_t st,
+                         const int* gate) {
+  static thread_local int done_dev = -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (done_dev != dev) {
+    e = cudaFuncSetAttribute(tc_slice_kernel<COLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SL_SHM));
+    if (e != cudaSuccess) return e;
+    cudaFuncSetAttribute(tc_slice_kernel<COLS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    done_dev = dev;
+  }
+  const int64_t items = na * nb;
+  int64_t grid = int64_t(num_sms()) * 3;  // three 67 KB CTAs per SM
+  if (grid > items) grid = items;
+  tc_slice_kernel<COLS><<<(unsigned)grid, 256, SL_SHM, st>>>(n, U, o, nb, items, gate);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t tc_slice_cols(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t st, const int* gate) {
   const int w = U.width;
   if (w <= 0 || n <= 0) return cudaSuccess;
   const Layout o = layout(buf, n, w);
-  dim3 grid((unsigned)(o.Mp / 64), (unsigned)cdiv(n, CH));
-  max_carveout(tc_slice_cols_kernel);
-  tc_slice_cols_kernel<<<grid, 256, 0, st>>>(n, U, o, gate);
-  count_launches(1);
-  return cudaGetLastError();
+  // squares: 64-row chunks of U (K) x 64-column blocks (operand rows, padded)
+  return slice_launch<true>(n, U, o, cdiv(n, CH), o.Mp / 64, st, gate);
 }
 
 cudaError_t tc_slice_rows(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t st, const int* gate) {
   const int w = U.width;
   if (w <= 0 || n <= 0) return cudaSuccess;
   const Layout o = layout(buf, w, n);
-  dim3 grid((unsigned)(o.Mp / 64), (unsigned)cdiv(w, CH));
-  max_carveout(tc_slice_rows_kernel);
-  tc_slice_rows_kernel<<<grid, 256, 0, st>>>(n, U, o, gate);
-  count_launches(1);
-  return cudaGetLastError();
+  // squares: 64-row blocks of U (operand rows, padded) x 64-column chunks (K)
+  return slice_launch<false>(n, U, o, o.Mp / 64, cdiv(w, CH), st, gate);
 }
 
 cudaError_t tc_slice_coef(int s, int c, const double* C, int64_t ldc, double scale, void* buf, cudaStream_t st,
