@@ -120,6 +120,10 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = uint64_t((saddr >> 4) & 0x3FFFu);
   d |= uint64_t((LBO >> 4) & 0x3FFFu) << 16;
@@ -253,10 +257,34 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb
     if (lane == 0) {
       // ---------------- producer ----------------
       int p = 0;
+      // L2 prefetch of the tiles PF stages ahead of the copy being issued, so
+      // that the ring's copies hit L2 instead of waiting on HBM
+      constexpr int PF = NST;
+      int pf_it = 0, pf_k = 0;
+      auto advance_pf = [&]() {
+        if (++pf_k == nkb_item) {
+          pf_k = 0;
+          ++pf_it;
+        }
+      };
+      auto prefetch = [&]() {
+        if (pf_it >= nitem_cta) return;
+        const int item = item0 + pf_it * item_step;
+        const int64_t m0 = int64_t(item / tiles_n) * BM, n0 = int64_t(item % tiles_n) * BN;
+        const int64_t kb = kb0 + pf_k;
+#pragma unroll 1
+        for (int q = 0; q < S; ++q) {
+          prefetch_l2(A.sl + (int64_t(q) * nkb + kb) * A.Mp * KB + m0 * KB, A_SLICE);
+          prefetch_l2(B.sl + (int64_t(q) * nkb + kb) * B.Mp * KB + n0 * KB, B_SLICE);
+        }
+        advance_pf();
+      };
+      for (int i = 0; i < PF; ++i) advance_pf();  // start PF positions ahead
       for (int it = 0; it < nitem_cta && !*abort; ++it) {
         const int item = item0 + it * item_step;
         const int64_t m0 = int64_t(item / tiles_n) * BM, n0 = int64_t(item % tiles_n) * BN;
         for (int kbi = 0; kbi < nkb_item; ++kbi, ++p) {
+          prefetch();
           const int s = p % NST;
           if (p >= NST && !mbar_wait(smem_u32(&bar_empty[s]), uint32_t((p / NST - 1) & 1), abort)) break;
           const uint32_t fb = smem_u32(&bar_full[s]);
