@@ -32,6 +32,7 @@
 // roles leave their loops, waits (bounded) for its own copies and MMAs and
 // frees TMEM before returning.
 #include <cstdint>
+#include <cstdlib>
 
 #include "blocks.cuh"
 #include "tc.cuh"
@@ -193,7 +194,8 @@ __device__ __forceinline__ void tmem_ld_levels(uint32_t taddr, float (*v)[16]) {
 // tiles_m x tiles_n output tiles, N fastest, all K blocks).
 template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb, int kb_per, int tiles_n,
-                                                         int nitems, GramOut go, UpdOut uo, const int* gate) {
+                                                         int nitems, GramOut go, UpdOut uo, const int* gate,
+                                                         int prefetch_on) {
   if (gate && *gate == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -279,6 +281,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb
         }
         advance_pf();
       };
+      if (!prefetch_on) pf_it = nitem_cta;        // EIG_TC_PREFETCH=0
       for (int i = 0; i < PF; ++i) advance_pf();  // start PF positions ahead
       for (int it = 0; it < nitem_cta && !*abort; ++it) {
         const int item = item0 + it * item_step;
@@ -396,6 +399,15 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
+// EIG_TC_PREFETCH=0 turns the L2 prefetch of the producer off (tuning)
+int prefetch_flag() {
+  static const int v = [] {
+    const char* e = std::getenv("EIG_TC_PREFETCH");
+    return (e && e[0] == '0') ? 0 : 1;
+  }();
+  return v;
+}
+
 template <int MODE>
 cudaError_t set_smem5() {
   static thread_local int done_dev = -1;
@@ -441,7 +453,7 @@ cudaError_t tc5_gram(int64_t n, int a, int b, const void* slu, const void* slv, 
   UpdOut uo{};
   dim3 grid(tn, tm, ns);
   tc5_kernel<0><<<grid, THREADS, SMEM, st>>>(opnd(slu, n, a), opnd(slv, n, b), int(nkb), int(kb_per), tn, tm * tn,
-                                             go, uo, gate);
+                                             go, uo, gate, prefetch_flag());
   count_launches(1);
   return cudaGetLastError();
 }
@@ -463,7 +475,7 @@ cudaError_t tc5_update(int64_t n, int s, int c, const void* slu, const void* slc
   uo.beta = dd{bh, float(beta - double(bh))};
   uo.has_beta = beta != 0.0;
   tc5_kernel<1><<<(unsigned)grid, THREADS, SMEM, st>>>(opnd(slu, s, n), opnd(slc, s, c), int(nkb), int(nkb), tn,
-                                                       int(items), go, uo, gate);
+                                                       int(items), go, uo, gate, prefetch_flag());
   count_launches(1);
   return cudaGetLastError();
 }
