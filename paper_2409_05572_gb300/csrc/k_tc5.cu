@@ -121,10 +121,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = uint64_t((saddr >> 4) & 0x3FFFu);
   d |= uint64_t((LBO >> 4) & 0x3FFFu) << 16;
@@ -194,8 +190,7 @@ __device__ __forceinline__ void tmem_ld_levels(uint32_t taddr, float (*v)[16]) {
 // tiles_m x tiles_n output tiles, N fastest, all K blocks).
 template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb, int kb_per, int tiles_n,
-                                                         int nitems, GramOut go, UpdOut uo, const int* gate,
-                                                         int prefetch_on) {
+                                                         int nitems, GramOut go, UpdOut uo, const int* gate) {
   if (gate && *gate == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -259,35 +254,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb
     if (lane == 0) {
       // ---------------- producer ----------------
       int p = 0;
-      // L2 prefetch of the tiles PF stages ahead of the copy being issued, so
-      // that the ring's copies hit L2 instead of waiting on HBM
-      constexpr int PF = NST;
-      int pf_it = 0, pf_k = 0;
-      auto advance_pf = [&]() {
-        if (++pf_k == nkb_item) {
-          pf_k = 0;
-          ++pf_it;
-        }
-      };
-      auto prefetch = [&]() {
-        if (pf_it >= nitem_cta) return;
-        const int item = item0 + pf_it * item_step;
-        const int64_t m0 = int64_t(item / tiles_n) * BM, n0 = int64_t(item % tiles_n) * BN;
-        const int64_t kb = kb0 + pf_k;
-#pragma unroll 1
-        for (int q = 0; q < S; ++q) {
-          prefetch_l2(A.sl + (int64_t(q) * nkb + kb) * A.Mp * KB + m0 * KB, A_SLICE);
-          prefetch_l2(B.sl + (int64_t(q) * nkb + kb) * B.Mp * KB + n0 * KB, B_SLICE);
-        }
-        advance_pf();
-      };
-      if (!prefetch_on) pf_it = nitem_cta;        // EIG_TC_PREFETCH=0
-      for (int i = 0; i < PF; ++i) advance_pf();  // start PF positions ahead
       for (int it = 0; it < nitem_cta && !*abort; ++it) {
         const int item = item0 + it * item_step;
         const int64_t m0 = int64_t(item / tiles_n) * BM, n0 = int64_t(item % tiles_n) * BN;
         for (int kbi = 0; kbi < nkb_item; ++kbi, ++p) {
-          prefetch();
           const int s = p % NST;
           if (p >= NST && !mbar_wait(smem_u32(&bar_empty[s]), uint32_t((p / NST - 1) & 1), abort)) break;
           const uint32_t fb = smem_u32(&bar_full[s]);
@@ -399,15 +369,6 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
-// EIG_TC_PREFETCH=0 turns the L2 prefetch of the producer off (tuning)
-int prefetch_flag() {
-  static const int v = [] {
-    const char* e = std::getenv("EIG_TC_PREFETCH");
-    return (e && e[0] == '0') ? 0 : 1;
-  }();
-  return v;
-}
-
 template <int MODE>
 cudaError_t set_smem5() {
   static thread_local int done_dev = -1;
@@ -453,7 +414,7 @@ cudaError_t tc5_gram(int64_t n, int a, int b, const void* slu, const void* slv, 
   UpdOut uo{};
   dim3 grid(tn, tm, ns);
   tc5_kernel<0><<<grid, THREADS, SMEM, st>>>(opnd(slu, n, a), opnd(slv, n, b), int(nkb), int(kb_per), tn, tm * tn,
-                                             go, uo, gate, prefetch_flag());
+                                             go, uo, gate);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -475,7 +436,7 @@ cudaError_t tc5_update(int64_t n, int s, int c, const void* slu, const void* slc
   uo.beta = dd{bh, float(beta - double(bh))};
   uo.has_beta = beta != 0.0;
   tc5_kernel<1><<<(unsigned)grid, THREADS, SMEM, st>>>(opnd(slu, s, n), opnd(slc, s, c), int(nkb), int(nkb), tn,
-                                                       int(items), go, uo, gate, prefetch_flag());
+                                                       int(items), go, uo, gate);
   count_launches(1);
   return cudaGetLastError();
 }
