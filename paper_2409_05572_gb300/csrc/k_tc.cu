@@ -6,15 +6,16 @@
 // Exact splitting, a fixed-point form of Ozaki, Ogita, Oishi and Rump
 // (Numer. Algorithms 59, 2012).  Both operands of a product P = A B^T
 // (A: M x K, B: N x K, contraction over K) are cut into six integer slices
-// against a power of two shared by one CHUNK of 64 consecutive K indices of
+// against a power of two shared by one CHUNK of 128 consecutive K indices of
 // one row of A (or B): with e the exponent of the chunk's largest |x|
 // (max < 2^e),
 //   x 2^(7 - e) = s_0 + s_1 2^-8 + ... + s_5 2^-40 + r,  |s_i| <= 128,
 //   |r| <= 2^-41, i.e. r is below 2^-47 of the chunk's max.
 // Integers of magnitude <= 256 are exact in bf16, every product s_i t_j
 // (<= 2^14) is exact in the fp32 accumulators of mma.sync, and for every level
-// l = i + j <= 5 the sum over one chunk (64 K indices) of its at most six
-// products per index stays below 6 * 64 * 2^14 < 2^23, so each level
+// l = i + j <= 5 the sum over one chunk (128 K indices) of its at most six
+// products per index stays below 6 * 128 * 2^14 < 2^24, an integer that fp32
+// represents exactly, so each level
 // accumulates EXACTLY in its own fp32 accumulator, whatever order the tensor
 // core adds in.  After every chunk the six level sums are combined into a
 // double-float (two TwoSums, the small levels added into the low part: about
@@ -123,42 +124,53 @@ __device__ __forceinline__ void cp_async_wait_s() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-constexpr int SL_PITCH = 65;                       // float2 pitch of a 64 x 64 tile in shared memory
-constexpr size_t SL_SHM = size_t(2) * 64 * SL_PITCH * sizeof(float2);
+// Slicer squares: one 128-index chunk of K x 32 operand rows, 256 threads,
+// two shared-memory buffers of 128 x 33 (COLS) or 32 x 129 (ROWS) float2.
+constexpr int SQ_K = CH;   // 128
+constexpr int SQ_M = 32;
+constexpr int SL_P_COLS = SQ_M + 1, SL_P_ROWS = SQ_K + 1;
+constexpr int SL_TILE = SQ_K * SQ_M + 128;  // float2 per buffer (either pitch fits)
+constexpr size_t SL_SHM = size_t(2) * SL_TILE * sizeof(float2);
 
-// Both slicers: persistent CTAs walk the 64 x 64 squares (row block a, column
-// block b) of U, item = a * nb + b; the next square's 8-byte loads are in
-// flight (cp.async, two shared-memory buffers) while the current one is cut.
-//  COLS (Gram operand): K = rows of U, operand rows = columns of U, one
-//       exponent per (64-row chunk a, column).
-//  ROWS (update operand): K = columns of U, operand rows = rows of U, one
-//       exponent per (row, 64-column chunk b).
+// Both slicers: persistent CTAs walk the squares (a, b) of U, item = a nb + b;
+// the next square's 8-byte loads are in flight (cp.async, two shared-memory
+// buffers) while the current one is cut.
+//  COLS (Gram operand): K = rows of U, operand rows = columns of U; square =
+//       rows 128 a .. + 127 x columns 32 b .. + 31; one exponent per
+//       (128-row chunk a, column).
+//  ROWS (update operand): K = columns of U, operand rows = rows of U; square
+//       = rows 32 a .. + 31 x columns 128 b .. + 127; one exponent per
+//       (row, 128-column chunk b).
 template <bool COLS>
 __global__ void __launch_bounds__(256) tc_slice_kernel(int64_t n, Blk<dd> U, Layout o, int64_t nb, int64_t items,
                                                        const int* gate) {
   if (gate && *gate == 0) return;
+  constexpr int P = COLS ? SL_P_COLS : SL_P_ROWS;
+  constexpr int ROWS_SQ = COLS ? SQ_K : SQ_M;  // rows of U in a square
+  constexpr int COLS_SQ = COLS ? SQ_M : SQ_K;  // columns of U in a square
+  constexpr int LC = COLS_SQ, LR = 256 / COLS_SQ;  // loader: LC columns x LR rows per step
   extern __shared__ __align__(16) float2 sdraw[];
-  __shared__ float pmax[4][64];
-  __shared__ int sexp[64];
+  __shared__ float pmax[8][32];
+  __shared__ int sexp[32];
   const int t = threadIdx.x;
   const int w = U.width;
   int64_t item = blockIdx.x;
   if (item >= items) return;
   auto issue = [&](int64_t it, int buf) {
-    const int64_t r0 = (it / nb) * 64;
-    const int cb = int(it % nb) * 64;
-    const int lc = t & 63, lr = t >> 6;
+    const int64_t r0 = (it / nb) * ROWS_SQ;
+    const int cb = int(it % nb) * COLS_SQ;
+    const int lc = t % LC, lr = t / LC;
     const int c = cb + lc;
     const dd* colp = nullptr;
     int64_t cld = 0;
     if (c < w) col_lookup(U, c, colp, cld);
-    float2* dst = sdraw + buf * (64 * SL_PITCH);
+    float2* dst = sdraw + buf * SL_TILE;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int rr = lr + 4 * i;
+    for (int i = 0; i < ROWS_SQ / LR; ++i) {
+      const int rr = lr + LR * i;
       const int64_t r = r0 + rr;
       const bool ok = colp && r < n;
-      cp_async8(dst + rr * SL_PITCH + lc, ok ? static_cast<const void*>(colp + r * cld) : static_cast<const void*>(U.ptr[0]),
+      cp_async8(dst + rr * P + lc, ok ? static_cast<const void*>(colp + r * cld) : static_cast<const void*>(U.ptr[0]),
                 ok ? 8 : 0);
     }
     cp_async_commit_s();
@@ -173,50 +185,53 @@ __global__ void __launch_bounds__(256) tc_slice_kernel(int64_t n, Blk<dd> U, Lay
       cp_async_commit_s();
     cp_async_wait_s<1>();
     __syncthreads();
-    const float2* sd = sdraw + buf * (64 * SL_PITCH);
+    const float2* sd = sdraw + buf * SL_TILE;
     const int64_t a = item / nb, b = item % nb;
     if (COLS) {
-      const int lc = t & 63, lr = t >> 6;
+      // column maxima over the 128 rows: 8 partial maxima per column
+      const int lc = t & 31, lr = t >> 5;
       float m = 0.f;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) m = fmaxf(m, fabsf(sd[(lr + 4 * i) * SL_PITCH + lc].x));
+      for (int i = 0; i < 16; ++i) m = fmaxf(m, fabsf(sd[(lr + 8 * i) * P + lc].x));
       pmax[lr][lc] = m;
       __syncthreads();
-      if (t < 64) {
-        const float mm = fmaxf(fmaxf(pmax[0][t], pmax[1][t]), fmaxf(pmax[2][t], pmax[3][t]));
+      if (t < 32) {
+        float mm = pmax[0][t];
+#pragma unroll
+        for (int i = 1; i < 8; ++i) mm = fmaxf(mm, pmax[i][t]);
         const int e = chunk_exp(mm);
         sexp[t] = e;
-        o.ex[a * o.Mp + b * 64 + t] = e == ZERO_EXP ? 0 : e;
+        o.ex[a * o.Mp + b * SQ_M + t] = e == ZERO_EXP ? 0 : e;
       }
     } else {
-      // row maxima: 4 threads per row, columns 8 part + i and 8 part + 32 + i
-      const int row = t >> 2, part = t & 3;
+      // row maxima over the 128 columns: 8 threads per row
+      const int row = t >> 3, part = t & 7;
       float m = 0.f;
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
-        m = fmaxf(m, fmaxf(fabsf(sd[row * SL_PITCH + 8 * part + i].x), fabsf(sd[row * SL_PITCH + 8 * part + 32 + i].x)));
+      for (int i = 0; i < 16; ++i) m = fmaxf(m, fabsf(sd[row * P + part + 8 * i].x));
       m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
       m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
       if (part == 0) {
         const int e = chunk_exp(m);
         sexp[row] = e;
-        o.ex[b * o.Mp + a * 64 + row] = e == ZERO_EXP ? 0 : e;
+        o.ex[b * o.Mp + a * SQ_M + row] = e == ZERO_EXP ? 0 : e;
       }
     }
     __syncthreads();
-    // thread -> (K block kbl, operand row idx of the square, K values k0 .. k0 + 15)
-    const int kbl = t >> 7, idx = (t & 127) >> 1, k0 = (t & 1) * 16;
+    // thread -> (group g of 16 K indices, operand row idx of the square)
+    const int g = t >> 5, idx = t & 31;
     const float scale = exp_scale(sexp[idx]);
     float v[16][S];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      const float2 x = COLS ? sd[(kbl * KB + k0 + i) * SL_PITCH + idx] : sd[idx * SL_PITCH + kbl * KB + k0 + i];
+      const float2 x = COLS ? sd[(16 * g + i) * P + idx] : sd[idx * P + 16 * g + i];
       cut(x.x, x.y, scale, v[i]);
     }
-    const int64_t kb = (COLS ? a : b) * KBC + kbl;
-    const int64_t orow = (COLS ? b : a) * 64 + idx;
+    const int64_t kb = (COLS ? a : b) * KBC + (g >> 1);
+    const int64_t orow = (COLS ? b : a) * SQ_M + idx;
 #pragma unroll
-    for (int q = 0; q < S; ++q) store16(o.sl + o.block(q, kb), orow, k0, v, q);
+    for (int q = 0; q < S; ++q) store16(o.sl + o.block(q, kb), orow, (g & 1) * 16, v, q);
     __syncthreads();  // the buffer is refilled by the next issue
     buf ^= 1;
   }
@@ -229,19 +244,19 @@ __global__ void __launch_bounds__(256) tc_slice_kernel(int64_t n, Blk<dd> U, Lay
 __global__ void __launch_bounds__(256) tc_slice_coef_kernel(int s, int c, const double* __restrict__ C, int64_t ldc,
                                                             double scale, Layout o, const int* gate) {
   if (gate && *gate == 0) return;
-  const int j0 = blockIdx.x * 64;
+  const int j0 = blockIdx.x * 32;
   const int kc = blockIdx.y;
   const int k00 = kc * CH;
-  __shared__ double sc[CH][65];
-  __shared__ double pmax[4][64];
-  __shared__ int sexp[64];
+  __shared__ double sc[CH][33];
+  __shared__ double pmax[8][32];
+  __shared__ int sexp[32];
   const int t = threadIdx.x;
   {
-    const int lj = t & 63, lk = t >> 6;
+    const int lj = t & 31, lk = t >> 5;
     const int j = j0 + lj;
     double m = 0.0;
-    for (int i = 0; i < CH / 4; ++i) {
-      const int kk = lk + 4 * i;
+    for (int i = 0; i < CH / 8; ++i) {
+      const int kk = lk + 8 * i;
       const int k = k00 + kk;
       const double x = (j < c && k < s) ? scale * C[int64_t(k) * ldc + j] : 0.0;
       sc[kk][lj] = x;
@@ -250,21 +265,21 @@ __global__ void __launch_bounds__(256) tc_slice_coef_kernel(int s, int c, const 
     pmax[lk][lj] = m;
   }
   __syncthreads();
-  if (t < 64) {
-    const double mm = fmax(fmax(pmax[0][t], pmax[1][t]), fmax(pmax[2][t], pmax[3][t]));
+  if (t < 32) {
+    double mm = pmax[0][t];
+    for (int i = 1; i < 8; ++i) mm = fmax(mm, pmax[i][t]);
     int e = ZERO_EXP;
     if (mm >= 0x1p-100) frexp(mm, &e);
     sexp[t] = e;
     o.ex[int64_t(kc) * o.Mp + j0 + t] = e == ZERO_EXP ? 0 : e;
   }
   __syncthreads();
-  const int kbl = t >> 7, col = (t & 127) >> 1, k0 = (t & 1) * 16;
-  const int j = j0 + col;
+  const int g = t >> 5, col = t & 31;
   const int e = sexp[col];
   float v[16][S];
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
-    double x = e == ZERO_EXP ? 0.0 : ldexp(sc[kbl * KB + k0 + i][col], 7 - e);
+    double x = e == ZERO_EXP ? 0.0 : ldexp(sc[16 * g + i][col], 7 - e);
 #pragma unroll
     for (int q = 0; q < S; ++q) {
       const double r = rint(x);
@@ -272,9 +287,9 @@ __global__ void __launch_bounds__(256) tc_slice_coef_kernel(int s, int c, const 
       x = (x - r) * 256.0;
     }
   }
-  const int64_t kb = int64_t(kc) * KBC + kbl;
+  const int64_t kb = int64_t(kc) * KBC + (g >> 1);
 #pragma unroll
-  for (int q = 0; q < S; ++q) store16(o.sl + o.block(q, kb), j, k0, v, q);
+  for (int q = 0; q < S; ++q) store16(o.sl + o.block(q, kb), j0 + col, (g & 1) * 16, v, q);
 }
 
 // ---------------------------------------------------------------------------
@@ -566,23 +581,23 @@ cudaError_t tc_slice_cols(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t s
   const int w = U.width;
   if (w <= 0 || n <= 0) return cudaSuccess;
   const Layout o = layout(buf, n, w);
-  // squares: 64-row chunks of U (K) x 64-column blocks (operand rows, padded)
-  return slice_launch<true>(n, U, o, cdiv(n, CH), o.Mp / 64, st, gate);
+  // squares: 128-row chunks of U (K) x 32-column blocks (operand rows, padded)
+  return slice_launch<true>(n, U, o, cdiv(n, CH), o.Mp / SQ_M, st, gate);
 }
 
 cudaError_t tc_slice_rows(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t st, const int* gate) {
   const int w = U.width;
   if (w <= 0 || n <= 0) return cudaSuccess;
   const Layout o = layout(buf, w, n);
-  // squares: 64-row blocks of U (operand rows, padded) x 64-column chunks (K)
-  return slice_launch<false>(n, U, o, o.Mp / 64, cdiv(w, CH), st, gate);
+  // squares: 32-row blocks of U (operand rows, padded) x 128-column chunks (K)
+  return slice_launch<false>(n, U, o, o.Mp / SQ_M, cdiv(w, CH), st, gate);
 }
 
 cudaError_t tc_slice_coef(int s, int c, const double* C, int64_t ldc, double scale, void* buf, cudaStream_t st,
                           const int* gate) {
   if (s <= 0 || c <= 0) return cudaSuccess;
   const Layout o = layout(buf, s, c);
-  dim3 grid((unsigned)(o.Mp / 64), (unsigned)cdiv(s, CH));
+  dim3 grid((unsigned)(o.Mp / 32), (unsigned)cdiv(s, CH));
   max_carveout(tc_slice_coef_kernel);
   tc_slice_coef_kernel<<<grid, 256, 0, st>>>(s, c, C, ldc, scale, o, gate);
   count_launches(1);

@@ -14,7 +14,7 @@
 //                        (M = 128, N = 64 .. 256, K = 16, bf16 in, fp32 out)
 //                        into the TMEM accumulators of the levels i + j (6 x 64
 //                        columns); tcgen05.commit frees the stage and, after
-//                        the second K block of a 64-index chunk, hands the
+//                        the last K block of a 128-index chunk, hands the
 //                        six exact level sums to the flush warps.
 //   warps 2..9           flush: each warp owns the 32 TMEM lanes (tile rows)
 //                        of its lane quarter and 32 of the 64 columns; per

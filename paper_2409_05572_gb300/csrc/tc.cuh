@@ -2,7 +2,7 @@
 // slicing and the mma.sync product; k_tc5.cu: the tcgen05 product).
 //
 // Slice buffer of an operand with contraction length K and M operand rows
-// (M padded to Mp, a multiple of 128; K padded to whole 64-index chunks):
+// (M padded to Mp, a multiple of 128; K padded to whole 128-index chunks):
 //   slices: [TC_S][nkb][Mp][32] bf16, nkb = 32-index K blocks.  Inside one
 //           (slice, K block) the Mp x 32 values are stored as 8 x 8 core
 //           matrices, rows of 16 bytes: element (r, k) at
@@ -11,7 +11,7 @@
 //           copy) and its shared-memory image is the no-swizzle K-major layout
 //           of tcgen05.mma (core matrices 128 bytes apart along K, 512 bytes
 //           apart along M).
-//   exponents: [nkc][Mp] int after the slices, nkc = 64-index chunks.
+//   exponents: [nkc][Mp] int after the slices, nkc = 128-index chunks.
 // Padding rows and K indices hold zeros.
 #pragma once
 #include <cuda_bf16.h>
@@ -23,7 +23,7 @@ namespace tc {
 
 constexpr int S = 6;        // slices per value
 constexpr int KB = 32;      // K indices per block
-constexpr int CH = 64;      // K indices per chunk (one exponent, one exact-level flush)
+constexpr int CH = 128;     // K indices per chunk (one exponent, one exact-level flush)
 constexpr int KBC = CH / KB;
 constexpr int MPAD = 128;   // operand rows are padded to this
 constexpr int ZERO_EXP = -1000;
@@ -59,10 +59,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - z)) + (b - z);
 }
 
-// (hi, lo) = sum_l a_l 2^(-8 l) for exact integer level sums |a_l| < 2^23:
+// (hi, lo) = sum_l a_l 2^(-8 l) for exact integer level sums |a_l| < 2^24:
 // the two leading terms error-free (TwoSum), the rest into lo.  With
-// |a_0| <= 2^20 (one product per K index), |lo| < 2^-1 and the four roundings
-// of lo stay below 2^-24, i.e. 2^-44 of the largest possible chunk sum.
+// |a_0| <= 2^21 (one product per K index), |lo| < 2^0 and the four roundings
+// of lo stay below 2^-23, i.e. 2^-44 of the largest possible chunk sum.
 __device__ __forceinline__ void combine_levels(float a0, float a1, float a2, float a3, float a4, float a5,
                                                float& hi, float& lo) {
   float h, e1, e2;

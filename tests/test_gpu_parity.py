@@ -288,8 +288,8 @@ def test_update_parity(arith, s, c, beta):
     assert np.all(np.abs(got - ref) <= tol * scale + 1e-300)
 
 
-def row_chunk_max(X, cols=64):
-    """max |x| over each row's chunks of 64 columns: (rows, chunks), counts."""
+def row_chunk_max(X, cols=128):
+    """max |x| over each row's chunks of 128 columns: (rows, chunks), counts."""
     m, k = X.shape
     nch = -(-k // cols)
     P = np.zeros((m, nch * cols))
@@ -303,8 +303,8 @@ def row_chunk_max(X, cols=64):
                                         (3001, 385, 257, 0.0), (1, 3, 2, 2.5), (65, 1, 129, -1.0)])
 def test_update_tc_parity(n, s, c, beta):
     """Y = U C + beta Y on the tensor cores (EIG_ARITH_DF64_TC): per output
-    at most about 24.4 * 2^-48 * sum over 64-column chunks k of
-    64 * max|U(row, k)| * max|C(k, col)|, plus double-float accumulation."""
+    at most about 24.4 * 2^-48 * sum over 128-column chunks k of
+    128 * max|U(row, k)| * max|C(k, col)|, plus double-float accumulation."""
     rng = np.random.default_rng(n + s * 3 + c)
     U = rng.standard_normal((n, s)) * 2.0 ** rng.integers(-20, 20, s)
     Cm = rng.standard_normal((s, c))
