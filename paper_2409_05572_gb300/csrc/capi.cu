@@ -119,7 +119,7 @@ int cholqr2_t(int64_t n, int w, void* W, int64_t ldw, int* status_out, cudaStrea
   const size_t esz = sizeof(T);
   Tmp scr(st), G(st), Rinv(st), work(st), Cs(st), tmp(st), flags(st);
   if (scr.alloc(sizeof(double) * gram_scratch_elems(n, w, w, true)) || G.alloc(sizeof(double) * w * w) ||
-      Rinv.alloc(sizeof(double) * w * w) || work.alloc(sizeof(double) * (size_t(w) * w + w)) ||
+      Rinv.alloc(sizeof(double) * w * w) || work.alloc(sizeof(double) * (size_t(w) * w + 2 * size_t(w))) ||
       Cs.alloc(sizeof(S) * w * w) || tmp.alloc(esz * size_t(n) * w) || flags.alloc(sizeof(int) * 4))
     return EIG_ENOMEM;
   int* fl = static_cast<int*>(flags.p);

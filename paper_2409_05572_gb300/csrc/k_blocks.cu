@@ -379,7 +379,7 @@ static int gram_nsplit(int64_t n, int a, int b, bool sym) {
   if (sym && ta != tb) tiles = ta * tb;
   int target = num_sms() * 4;
   int ns = (target + tiles - 1) / tiles;
-  int64_t max_ns = cdiv(n, GK * 8);
+  int64_t max_ns = cdiv(n, GK * 2);  // at least 64 rows per split (short inputs: more splits)
   if (ns > max_ns) ns = (int)max_ns;
   if (ns < 1) ns = 1;
   return ns;

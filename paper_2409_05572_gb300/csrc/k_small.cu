@@ -22,6 +22,7 @@ namespace eig {
 // ---------------------------------------------------------------------------
 __device__ bool chol_upper_inplace(double* Rm, int w, int ld, const double* diag0, double* sh) {
   // Rm holds G (upper triangle used); on success its upper triangle is R.
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int j = 0; j < w; ++j) {
     if (threadIdx.x == 0) {
       const double d = Rm[j * ld + j];
@@ -38,11 +39,10 @@ __device__ bool chol_upper_inplace(double* Rm, int w, int ld, const double* diag
     if (r < 0.0) return false;
     for (int k = j + 1 + threadIdx.x; k < w; k += blockDim.x) Rm[j * ld + k] /= r;
     __syncthreads();
-    const int m = w - j - 1;
-    const int64_t tot = int64_t(m) * m;
-    for (int64_t idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-      const int i = j + 1 + int(idx / m), k = j + 1 + int(idx % m);
-      if (k >= i) Rm[i * ld + k] -= Rm[j * ld + i] * Rm[j * ld + k];
+    // trailing update of the upper triangle: warps over rows, lanes over columns
+    for (int i = j + 1 + warp; i < w; i += nw) {
+      const double rji = Rm[j * ld + i];
+      for (int k = i + lane; k < w; k += 32) Rm[i * ld + k] -= rji * Rm[j * ld + k];
     }
     __syncthreads();
   }
@@ -56,13 +56,12 @@ __global__ void __launch_bounds__(512) chol_rinv_kernel(int w, int64_t nrows, co
   if (gate && *gate == 0) return;
   extern __shared__ double smem[];
   __shared__ double sh[2];
-  const bool in_smem = (size_t(w) * w + w) * sizeof(double) <= 160 * 1024;
+  const bool in_smem = (size_t(w) * w + 2 * size_t(w)) * sizeof(double) <= 160 * 1024;
   double* Rm = in_smem ? smem : work;
-  double* diag0 = in_smem ? smem + size_t(w) * w : work + size_t(w) * w;
-  for (int64_t idx = threadIdx.x; idx < int64_t(w) * w; idx += blockDim.x) {
-    const int i = int(idx / w), k = int(idx % w);
-    Rm[idx] = G[i * ldg + k];
-  }
+  double* diag0 = (in_smem ? smem : work) + size_t(w) * w;
+  double* dinv = diag0 + w;
+  for (int i = threadIdx.x >> 5; i < w; i += blockDim.x >> 5)
+    for (int k = threadIdx.x & 31; k < w; k += 32) Rm[i * w + k] = G[i * ldg + k];
   for (int i = threadIdx.x; i < w; i += blockDim.x) diag0[i] = G[i * ldg + i];
   __syncthreads();
   int st = 0;
@@ -76,10 +75,8 @@ __global__ void __launch_bounds__(512) chol_rinv_kernel(int w, int64_t nrows, co
     }
     __syncthreads();
     const double shift = sh[1];
-    for (int64_t idx = threadIdx.x; idx < int64_t(w) * w; idx += blockDim.x) {
-      const int i = int(idx / w), k = int(idx % w);
-      Rm[idx] = G[i * ldg + k] + (i == k ? shift : 0.0);
-    }
+    for (int i = threadIdx.x >> 5; i < w; i += blockDim.x >> 5)
+      for (int k = threadIdx.x & 31; k < w; k += 32) Rm[i * w + k] = G[i * ldg + k] + (i == k ? shift : 0.0);
     __syncthreads();
     ok = chol_upper_inplace(Rm, w, w, diag0, sh);
     st = ok ? 1 : 2;
@@ -90,28 +87,32 @@ __global__ void __launch_bounds__(512) chol_rinv_kernel(int w, int64_t nrows, co
       Rinv[idx] = (idx / w == idx % w) ? 1.0 : 0.0;
     return;
   }
-  // R^{-1}, column by column: Rinv[i][j] = -(sum_{k=i}^{j-1} Rinv[i][k] R[k][j]) / R[j][j]
-  for (int64_t idx = threadIdx.x; idx < int64_t(w) * w; idx += blockDim.x) Rinv[idx] = 0.0;
+  // R^{-1}: diagonal 1 / R_jj in dinv, Rinv[i][j] (i < j) kept in the free
+  // lower triangle at Rm[j][i]; column j from the finished columns < j:
+  // Rinv[i][j] = -(sum_{k=i}^{j-1} Rinv[i][k] R[k][j]) / R[j][j], one warp per i
+  for (int j = threadIdx.x; j < w; j += blockDim.x) dinv[j] = 1.0 / Rm[j * w + j];
   __syncthreads();
-  for (int j = 0; j < w; ++j) {
-    const double rjj = Rm[j * w + j];
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-      if (i == j) {
-        Rinv[j * w + j] = 1.0 / rjj;
-      } else {
-        double s = 0.0;
-        for (int k = i; k < j; ++k) s += Rinv[i * w + k] * Rm[k * w + j];
-        Rinv[i * w + j] = -s / rjj;
-      }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = 1; j < w; ++j) {
+    for (int i = warp; i < j; i += nw) {
+      double acc = 0.0;
+      for (int k = i + lane; k < j; k += 32) acc += (k == i ? dinv[i] : Rm[k * w + i]) * Rm[k * w + j];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) Rm[j * w + i] = -acc * dinv[j];
     }
     __syncthreads();
   }
+  for (int i = threadIdx.x >> 5; i < w; i += blockDim.x >> 5)
+    for (int k = threadIdx.x & 31; k < w; k += 32)
+      Rinv[i * w + k] = k == i ? dinv[i] : (k > i ? Rm[k * w + i] : 0.0);
   if (threadIdx.x == 0) *status = st;
 }
 
 cudaError_t chol_rinv(int w, int64_t nrows, const double* G, int64_t ldg, double* Rinv, double* work,
                       int* status, cudaStream_t st, const int* gate, double unit_round) {
-  const size_t need = (size_t(w) * w + w) * sizeof(double);
+  // Cholesky factor, first diagonal of G and 1 / R_jj (w^2 + 2w float64): in
+  // shared memory when they fit, else in work (which must hold them)
+  const size_t need = (size_t(w) * w + 2 * size_t(w)) * sizeof(double);
   const size_t shm = need <= 160 * 1024 ? need : 0;
   static bool attr = false;
   if (!attr) {
@@ -165,7 +166,7 @@ HLWork hl_carve(void* work, int m, int q) {
   w.Y2 = take(size_t(m) * q);
   w.G = take(size_t(q) * q);
   w.Rinv = take(size_t(q) * q);
-  w.cholw = take(size_t(q) * q + q);
+  w.cholw = take(size_t(q) * q + 2 * size_t(q));
   w.Cs = take(size_t(m) * q);
   w.scr = take(gram_scratch_elems(m, q, q, true));
   w.status = reinterpret_cast<int*>(c);
@@ -175,7 +176,7 @@ HLWork hl_carve(void* work, int m, int q) {
 
 size_t hl_work_bytes(int s, int nnow, int nlock) {
   const size_t m = size_t(s - nnow), q = size_t(nnow - nlock);
-  return 3 * al256(m * q * sizeof(double)) + 2 * al256(q * q * sizeof(double)) + al256((q * q + q) * sizeof(double)) +
+  return 3 * al256(m * q * sizeof(double)) + 2 * al256(q * q * sizeof(double)) + al256((q * q + 2 * q) * sizeof(double)) +
          al256(gram_scratch_elems(int64_t(m), int(q), int(q), true) * sizeof(double)) + 256;
 }
 

@@ -7,7 +7,7 @@ namespace eig {
 // R^{-1} (w x w upper, leading dimension w) of the Cholesky factor of G;
 // unit_round is the unit roundoff of the data G came from (it sets the shift);
 // *status: 0 plain, 1 shifted (Fukaya et al. 2020), 2 broken down.  work:
-// (w*w + w) doubles, used when the factor does not fit in shared memory.
+// (w*w + 2w) doubles, used when the factor does not fit in shared memory.
 cudaError_t chol_rinv(int w, int64_t nrows, const double* G, int64_t ldg, double* Rinv, double* work,
                       int* status, cudaStream_t st, const int* gate = nullptr,
                       double unit_round = 1.1102230246251565e-16);

@@ -1287,7 +1287,7 @@ size_t footprint_bytes(int64_t n, int64_t nnz, int nev, int k_max, int nes, int 
   b += 4 * 8 * size_t(n) * LDS;                  // S, AS (two copies each)
   b += 2 * 8 * size_t(n) * std::max(wtw, size_t(nev));
   b += 8 * size_t(n) * nev;                      // V
-  b += 8 * (smax * smax * 2 + cq * cq * 2 + cq + smax * k_max + smax * (2 * k_max + 1) + 4 * smax);
+  b += 8 * (smax * smax * 2 + cq * cq * 2 + 2 * cq + smax * k_max + smax * (2 * k_max + 1) + 4 * smax);
   b += 8 * (size_t(2) * num_sms() * 4 * 64 * 64 + smax * smax + 4096);
   b += 8 * residual_scratch_elems(n, k_max);
   b += syev_work_bytes(int(smax)) + hl_work_bytes(int(smax), k_max, 0) + 8 * smax * smax;
@@ -1440,7 +1440,7 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
   // mixed form promotes, [X, P] (<= 2 k_max)
   h->cqmax = std::max(h->wtw, 2 * k_max);
   AL(h->Rinv, sizeof(double) * size_t(h->cqmax) * h->cqmax);
-  AL(h->cholw, sizeof(double) * (size_t(h->cqmax) * h->cqmax + h->cqmax));
+  AL(h->cholw, sizeof(double) * (size_t(h->cqmax) * h->cqmax + 2 * size_t(h->cqmax)));
   AL(h->Z, sizeof(double) * size_t(smax) * smax);
   AL(h->lamd, sizeof(double) * smax);
   AL(h->CP, sizeof(double) * size_t(smax) * k_max);
