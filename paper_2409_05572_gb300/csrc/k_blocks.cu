@@ -147,25 +147,46 @@ __global__ void __launch_bounds__(256) spmm_kernel(
         aj = scale ? scale_val<A>(v, alpha) : P::stage(v);
       }
       const int cnt = min(G, end - base);
-      for (int t = 0; t < cnt; ++t) {
-        const int c = __shfl_sync(mask, cj, gbase + t, 32);
-        const S a = shfl_t<S>(mask, aj, gbase + t, 32);
-        const T* vrow = V + int64_t(c) * ldv;
+      // UNR nonzeros per step: all their row loads are issued before the
+      // multiply-adds, so a warp keeps several neighbour rows in flight
+      constexpr int UNR = MAXT <= 2 ? 4 : (MAXT <= 4 ? 2 : 1);
+      for (int t0 = 0; t0 < cnt; t0 += UNR) {
+        const T* vrow[UNR];
+        S a[UNR];
+        bool ok[UNR];
 #pragma unroll
-        for (int s = 0; s < MAXT; ++s) {
-          const int col = (g + s * G) * VEC;
-          if (col < w) {
-            T x[VEC];
-            if (col + VEC <= w) {
-              VecIO<T, VEC>::load(vrow + col, x);
-            } else {
-#pragma unroll
-              for (int v = 0; v < VEC; ++v) x[v] = (col + v < w) ? vrow[col + v] : T{};
-            }
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) P::mac(acc[s][v], a, P::stage(x[v]));
-          }
+        for (int u = 0; u < UNR; ++u) {
+          const int tt = min(t0 + u, cnt - 1);  // every lane of the group shuffles
+          const int c = __shfl_sync(mask, cj, gbase + tt, 32);
+          a[u] = shfl_t<S>(mask, aj, gbase + tt, 32);
+          ok[u] = t0 + u < cnt;
+          vrow[u] = V + int64_t(c) * ldv;
         }
+        T x[UNR][MAXT][VEC];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+#pragma unroll
+          for (int s = 0; s < MAXT; ++s) {
+            const int col = (g + s * G) * VEC;
+            if (ok[u] && col < w) {
+              if (col + VEC <= w) {
+                VecIO<T, VEC>::load(vrow[u] + col, x[u][s]);
+              } else {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) x[u][s][v] = (col + v < w) ? vrow[u][col + v] : T{};
+              }
+            }
+          }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+#pragma unroll
+          for (int s = 0; s < MAXT; ++s) {
+            const int col = (g + s * G) * VEC;
+            if (ok[u] && col < w) {
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) P::mac(acc[s][v], a[u], P::stage(x[u][s][v]));
+            }
+          }
       }
     }
 #pragma unroll
