@@ -46,8 +46,8 @@ TRAFFIC_RATIO = {"gram": 1.387 / 0.805, "update": 1.447 / 1.342}
 # the same for the tensor-core classes (slicing + product kernels), from ncu
 # captures at n = 262,144 (profiles/tc5_gram_*.md, profiles/tc5_update_*.md):
 # DRAM bytes of the class's kernels / the class's algorithmic bytes
-TC_TRAFFIC_RATIO = {"gram": (0.805 + 1.299 + 1.219 + 0.005) / 0.805,
-                    "update": (0.805 + 1.299 + 1.217 + 0.513) / 1.342}
+TC_TRAFFIC_RATIO = {"gram": (0.809 + 1.167 + 1.213 + 0.001) / 0.805,
+                    "update": (0.001 + 0.809 + 1.166 + 1.215 + 0.509) / 1.342}
 
 
 def peaks():

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) spmm_kernel(
       const int cnt = min(G, end - base);
       // UNR nonzeros per step: all their row loads are issued before the
       // multiply-adds, so a warp keeps several neighbour rows in flight
-      constexpr int UNR = MAXT <= 2 ? 4 : (MAXT <= 4 ? 2 : 1);
+      constexpr int UNR = MAXT <= 4 ? 2 : 1;
       for (int t0 = 0; t0 < cnt; t0 += UNR) {
         const T* vrow[UNR];
         S a[UNR];
