@@ -341,20 +341,47 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb
       }
       if (!ok) break;
       const int64_t r = m0 + rloc;
+      const int64_t c0 = n0 + 32 * half;
       if (r < A.M) {
+        // update: when the thread's 32 columns are one contiguous run of one
+        // segment of Y, 16-byte aligned, write them as 16 two-element vectors
+        bool fast = false;
+        dd* yrow = nullptr;
+        if (MODE == 1 && c0 + 32 <= B.M) {
+          int sg = 0;
+          while (sg + 1 < uo.Y.nseg && c0 >= uo.Y.start[sg + 1]) ++sg;
+          yrow = uo.Y.ptr[sg] + r * uo.Y.ld[sg] + (c0 - uo.Y.start[sg]);
+          fast = c0 + 32 <= uo.Y.start[sg + 1] && (reinterpret_cast<uintptr_t>(yrow) & 15) == 0;
+        }
+        if (fast) {
+          float4* y4 = reinterpret_cast<float4*>(yrow);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int64_t col = n0 + 32 * half + j;
-          if (col < B.M) {
-            if (MODE == 0) {
-              go.part[int64_t(blockIdx.z) * A.M * B.M + r * B.M + col] =
-                  double(master[j].hi) + double(master[j].lo);
-            } else {
-              dd* yp = uo.Y.at(r, int(col));
-              dd v = master[j];
-              if (uo.has_beta) dd_mac(v, *yp, uo.beta);
-              dd_renorm(v);
-              *yp = v;
+          for (int j = 0; j < 32; j += 2) {
+            dd v0 = master[j], v1 = master[j + 1];
+            if (uo.has_beta) {
+              const float4 old = y4[j / 2];
+              dd_mac(v0, dd{old.x, old.y}, uo.beta);
+              dd_mac(v1, dd{old.z, old.w}, uo.beta);
+            }
+            dd_renorm(v0);
+            dd_renorm(v1);
+            y4[j / 2] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t col = c0 + j;
+            if (col < B.M) {
+              if (MODE == 0) {
+                go.part[int64_t(blockIdx.z) * A.M * B.M + r * B.M + col] =
+                    double(master[j].hi) + double(master[j].lo);
+              } else {
+                dd* yp = uo.Y.at(r, int(col));
+                dd v = master[j];
+                if (uo.has_beta) dd_mac(v, *yp, uo.beta);
+                dd_renorm(v);
+                *yp = v;
+              }
             }
           }
         }

@@ -144,6 +144,11 @@ struct eig_handle {
   void* tcU = nullptr;
   void* tcV = nullptr;
   void* tcC = nullptr;  // slices of the update coefficients
+  // slices of the projection basis Q of an orthogonalisation, both layouts
+  // (kept for the two projections of one orth())
+  void* tcQc = nullptr;
+  void* tcQr = nullptr;
+  int qcmax = 0;
   // small float64 work
   int smax = 0;
   double *Gp = nullptr, *Rinv = nullptr, *cholw = nullptr, *Z = nullptr, *lamd = nullptr, *CP = nullptr;
@@ -320,6 +325,11 @@ struct Ops {
   static constexpr double kUnitRound = sizeof(T) == 4 ? 5.960464477539063e-08
                                        : (std::is_same<T, dd>::value ? 1.7763568394002505e-15
                                                                      : 1.1102230246251565e-16);
+  // Q of the current orth() whose slices (both layouts) are in tcQc / tcQr
+  bool qcache = false;
+  Blk<T> qblk;
+  bool q_cached(const Blk<T>& U) const { return qcache && same_blk(U, qblk); }
+
   // G = U^T V into h->Gp (leading dimension b)
   int gram(const Blk<T>& U, const Blk<T>& V, bool sym, const int* gate = nullptr) {
     const double nn = double(h->n), a = U.width, b = V.width;
@@ -328,10 +338,12 @@ struct Ops {
     if constexpr (AG == Arith::DF64) {
       if (h->tcU) {  // tensor-core product on exact bf16 slices
         const bool one = same_blk(U, V);
-        CK(tc_slice_cols(h->n, U, h->tcU, st(), gate));
+        const bool ucached = q_cached(U);
+        void* su = ucached ? h->tcQc : h->tcU;
+        if (!ucached) CK(tc_slice_cols(h->n, U, h->tcU, st(), gate));
         if (!one) CK(tc_slice_cols(h->n, V, h->tcV, st(), gate));
-        CK(gram_tc_product(h->n, U.width, V.width, h->tcU, one ? h->tcU : h->tcV, sym, h->Gp, V.width, h->gscr,
-                           st(), gate));
+        CK(gram_tc_product(h->n, U.width, V.width, su, one ? su : h->tcV, sym, h->Gp, V.width, h->gscr, st(),
+                           gate));
         return EIG_OK;
       }
     }
@@ -349,8 +361,9 @@ struct Ops {
         }
         const double nn = double(h->n);
         Prof p(h, EIG_K_UPDATE, 2.0 * nn * U.width * c, E * nn * (U.width + c * (beta != 0.0 ? 2.0 : 1.0)));
-        CK(tc_slice_rows(h->n, U, h->tcU, st(), gate));
-        CK(update_tc_product(h->n, U.width, c, h->tcU, h->tcC, Y, beta, st(), gate));
+        const bool ucached = q_cached(U);
+        if (!ucached) CK(tc_slice_rows(h->n, U, h->tcU, st(), gate));
+        CK(update_tc_product(h->n, U.width, c, ucached ? h->tcQr : h->tcU, h->tcC, Y, beta, st(), gate));
         return EIG_OK;
       }
     }
@@ -459,6 +472,27 @@ struct Ops {
   // projection + CholeskyQR (a third CholeskyQR when the first needed the
   // shift).  Dmid is scratch; Dsrc is clobbered (Ddst may alias Dsrc).
   int orth(const Blk<T>& Q, const Blk<T>& Dsrc, const Blk<T>& Dmid, const Blk<T>& Ddst, bool trace = false) {
+    // tensor-core form: Q does not change during the orthogonalisation, so
+    // its slices are made once, in both layouts, for both projections
+    struct Clear {
+      bool& f;
+      ~Clear() { f = false; }
+    } clear{qcache};
+    if constexpr (AU == Arith::DF64 && AG == Arith::DF64) {
+      if (h->tcQc && Q.width > 0 && Q.width <= h->qcmax) {
+        const double nn = double(h->n);
+        {
+          Prof p(h, EIG_K_GRAM, 0.0, E * nn * Q.width);
+          CK(tc_slice_cols(h->n, Q, h->tcQc, st()));
+        }
+        {
+          Prof p(h, EIG_K_UPDATE, 0.0, E * nn * Q.width);
+          CK(tc_slice_rows(h->n, Q, h->tcQr, st()));
+        }
+        qcache = true;
+        qblk = Q;
+      }
+    }
     int rc;
     if ((rc = project(Q, Dsrc))) return rc;
     if (trace) dbg("  after projection 1", Dsrc);
@@ -1235,6 +1269,8 @@ void free_all(eig_handle* h) {
   F(h->tcU);
   F(h->tcV);
   F(h->tcC);
+  F(h->tcQc);
+  F(h->tcQr);
   F(h->Gp);
   F(h->Rinv);
   F(h->cholw);
@@ -1292,7 +1328,8 @@ size_t footprint_bytes(int64_t n, int64_t nnz, int nev, int k_max, int nes, int 
   b += 8 * residual_scratch_elems(n, k_max);
   b += syev_work_bytes(int(smax)) + hl_work_bytes(int(smax), k_max, 0) + 8 * smax * smax;
   if (gram_tc && form != EIG_FORM_F64)
-    b += 2 * tc_operand_bytes(n, int(smax)) + tc_slice_bytes(int64_t(smax), 2 * k_max + 1);
+    b += 2 * tc_operand_bytes(n, int(smax)) + tc_slice_bytes(int64_t(smax), 2 * k_max + 1) +
+         2 * tc_operand_bytes(n, 2 * k_max + 1);
   return b + b / 16 + (size_t(32) << 20);        // allocator rounding and slack
 }
 
@@ -1431,6 +1468,9 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
     AL(h->tcU, tc_operand_bytes(n, 3 * k_max + 1));
     AL(h->tcV, tc_operand_bytes(n, 3 * k_max + 1));
     AL(h->tcC, tc_slice_bytes(3 * k_max + 1, 2 * k_max + 1));
+    h->qcmax = 2 * k_max + 1;  // [u0, X, P]
+    AL(h->tcQc, tc_operand_bytes(n, h->qcmax));
+    AL(h->tcQr, tc_operand_bytes(n, h->qcmax));
   }
   // small
   const int smax = 3 * k_max + 1;
