@@ -47,7 +47,7 @@ TRAFFIC_RATIO = {"gram": 1.387 / 0.805, "update": 1.447 / 1.342}
 # captures at n = 262,144 (profiles/tc5_gram_*.md, profiles/tc5_update_*.md):
 # DRAM bytes of the class's kernels / the class's algorithmic bytes
 TC_TRAFFIC_RATIO = {"gram": (0.809 + 1.167 + 1.213 + 0.001) / 0.805,
-                    "update": (0.001 + 0.809 + 1.166 + 1.215 + 0.509) / 1.342}
+                    "update": (0.001 + 0.809 + 1.166 + 1.213 + 0.506) / 1.342}
 
 
 def peaks():

@@ -59,13 +59,16 @@ extern "C" {
 #define EIG_ARITH_DF64 1  /* double-float blocks, FP32-pipe dd arithmetic    */
 #define EIG_ARITH_F32 2   /* float32 blocks, float32 arithmetic              */
 #define EIG_ARITH_C32 3   /* float32 blocks, compensated (Dot2) accumulation */
-/* eig_gram only: double-float blocks, product on the bf16 tensor cores by an
- * exact integer splitting (Ozaki et al. 2012): each value is cut into six
- * 8-bit slices against a power-of-two scale per 128-row chunk and column;
- * the slice products of levels 0..5 are summed exactly and the rest dropped,
- * an error of about 2^-48 (at most 20 * 2^-48) of max|u| max|v| over the
- * chunk per row, i.e. normwise rather than componentwise double-float
- * accuracy.  Chunk columns whose maximum is below 2^-100 count as zero. */
+/* eig_gram and eig_block_update only: double-float blocks, product on the
+ * bf16 tensor cores by an exact integer splitting (Ozaki et al. 2012): each
+ * value is cut into six 8-bit slices against a power-of-two scale shared by a
+ * 128-index chunk of the contraction (128 rows of a column of U or V for the
+ * Gram; 128 columns of a row of U and 128 rows of a column of C for the
+ * update); the slice products of levels 0..5 are summed exactly and the rest
+ * dropped, an error of about 2^-48 (at most about 28 * 2^-48) of the product
+ * of the two chunk maxima per contraction index, i.e. normwise rather than
+ * componentwise double-float accuracy.  Chunks whose maximum is below 2^-100
+ * count as zero. */
 #define EIG_ARITH_DF64_TC 4
 
 /* ---- conversions ------------------------------------------------------- */
@@ -135,7 +138,9 @@ int eig_gram_noalloc(int64_t n, int a, int b, const void *U, int64_t ldu, const 
 /* ---- a4 / a11: block update (X <- S C_X, P <- S C_P, W <- W - Q C) ------
  * Y = U C + beta * Y.  U: n x s block, C: s x c float64 row-major (device,
  * leading dimension ldc), Y: n x c block; U and Y use the element format of
- * arith.  Y must not overlap U. */
+ * arith (EIG_DF64 blocks for EIG_ARITH_DF64_TC, which also holds the bf16
+ * slices of U and C, 12 bytes per element, in temporary device memory).  Y
+ * must not overlap U. */
 int eig_block_update(int64_t n, int s, int c, const void *U, int64_t ldu, const double *C,
                      int64_t ldc, void *Y, int64_t ldy, double beta, int arith, void *stream);
 

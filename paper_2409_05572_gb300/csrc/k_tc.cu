@@ -21,15 +21,17 @@
 // double-float (two TwoSums, the small levels added into the low part: about
 // 2^-44 of the largest possible chunk sum), scaled by 2^(e_a - 7) 2^(e_b - 7)
 // (each factor a normal float for the exponents -99 .. 128 a chunk can have)
-// and added to a double-float accumulator.  The levels l >= 6 are dropped:
-// per K index that is at most 20 * 2^-48 of max|a| max|b| over the chunk,
-// and about 2^-48 of it on average.  The result is accurate normwise (to the chunk maxima)
-// rather than componentwise like the FP32-pipe double-float kernels.
+// and added to a double-float accumulator.  The levels l >= 6 are dropped
+// (per K index at most 20 * 2^-48 of max|a| max|b| over the chunk) and six
+// slices leave at most 2^-41 of the scaled value (another 8 * 2^-48): at most
+// about 28 * 2^-48 per K index in all, about 2^-48 of it on average.  The
+// result is accurate normwise (to the chunk maxima) rather than componentwise
+// like the FP32-pipe double-float kernels.
 //
-//  Gram G = U^T V:   A = U^T, B = V^T, K = the n rows; chunks are 64 rows of
+//  Gram G = U^T V:   A = U^T, B = V^T, K = the n rows; chunks are 128 rows of
 //                    one column (tc_slice_cols).
-//  Update U C:       A = U, B = C^T, K = the s columns of U; chunks are 64
-//                    columns of one row of U (tc_slice_rows) and 64 rows of one
+//  Update U C:       A = U, B = C^T, K = the s columns of U; chunks are 128
+//                    columns of one row of U (tc_slice_rows) and 128 rows of one
 //                    column of C (tc_slice_coef, from float64 C).
 //
 // The slice layout is described in tc.cuh.  Two product kernels read it:

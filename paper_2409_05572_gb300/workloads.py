@@ -211,6 +211,17 @@ def gaussian_block(n: int, k: int, seed: int) -> np.ndarray:
     return _rng(seed).standard_normal((n, k))
 
 
+def gaussian_block_cuda(n: int, k: int, seed: int):
+    """n x k row-major float64 block of i.i.d. standard normals drawn on the
+    current CUDA device by PyTorch's seeded Philox generator: test inputs of
+    full size (gigabytes), which NumPy would take tens of seconds to draw.
+    Whatever the oracle needs of it is copied to the host."""
+    import torch
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    return torch.randn(n, k, dtype=torch.float64, device="cuda", generator=g)
+
+
 @dataclass
 class Request:
     rid: int

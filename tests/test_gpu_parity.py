@@ -19,6 +19,7 @@ from oracle import blocks as B
 from oracle.chebsi import chebsi as o_chebsi
 from oracle.lobpcg import lobpcg as o_lobpcg
 from paper_2409_05572_gb300 import workloads as W
+from tc_bounds import gram_bound as tc_bound, row_chunk_max
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -156,27 +157,11 @@ def test_gram_deterministic_and_empty():
 
 # ---------------------------------------------------------------------------
 # a4 / a5 / a8: Gram on the tensor cores (EIG_ARITH_DF64_TC)
-# Error model of the exact slicing: per row at most about 24.4 * 2^-48 of
+# Error model of the exact slicing: per row at most about 28 * 2^-48 of
 # M_u M_v (M = the column's max |x| over the row's 128-row chunk) from the
 # six-slice representation and the dropped levels, plus the double-float
 # accumulation (the DF64 tolerance above).  The test allows 32 * 2^-48.
 # ---------------------------------------------------------------------------
-def chunk_max(X, rows=128):
-    n = X.shape[0]
-    nch = -(-n // rows)
-    P = np.zeros((nch * rows, X.shape[1]))
-    P[:n] = np.abs(X)
-    cnt = np.full(nch, rows, dtype=np.float64)
-    cnt[-1] = n - (nch - 1) * rows
-    return P.reshape(nch, rows, -1).max(axis=1), cnt
-
-
-def tc_bound(U, V):
-    Mu, cnt = chunk_max(U)
-    Mv, _ = chunk_max(V)
-    return RTOL["df64"] * (np.abs(U).T @ np.abs(V)) + 32 * 2.0 ** -48 * ((Mu * cnt[:, None]).T @ Mv)
-
-
 def tc_gram(U, V, sym, ldu_pad=0, ldv_pad=0):
     n, a = U.shape
     b = V.shape[1]
@@ -288,22 +273,11 @@ def test_update_parity(arith, s, c, beta):
     assert np.all(np.abs(got - ref) <= tol * scale + 1e-300)
 
 
-def row_chunk_max(X, cols=128):
-    """max |x| over each row's chunks of 128 columns: (rows, chunks), counts."""
-    m, k = X.shape
-    nch = -(-k // cols)
-    P = np.zeros((m, nch * cols))
-    P[:, :k] = np.abs(X)
-    cnt = np.full(nch, cols, dtype=np.float64)
-    cnt[-1] = k - (nch - 1) * cols
-    return P.reshape(m, nch, cols).max(axis=2), cnt
-
-
 @pytest.mark.parametrize("n,s,c,beta", [(5017, 7, 5, 0.0), (5017, 64, 64, 1.0), (5017, 130, 70, -0.37),
                                         (3001, 385, 257, 0.0), (1, 3, 2, 2.5), (65, 1, 129, -1.0)])
 def test_update_tc_parity(n, s, c, beta):
     """Y = U C + beta Y on the tensor cores (EIG_ARITH_DF64_TC): per output
-    at most about 24.4 * 2^-48 * sum over 128-column chunks k of
+    at most about 28 * 2^-48 * sum over 128-column chunks k of
     128 * max|U(row, k)| * max|C(k, col)|, plus double-float accumulation."""
     rng = np.random.default_rng(n + s * 3 + c)
     U = rng.standard_normal((n, s)) * 2.0 ** rng.integers(-20, 20, s)
