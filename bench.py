@@ -337,7 +337,7 @@ def main():
                     help="1: double-float Gram and update on the tensor cores; 0: on the FP32 pipes")
     ap.add_argument("--max-iter", type=int, default=1000,
                     help="iteration cap per solve (profiling runs use a small cap)")
-    ap.add_argument("--ref-iters", type=int, default=322,
+    ap.add_argument("--ref-iters", type=int, default=315,
                     help="iterations per solve used to scale the reference arm's per-iteration time")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
