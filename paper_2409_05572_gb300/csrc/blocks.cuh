@@ -85,17 +85,6 @@ cudaError_t update(int64_t n, const Blk<typename Pol<A>::T>& U, const typename P
                    int c, const Blk<typename Pol<A>::T>& Y, double beta, cudaStream_t st,
                    const int* gate = nullptr);
 
-// update() with the contraction split over CTAs when the n x c output alone
-// gives too few of them (short inputs: the s x s products of the small
-// eigensolver's refinement, the HL trick); partial accumulators in scratch
-// (update_split_scratch_elems(n, c) float64 elements suffice), summed in a
-// fixed order.  F64 and DF64 only.
-size_t update_split_scratch_elems(int64_t n, int c);
-template <Arith A>
-cudaError_t update_split(int64_t n, const Blk<typename Pol<A>::T>& U, const typename Pol<A>::S* Cs, int c,
-                         const Blk<typename Pol<A>::T>& Y, double beta, double* scratch, size_t scratch_elems,
-                         cudaStream_t st, const int* gate = nullptr);
-
 // Scratch (float64 elements) for residual(): 2 * blocks * w.
 size_t residual_scratch_elems(int64_t n, int w);
 

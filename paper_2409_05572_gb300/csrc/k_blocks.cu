@@ -10,8 +10,6 @@
 #include <atomic>
 #include <cstdio>
 
-#include <algorithm>
-
 #include "blocks.cuh"
 
 namespace eig {
@@ -457,21 +455,17 @@ cudaError_t gram_capped(int64_t n, const Blk<typename Pol<A>::T>& U, const Blk<t
 // the column tile is the fast grid index so CTAs sharing U rows run together
 // and U is read from HBM about once.
 // ---------------------------------------------------------------------------
-// kchunk > 0: split-K, CTA z covers U columns [z kchunk, (z + 1) kchunk) and
-// writes its accumulators to part[z][r][cc] (n x c) instead of Y.
 template <Arith A>
 __global__ void __launch_bounds__(256) update_kernel(int64_t n, Blk<typename Pol<A>::T> U,
                                                      const typename Pol<A>::S* __restrict__ Cs,
                                                      int c, Blk<typename Pol<A>::T> Y,
                                                      typename Pol<A>::S beta, bool has_beta,
-                                                     const int* gate, int kchunk = 0,
-                                                     typename Pol<A>::Acc* part = nullptr) {
+                                                     const int* gate) {
   using P = Pol<A>;
   using T = typename P::T;
   using S = typename P::S;
   if (gate && *gate == 0) return;
-  const int k_lo = kchunk > 0 ? int(blockIdx.z) * kchunk : 0;
-  const int s_dim = kchunk > 0 ? min(U.width, k_lo + kchunk) : U.width;
+  const int s_dim = U.width;
   const int64_t m0 = int64_t(blockIdx.y) * GT;
   const int n0 = blockIdx.x * GT;
   __shared__ S Us[GK][GT + 1];
@@ -485,7 +479,7 @@ __global__ void __launch_bounds__(256) update_kernel(int64_t n, Blk<typename Pol
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = P::zero();
 
-  for (int k0 = k_lo; k0 < s_dim; k0 += GK) {
+  for (int k0 = 0; k0 < s_dim; k0 += GK) {
     const int kk = k0 + lk;
     const T* up = nullptr;
     int64_t uld = 0;
@@ -534,35 +528,11 @@ __global__ void __launch_bounds__(256) update_kernel(int64_t n, Blk<typename Pol
     for (int j = 0; j < 4; ++j) {
       const int cc = n0 + tx + 16 * j;
       if (cc >= c) continue;
-      if (part) {
-        part[(int64_t(blockIdx.z) * n + r) * c + cc] = acc[i][j];
-        continue;
-      }
       T* yp = Y.at(r, cc);
       if (has_beta) P::mac(acc[i][j], beta, P::stage(*yp));
       *yp = P::store(acc[i][j]);
     }
   }
-}
-
-// Y = sum_z part[z] (fixed order) + beta Y
-template <Arith A>
-__global__ void update_reduce_kernel(int64_t n, int c, int ks, const typename Pol<A>::Acc* __restrict__ part,
-                                     Blk<typename Pol<A>::T> Y, typename Pol<A>::S beta, bool has_beta,
-                                     typename Pol<A>::S one, const int* gate) {
-  using P = Pol<A>;
-  if (gate && *gate == 0) return;
-  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= n * c) return;
-  const int64_t r = idx / c;
-  const int cc = int(idx % c);
-  typename P::Acc acc = part[idx];
-  // F64 and DF64 only: there the accumulator is also the staged type, and a
-  // multiply-add by one is an (error-compensated) addition
-  for (int z = 1; z < ks; ++z) P::mac(acc, one, part[int64_t(z) * n * c + idx]);
-  typename P::T* yp = Y.at(r, cc);
-  if (has_beta) P::mac(acc, beta, P::stage(*yp));
-  *yp = P::store(acc);
 }
 
 template <Arith A>
@@ -652,46 +622,6 @@ cudaError_t update(int64_t n, const Blk<typename Pol<A>::T>& U, const typename P
   if (n <= 0 || c <= 0) return cudaSuccess;
   dim3 grid((c + GT - 1) / GT, (unsigned)cdiv(n, GT));
   update_kernel<A><<<grid, 256, 0, st>>>(n, U, Cs, c, Y, host_coef<A>(beta), beta != 0.0, gate); count_launches(1);
-  return cudaGetLastError();
-}
-
-// Split-K count for update_split: enough CTAs for all SMs when the output
-// tiles alone are few; 1 when they already fill the GPU.
-static int update_ksplit(int64_t n, int s, int c, size_t scratch_elems, size_t acc_elems_per_out) {
-  const int64_t tiles = cdiv(c, GT) * cdiv(n, GT);
-  int ks = int(std::min<int64_t>(cdiv(num_sms(), tiles), cdiv(s, GK)));
-  const size_t per = size_t(n) * size_t(c) * acc_elems_per_out;
-  if (per > 0 && size_t(ks) * per > scratch_elems) ks = int(scratch_elems / per);
-  return ks < 1 ? 1 : ks;
-}
-
-size_t update_split_scratch_elems(int64_t n, int c) {
-  // ks <= num_sms / tiles + 1 and n c <= tiles GT^2, so ks n c <=
-  // (num_sms + tiles) GT^2.  The bound grows with n and c, so a work area
-  // sized for the largest n, c also covers every smaller call carved from it.
-  if (n <= 0 || c <= 0) return 0;
-  const int64_t tiles = cdiv(c, GT) * cdiv(n, GT);
-  return size_t(num_sms() + tiles) * size_t(GT) * size_t(GT);
-}
-
-template <Arith A>
-cudaError_t update_split(int64_t n, const Blk<typename Pol<A>::T>& U, const typename Pol<A>::S* Cs, int c,
-                         const Blk<typename Pol<A>::T>& Y, double beta, double* scratch, size_t scratch_elems,
-                         cudaStream_t st, const int* gate) {
-  using Acc = typename Pol<A>::Acc;
-  if (n <= 0 || c <= 0) return cudaSuccess;
-  const int s = U.width;
-  const int ks = update_ksplit(n, s, c, scratch_elems, (sizeof(Acc) + 7) / 8);
-  if (ks <= 1 || s <= GK) return update<A>(n, U, Cs, c, Y, beta, st, gate);
-  const int kchunk = int(cdiv(cdiv(s, ks), GK) * GK);
-  const int ksu = int(cdiv(s, kchunk));
-  Acc* part = reinterpret_cast<Acc*>(scratch);
-  dim3 grid((c + GT - 1) / GT, (unsigned)cdiv(n, GT), ksu);
-  update_kernel<A><<<grid, 256, 0, st>>>(n, U, Cs, c, Y, host_coef<A>(beta), false, gate, kchunk, part);
-  count_launches(1);
-  update_reduce_kernel<A><<<(unsigned)cdiv(n * c, 256), 256, 0, st>>>(n, c, ksu, part, Y, host_coef<A>(beta),
-                                                                     beta != 0.0, host_coef<A>(1.0), gate);
-  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -854,11 +784,6 @@ EIG_INST(Arith::F64)
 EIG_INST(Arith::DF64)
 EIG_INST(Arith::F32)
 EIG_INST(Arith::C32)
-
-template cudaError_t update_split<Arith::F64>(int64_t, const Blk<double>&, const double*, int, const Blk<double>&,
-                                              double, double*, size_t, cudaStream_t, const int*);
-template cudaError_t update_split<Arith::DF64>(int64_t, const Blk<dd>&, const dd*, int, const Blk<dd>&, double,
-                                               double*, size_t, cudaStream_t, const int*);
 
 #define EIG_INST_CAPPED(A)                                                                          \
   template cudaError_t gram_capped<A>(int64_t, const Blk<Pol<A>::T>&, const Blk<Pol<A>::T>&, bool, \

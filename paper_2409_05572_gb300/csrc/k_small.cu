@@ -150,12 +150,11 @@ __global__ void hl_gather_kernel(int nnow, int nlock, int m, int q, const double
 
 namespace {
 struct HLWork {
-  double *Y, *Y2, *G, *Rinv, *cholw, *Cs, *scr, *uscr;
-  size_t uscr_elems;
+  double *Y, *Y2, *G, *Rinv, *cholw, *Cs, *scr;
   int* status;
 };
 size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
-HLWork hl_carve(void* work, int s, int m, int q) {
+HLWork hl_carve(void* work, int m, int q) {
   char* c = static_cast<char*>(work);
   HLWork w;
   auto take = [&](size_t n) {
@@ -170,8 +169,6 @@ HLWork hl_carve(void* work, int s, int m, int q) {
   w.cholw = take(size_t(q) * q + 2 * size_t(q));
   w.Cs = take(size_t(m) * q);
   w.scr = take(gram_scratch_elems(m, q, q, true));
-  w.uscr_elems = update_split_scratch_elems(s, q);  // rows: m (passes), s (C_P)
-  w.uscr = take(w.uscr_elems);
   w.status = reinterpret_cast<int*>(c);
   return w;
 }
@@ -180,8 +177,7 @@ HLWork hl_carve(void* work, int s, int m, int q) {
 size_t hl_work_bytes(int s, int nnow, int nlock) {
   const size_t m = size_t(s - nnow), q = size_t(nnow - nlock);
   return 3 * al256(m * q * sizeof(double)) + 2 * al256(q * q * sizeof(double)) + al256((q * q + 2 * q) * sizeof(double)) +
-         al256(gram_scratch_elems(int64_t(m), int(q), int(q), true) * sizeof(double)) +
-         al256(update_split_scratch_elems(int64_t(s), int(q)) * sizeof(double)) + 256;
+         al256(gram_scratch_elems(int64_t(m), int(q), int(q), true) * sizeof(double)) + 256;
 }
 
 cudaError_t hl_trick(int s, int nnow, int nlock, const double* Z, int64_t ldz, double* CP, int64_t ldcp,
@@ -189,7 +185,7 @@ cudaError_t hl_trick(int s, int nnow, int nlock, const double* Z, int64_t ldz, d
   const int m = s - nnow, q = nnow - nlock;
   if (q <= 0) return cudaSuccess;
   if (m < q) return cudaErrorInvalidValue;
-  HLWork w = hl_carve(work, s, m, q);
+  HLWork w = hl_carve(work, m, q);
   hl_gather_kernel<<<(unsigned)cdiv(int64_t(m) * q, 256), 256, 0, st>>>(nnow, nlock, m, q, Z, ldz, w.Y);
   count_launches(1);
   cudaError_t e = cudaGetLastError();
@@ -202,7 +198,7 @@ cudaError_t hl_trick(int s, int nnow, int nlock, const double* Z, int64_t ldz, d
     e = gram<Arith::F64>(m, Yb, Yb, true, w.G, q, w.scr, st);
     if (e == cudaSuccess) e = chol_rinv(q, m, w.G, q, w.Rinv, w.cholw, w.status, st, nullptr, 1.1102230246251565e-16);
     if (e == cudaSuccess) e = stage_coef<Arith::F64>(q, q, w.Rinv, q, w.Cs, q, 1.0, st);
-    if (e == cudaSuccess) e = update_split<Arith::F64>(m, Yb, w.Cs, q, Yo, 0.0, w.uscr, w.uscr_elems, st);
+    if (e == cudaSuccess) e = update<Arith::F64>(m, Yb, w.Cs, q, Yo, 0.0, st);
     std::swap(y, y2);
   }
   if (e != cudaSuccess) return e;
@@ -211,7 +207,7 @@ cudaError_t hl_trick(int s, int nnow, int nlock, const double* Z, int64_t ldz, d
   Zr.add(const_cast<double*>(Z) + nnow, ldz, m);
   Cb.add(CP, ldcp, q);
   e = stage_coef<Arith::F64>(m, q, y, q, w.Cs, q, 1.0, st);
-  if (e == cudaSuccess) e = update_split<Arith::F64>(s, Zr, w.Cs, q, Cb, 0.0, w.uscr, w.uscr_elems, st);
+  if (e == cudaSuccess) e = update<Arith::F64>(s, Zr, w.Cs, q, Cb, 0.0, st);
   return e;
 }
 

@@ -25,7 +25,6 @@
 // syev_qr64 for comparison and testing.
 #include <cooperative_groups.h>
 
-#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -891,8 +890,7 @@ __global__ void permute_kernel(int s, const dd* __restrict__ X, const int* __res
 
 struct RefWork {
   QLWork<float> ql;
-  double *Zd, *G, *S, *E, *Q, *lam, *scr, *uscr;
-  size_t uscr_elems;
+  double *Zd, *G, *S, *E, *Q, *lam, *scr;
   dd *Add, *X, *X2, *AX, *Cs;
   int* cid;
   int* rank;
@@ -902,18 +900,10 @@ static size_t ref_bytes(int s) {
   const size_t ss = size_t(s) * s;
   const size_t scr = gram_scratch_elems(s, s, s, true);
   return ql_work_bytes<float>(s) + 5 * (ss * 8 + 256) + (size_t(s) * 8 + 256) + (scr * 8 + 256) +
-         (update_split_scratch_elems(s, s) * 8 + 256) + 5 * (ss * sizeof(dd) + 256) + 2 * (size_t(s) * 4 + 256) +
-         1024;
+         5 * (ss * sizeof(dd) + 256) + 2 * (size_t(s) * 4 + 256) + 1024;
 }
 
-// the largest need of any size up to s: a work area sized for the largest
-// projected problem then serves every smaller one (the split-K scratch of the
-// Gram products does not grow monotonically with s)
-size_t syev_work_bytes(int s) {
-  size_t b = 0;
-  for (int t = 1; t <= s; ++t) b = std::max(b, ref_bytes(t));
-  return b;
-}
+size_t syev_work_bytes(int s) { return ref_bytes(s); }
 
 static RefWork ref_carve(int s, void* base) {
   Carver cv(base);
@@ -927,8 +917,6 @@ static RefWork ref_carve(int s, void* base) {
   w.Q = cv.take<double>(ss);
   w.lam = cv.take<double>(s);
   w.scr = cv.take<double>(gram_scratch_elems(s, s, s, true));
-  w.uscr_elems = update_split_scratch_elems(s, s);
-  w.uscr = cv.take<double>(w.uscr_elems);
   w.Add = cv.take<dd>(ss);
   w.X = cv.take<dd>(ss);
   w.X2 = cv.take<dd>(ss);
@@ -951,7 +939,7 @@ static cudaError_t oa_products(int s, RefWork& w, cudaStream_t st) {
   if ((e = gram<Arith::DF64>(s, sq(w.X, s), sq(w.X, s), true, w.G, s, w.scr, st))) return e;
   if ((e = convert2d(s, s, w.X, s, EIG_DF64, w.Zd, s, EIG_F64, st))) return e;
   if ((e = stage_coef<Arith::DF64>(s, s, w.Zd, s, w.Cs, s, 1.0, st))) return e;
-  if ((e = update_split<Arith::DF64>(s, sq(w.Add, s), w.Cs, s, sq(w.AX, s), 0.0, w.uscr, w.uscr_elems, st))) return e;
+  if ((e = update<Arith::DF64>(s, sq(w.Add, s), w.Cs, s, sq(w.AX, s), 0.0, st))) return e;
   return gram<Arith::DF64>(s, sq(w.X, s), sq(w.AX, s), true, w.S, s, w.scr, st);
 }
 
@@ -984,7 +972,7 @@ cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, in
     eye_kernel<<<gb, 256, 0, st>>>(s, w.Q); count_launches(1);
     cluster_jacobi_kernel<<<s, 32, 0, st>>>(s, w.S, w.cid, w.Q, w.lam); count_launches(1);
     if ((e = stage_coef<Arith::DF64>(s, s, w.Q, s, w.Cs, s, 1.0, st))) return e;
-    if ((e = update_split<Arith::DF64>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 0.0, w.uscr, w.uscr_elems, st))) return e;
+    if ((e = update<Arith::DF64>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 0.0, st))) return e;
     std::swap(w.X, w.X2);
     if ((e = oa_products(s, w, st))) return e;
     oa_lambda_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.G, w.S, w.lam); count_launches(1);
@@ -992,7 +980,7 @@ cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, in
     // X2 = X + X E
     if ((e = cudaMemcpyAsync(w.X2, w.X, sizeof(dd) * ss, cudaMemcpyDeviceToDevice, st))) return e;
     if ((e = stage_coef<Arith::DF64>(s, s, w.E, s, w.Cs, s, 1.0, st))) return e;
-    if ((e = update_split<Arith::DF64>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 1.0, w.uscr, w.uscr_elems, st))) return e;
+    if ((e = update<Arith::DF64>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 1.0, st))) return e;
     std::swap(w.X, w.X2);
   }
   // final: eigenvalues, cluster diagonalisation, ascending order
@@ -1001,7 +989,7 @@ cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, in
   eye_kernel<<<gb, 256, 0, st>>>(s, w.Q); count_launches(1);
   cluster_jacobi_kernel<<<s, 32, 0, st>>>(s, w.S, w.cid, w.Q, w.lam); count_launches(1);
   if ((e = stage_coef<Arith::DF64>(s, s, w.Q, s, w.Cs, s, 1.0, st))) return e;
-  if ((e = update_split<Arith::DF64>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 0.0, w.uscr, w.uscr_elems, st))) return e;
+  if ((e = update<Arith::DF64>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 0.0, st))) return e;
   rank_kernel<double><<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.lam, w.rank, nullptr); count_launches(1);
   permute_kernel<<<gb, 256, 0, st>>>(s, w.X2, w.rank, w.lam, Z, ldz, lam); count_launches(1);
   return cudaGetLastError();
