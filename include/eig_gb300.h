@@ -225,11 +225,12 @@ typedef struct {
   int profile;         /* 1: time every kernel class with CUDA events          */
   int expand_powered;  /* EIG_CHEB_SI: 1 = "Powered X_drop" (Sec. 6.4): apply
                           the filter to the saved columns every iteration     */
-  int gram_tc;         /* 1 (default): double-float Gram products on the
-                          tensor cores (EIG_ARITH_DF64_TC, normwise ~2^-48
-                          accuracy, 24 extra bytes per n x (3 k_max + 1)
-                          element pair of device memory); 0: FP32-pipe
-                          double-float Gram (componentwise ~2^-48)            */
+  int gram_tc;         /* 1 (default): double-float Gram products and block
+                          updates on the tensor cores (EIG_ARITH_DF64_TC,
+                          normwise ~2^-48 accuracy; slice buffers of 12 bytes
+                          per element for two n x (3 k_max + 1) and two
+                          n x (2 k_max + 1) operands); 0: FP32-pipe
+                          double-float products (componentwise ~2^-48)        */
 } eig_options;
 
 /* kernel classes of the per-class statistics (eig_result.kstats) */
@@ -280,6 +281,26 @@ int eig_solve(eig_handle *h);
 int eig_query(const eig_handle *h, eig_result *out);
 void eig_destroy(eig_handle *h);
 const char *eig_strerror(int status);
+
+/* ---- a3: the shrink-and-expand decisions on a scripted history (host
+ * only, no device work; no counterpart in the paper) -----------------------
+ * Runs the decision rule that eig_solve applies (Algorithms 6 and 7, Eqs.
+ * ckslope / ckslopek, the warm-up rule at the end of Sec. 3.2) over the host
+ * array r[0 .. m-1] = r^(1) .. r^(m), with the active width nnow starting at
+ * nex.  For each j it records r^(j), asks whether to expand (nnow = nex when
+ * it does), stores width[j-1] = nnow (host array of m ints, or NULL), then
+ * asks whether to shrink (nnow = nes when it does) -- the order of the two
+ * decision points inside one iteration of eig_solve.  The first max_events
+ * events go to events[2 e] = j, events[2 e + 1] = EIG_EVENT_SHRINK or
+ * EIG_EVENT_EXPAND (host array of 2 max_events ints, NULL if max_events is
+ * 0); *n_events receives the total count.  opt supplies je, js, jp, j_warm,
+ * mu and r_warm (NULL: the defaults).  Returns EIG_EINVAL for an unknown
+ * strategy, nes outside [1, nex), m < 0, a negative or NaN r^(j), je, js or
+ * jp below 1, or a missing array. */
+#define EIG_EVENT_SHRINK 1
+#define EIG_EVENT_EXPAND 2
+int eig_strategy_trace(int strategy, int nes, int nex, const eig_options *opt, const double *r, int m,
+                       int *width, int *events, int max_events, int *n_events);
 
 /* ---- serving: many independent solves advanced together ----------------
  * A request loop for the serving workload of many eigenproblems of different

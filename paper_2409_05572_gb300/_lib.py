@@ -28,7 +28,8 @@ FORMS = {"df64": 0, "f64": 1, "mixed": 2}
 EXPORTS = ("eig_convert", "eig_spmm", "eig_gram", "eig_gram_noalloc", "eig_block_update", "eig_residual",
            "eig_cholqr2", "eig_syev", "eig_hl_trick", "eig_options_default", "eig_create", "eig_solve",
            "eig_query", "eig_destroy", "eig_strerror", "eig_footprint", "eig_server_create", "eig_submit",
-           "eig_server_step", "eig_poll", "eig_release", "eig_server_destroy", "eig_device_status")
+           "eig_server_step", "eig_poll", "eig_release", "eig_server_destroy", "eig_device_status",
+           "eig_strategy_trace")
 
 
 class EigError(RuntimeError):
@@ -103,6 +104,7 @@ def load(path: str = LIB_PATH):
         "eig_release": [p, C.c_uint64],
         "eig_server_destroy": [p],
         "eig_footprint": [i64, i64, i32, i32, C.POINTER(eig_options)],
+        "eig_strategy_trace": [i32, i32, i32, C.POINTER(eig_options), p, i32, p, p, i32, C.POINTER(C.c_int)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -184,6 +186,39 @@ def eig_spmm(n, rowptr, colind, val, dtype, w, V, ldv, Y, ldy, alpha=1.0, beta=0
 def eig_gram(n, a, b, U, ldu, V, ldv, arith, sym, G, ldg, stream=None):
     return _check("eig_gram", load().eig_gram(n, a, b, _ptr(U), ldu, _ptr(V), ldv, arith, int(sym), _ptr(G), ldg,
                                               _stream(stream)))
+
+
+EVENT_SHRINK, EVENT_EXPAND = 1, 2
+
+
+def eig_strategy_trace(strategy, nes, nex, r, **opts):
+    """The shrink-and-expand decisions eig_solve takes on the scripted
+    residual history r^(1) .. r^(m) (host only, no device work).  Returns
+    (events, widths): events as (j, "shrink" | "expand") in order, widths[j-1]
+    the active width of iteration j.  opts: je, js, jp, j_warm, mu, r_warm."""
+    import numpy as np
+    lib = load()
+    rr = np.ascontiguousarray(r, dtype=np.float64)
+    m = int(rr.size)
+    width = np.zeros(max(m, 1), dtype=np.int32)
+    cap = 2 * m + 2
+    ev = np.zeros(2 * cap, dtype=np.int32)
+    n_ev = C.c_int(0)
+    opt = None
+    if opts:
+        o = eig_options()
+        lib.eig_options_default(C.byref(o))
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        opt = C.byref(o)
+    _check("eig_strategy_trace", lib.eig_strategy_trace(STRATEGIES[strategy], nes, nex, opt,
+                                                        rr.ctypes.data if m else None, m, width.ctypes.data,
+                                                        ev.ctypes.data, cap, C.byref(n_ev)))
+    names = {EVENT_SHRINK: "shrink", EVENT_EXPAND: "expand"}
+    events = [(int(ev[2 * e]), names[int(ev[2 * e + 1])]) for e in range(min(n_ev.value, cap))]
+    return events, [int(x) for x in width[:m]]
 
 
 def device_status():

@@ -1377,6 +1377,51 @@ int eig_options_default(eig_options* o) {
   return EIG_OK;
 }
 
+int eig_strategy_trace(int strategy, int nes, int nex, const eig_options* opt, const double* r, int m, int* width,
+                       int* events, int max_events, int* n_events) {
+  if (strategy < EIG_NONE || strategy > EIG_SLOPEK || nes < 1 || nes >= nex || m < 0 || max_events < 0 ||
+      !n_events || (m > 0 && !r) || (max_events > 0 && !events))
+    return EIG_EINVAL;
+  eig_options d;
+  eig_options_default(&d);
+  const eig_options* o = opt ? opt : &d;
+  SEStrategy se;
+  se.kind = strategy;
+  se.nes = nes;
+  se.nex = nex;
+  se.je = o->je;
+  se.js = o->js;
+  se.jp = o->jp;
+  se.j_warm = o->j_warm;
+  se.mu = o->mu;
+  se.r_warm = o->r_warm;
+  if (se.je < 1 || se.js < 1 || se.jp < 1) return EIG_EINVAL;
+  int nnow = nex, ne = 0;
+  auto event = [&](int j, int kind) {
+    if (ne < max_events) {
+      events[2 * ne] = j;
+      events[2 * ne + 1] = kind;
+    }
+    ++ne;
+  };
+  // the order of the decision points in an iteration of eig_solve
+  for (int j = 1; j <= m; ++j) {
+    if (!(r[j - 1] >= 0.0)) return EIG_EINVAL;
+    se.record(j, r[j - 1]);
+    if (se.ifexpand(j, nnow)) {
+      nnow = nex;
+      event(j, EIG_EVENT_EXPAND);
+    }
+    if (width) width[j - 1] = nnow;
+    if (se.ifshrink(j, nnow)) {
+      nnow = nes;
+      event(j, EIG_EVENT_SHRINK);
+    }
+  }
+  *n_events = ne;
+  return EIG_OK;
+}
+
 int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_options* opt, eig_handle** out) {
   if (!A || !out || !opt) return EIG_EINVAL;
   *out = nullptr;
