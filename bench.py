@@ -478,9 +478,12 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         fms = e0.elapsed_time(e1)
-        line["fixed_block"] = {"value": nev / (fms / 1e3), "unit": UNIT, "ms": fms, "iters": fo["iters"],
-                               "converged": bool(fo["status"] == 0 and np.max(fo["resid"]) <= tol),
-                               "speedup_of_shrink_expand": fms / ms_step}
+        fconv = bool(fo["status"] == 0 and np.max(fo["resid"]) <= tol)
+        # a solve stopped by the iteration cap has no time-to-converged-nev:
+        # no throughput and no speed-up are derived from it
+        line["fixed_block"] = {"value": nev / (fms / 1e3) if fconv else None, "unit": UNIT, "ms": fms,
+                               "iters": fo["iters"], "converged": fconv,
+                               "speedup_of_shrink_expand": fms / ms_step if fconv else None}
         fixed.close()
 
     if rank == 0 and not args.no_e2e:
