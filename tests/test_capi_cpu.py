@@ -118,3 +118,21 @@ def test_struct_layouts_match_header(tmp_path):
         assert int(out[name]) == ctypes.sizeof(S), name
         for f in S._fields_:
             assert int(out[f"{name}.{f[0]}"]) == getattr(S, f[0]).offset, (name, f[0])
+
+
+def test_footprint_orders_the_configurations(libpath):
+    """eig_footprint (host arithmetic only): the tensor-core slice buffers
+    cost memory, the c4 graph workload only fits the 280 GB of HBM without
+    them, and the footprint grows with n and k_max."""
+    from paper_2409_05572_gb300 import _lib
+    _lib.load()
+    f = _lib.footprint
+    c2 = f(2_097_152, 14_581_760, 64, 128)
+    assert 60e9 < c2 < 100e9
+    assert f(2_097_152, 14_581_760, 64, 128, gram_tc=0) < c2
+    c4 = dict(precond=1, deflate_ones=1)
+    assert f(4_000_000, 44_000_000, 200, 400, **c4) > 280e9 > f(4_000_000, 44_000_000, 200, 400, gram_tc=0, **c4)
+    sizes = [f(n, 7 * n, 32, k) for n in (10_000, 100_000, 1_000_000) for k in (64, 96, 128)]
+    assert sizes == sorted(sizes[:3]) + sorted(sizes[3:6]) + sorted(sizes[6:])
+    for k in range(3):
+        assert sizes[k] < sizes[3 + k] < sizes[6 + k]
