@@ -335,6 +335,9 @@ def main():
     ap.add_argument("--max-active", type=int, default=64, help="c5: solves advanced per step")
     ap.add_argument("--gram-tc", type=int, default=1, choices=[0, 1],
                     help="1: double-float Gram and update on the tensor cores; 0: on the FP32 pipes")
+    ap.add_argument("--aggressive-warmup", action="store_true",
+                    help="warm-up gate on the first pair's residual with r_warm = 1e-1 (the paper's closing "
+                         "remarks) instead of r^(j) <= 1e-4")
     ap.add_argument("--max-iter", type=int, default=1000,
                     help="iteration cap per solve (profiling runs use a small cap)")
     ap.add_argument("--ref-iters", type=int, default=315,
@@ -370,6 +373,8 @@ def main():
     algo = wl.get("algo", "lobpcg")
     extra = dict(wl.get("extra", {}))
     extra["gram_tc"] = args.gram_tc
+    if args.aggressive_warmup:
+        extra.update(warm_first=1, r_warm=1e-1)
     solver = L.Solver((rp, ci, va), nev=nev, k_max=k, strategy=args.strategy, X0=X0d, normA=normA,
                       tol=0.5 * tol, form=args.form, stream=stream, profile=1, max_iter=args.max_iter,
                       algo=algo, **extra)
@@ -416,7 +421,8 @@ def main():
                        "form": args.form, "tol": tol, "parallelism": f"replicas x{ws}",
                        "products": "tensor cores (tcgen05, exact bf16 slices)" if (args.gram_tc and args.form != "f64")
                        else "CUDA cores",
-                       "l2": "inputs larger than L2 (each n x k block is 4.3 GB); no flush"},
+                       "l2": "inputs larger than L2 (each n x k block is 4.3 GB); no flush",
+                       "warmup_rule": "first pair, r_warm 1e-1" if args.aggressive_warmup else "r^(j), r_warm 1e-4"},
             "converged": bool(ok), "iters": last["iters"], "n_shrink": last["n_shrink"],
             "n_expand": last["n_expand"], "max_resid": float(np.max(last["resid"])),
             "max_rel_eig_err_vs_closed_form": eig_err, "clocks": clk}

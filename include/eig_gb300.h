@@ -231,6 +231,12 @@ typedef struct {
                           per element for two n x (3 k_max + 1) and two
                           n x (2 k_max + 1) operands); 0: FP32-pipe
                           double-float products (componentwise ~2^-48)        */
+  int warm_first;      /* 0 (default): the warm-up gate (end of Sec. 3.2)
+                          compares r^(j), the largest Eq. conv residual of the
+                          first nev pairs, with r_warm; 1: it compares the
+                          residual of the first pair instead (the more
+                          aggressive warm-up of the paper's closing remarks,
+                          there with r_warm = 1e-1)                          */
 } eig_options;
 
 /* kernel classes of the per-class statistics (eig_result.kstats) */
@@ -287,20 +293,21 @@ const char *eig_strerror(int status);
  * Runs the decision rule that eig_solve applies (Algorithms 6 and 7, Eqs.
  * ckslope / ckslopek, the warm-up rule at the end of Sec. 3.2) over the host
  * array r[0 .. m-1] = r^(1) .. r^(m), with the active width nnow starting at
- * nex.  For each j it records r^(j), asks whether to expand (nnow = nex when
+ * nex.  r1 (host, m values, or NULL for r itself) is the residual of the
+ * first pair, which the warm-up gate reads when opt->warm_first is set.  For each j it records r^(j), asks whether to expand (nnow = nex when
  * it does), stores width[j-1] = nnow (host array of m ints, or NULL), then
  * asks whether to shrink (nnow = nes when it does) -- the order of the two
  * decision points inside one iteration of eig_solve.  The first max_events
  * events go to events[2 e] = j, events[2 e + 1] = EIG_EVENT_SHRINK or
  * EIG_EVENT_EXPAND (host array of 2 max_events ints, NULL if max_events is
  * 0); *n_events receives the total count.  opt supplies je, js, jp, j_warm,
- * mu and r_warm (NULL: the defaults).  Returns EIG_EINVAL for an unknown
- * strategy, nes outside [1, nex), m < 0, a negative or NaN r^(j), je, js or
- * jp below 1, or a missing array. */
+ * mu, r_warm and warm_first (NULL: the defaults).  Returns EIG_EINVAL for
+ * an unknown strategy, nes outside [1, nex), m < 0, a negative or NaN
+ * residual, je, js or jp below 1, or a missing array. */
 #define EIG_EVENT_SHRINK 1
 #define EIG_EVENT_EXPAND 2
-int eig_strategy_trace(int strategy, int nes, int nex, const eig_options *opt, const double *r, int m,
-                       int *width, int *events, int max_events, int *n_events);
+int eig_strategy_trace(int strategy, int nes, int nex, const eig_options *opt, const double *r,
+                       const double *r1, int m, int *width, int *events, int max_events, int *n_events);
 
 /* ---- serving: many independent solves advanced together ----------------
  * A request loop for the serving workload of many eigenproblems of different

@@ -72,7 +72,7 @@ def lobpcg(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none",
     for j in range(1, max_iter + 1):
         # R = AX - X Lambda; Eq. conv per column, Eq. rk overall.
         R, rho, r = B.residual_test(X, AX, lam, normA, nev)
-        strat.record(j, r)
+        strat.record(j, r, float(rho[0]))
         res.history.append(r)
         res.iters = j
         if r <= tol:

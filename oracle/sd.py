@@ -35,7 +35,7 @@ def sd(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none", tol: float
     res = Result(lam[:nev], X[:, :nev], False, 0)
     for j in range(1, max_iter + 1):
         R, rho, r = B.residual_test(X, AX, lam, normA, nev)
-        strat.record(j, r)
+        strat.record(j, r, float(rho[0]))
         res.history.append(r)
         res.iters = j
         if r <= tol:

@@ -20,6 +20,10 @@ Readings taken where the paper is silent or garbled:
   mu * c < c_max (same as c_max/c > mu for c > 0), with c_max the largest slope
   since the last shrink including the current iteration's slope.
 * A shrink only happens when nnow > nes (it would be a no-op otherwise).
+* Aggressive warm-up (closing remarks of the paper): with warm_first the
+  gate compares the residual of the first Ritz pair, instead of r^(j) (in
+  practice the nev-th pair's), with r_warm; the paper pairs it with
+  r_warm = 1e-1.
 """
 from __future__ import annotations
 
@@ -31,13 +35,16 @@ KINDS = (NONE, FIX, SLOPE, SLOPEK)
 
 class Strategy:
     def __init__(self, kind: str, nes: int, nex: int, je: int = 12, js: int = 2,
-                 mu: float = 1.1, jp: int = 10, j_warm: int = 5, r_warm: float = 1e-4):
+                 mu: float = 1.1, jp: int = 10, j_warm: int = 5, r_warm: float = 1e-4,
+                 warm_first: bool = False):
         if kind not in KINDS:
             raise ValueError(kind)
         self.kind, self.nes, self.nex = kind, nes, nex
         self.je, self.js, self.mu, self.jp = je, js, mu, jp
         self.j_warm, self.r_warm = j_warm, r_warm
+        self.warm_first = bool(warm_first)
         self.r = {}            # j -> r^(j)
+        self.r1 = {}           # j -> Eq. conv residual of the first Ritz pair
         self.warmed = False
         self.j0 = None         # iteration of the first shrink
         self.j_exp = None      # iteration of the last expansion
@@ -45,8 +52,9 @@ class Strategy:
         self.events = []       # (j, "shrink" | "expand")
 
     # -- Eq. rk history -------------------------------------------------
-    def record(self, j: int, r: float) -> None:
+    def record(self, j: int, r: float, r1: float | None = None) -> None:
         self.r[j] = r
+        self.r1[j] = r if r1 is None else r1
 
     @staticmethod
     def _log10(x: float) -> float:
@@ -86,7 +94,8 @@ class Strategy:
         if self.kind == NONE or nnow <= self.nes:
             return False
         if not self.warmed:
-            go = j >= self.j_warm and self.r[j] <= self.r_warm
+            gate = self.r1[j] if self.warm_first else self.r[j]
+            go = j >= self.j_warm and gate <= self.r_warm
             if go:
                 self.warmed = True
                 self.j0 = j

@@ -50,7 +50,7 @@ class eig_options(C.Structure):
                 ("cheb_upper", C.c_double), ("precond", C.c_int), ("deflate_ones", C.c_int),
                 ("normA", C.c_double), ("mixed_switch", C.c_double), ("X0", C.c_void_p),
                 ("x0_on_device", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int),
-                ("expand_powered", C.c_int), ("gram_tc", C.c_int)]
+                ("expand_powered", C.c_int), ("gram_tc", C.c_int), ("warm_first", C.c_int)]
 
 
 class eig_server_opts(C.Structure):
@@ -104,7 +104,7 @@ def load(path: str = LIB_PATH):
         "eig_release": [p, C.c_uint64],
         "eig_server_destroy": [p],
         "eig_footprint": [i64, i64, i32, i32, C.POINTER(eig_options)],
-        "eig_strategy_trace": [i32, i32, i32, C.POINTER(eig_options), p, i32, p, p, i32, C.POINTER(C.c_int)],
+        "eig_strategy_trace": [i32, i32, i32, C.POINTER(eig_options), p, p, i32, p, p, i32, C.POINTER(C.c_int)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -191,15 +191,20 @@ def eig_gram(n, a, b, U, ldu, V, ldv, arith, sym, G, ldg, stream=None):
 EVENT_SHRINK, EVENT_EXPAND = 1, 2
 
 
-def eig_strategy_trace(strategy, nes, nex, r, **opts):
+def eig_strategy_trace(strategy, nes, nex, r, r1=None, **opts):
     """The shrink-and-expand decisions eig_solve takes on the scripted
-    residual history r^(1) .. r^(m) (host only, no device work).  Returns
-    (events, widths): events as (j, "shrink" | "expand") in order, widths[j-1]
-    the active width of iteration j.  opts: je, js, jp, j_warm, mu, r_warm."""
+    residual history r^(1) .. r^(m) (host only, no device work); r1, if
+    given, is the first pair's residual history (read by the warm-up gate
+    when warm_first is set).  Returns (events, widths): events as
+    (j, "shrink" | "expand") in order, widths[j-1] the active width of
+    iteration j.  opts: je, js, jp, j_warm, mu, r_warm, warm_first."""
     import numpy as np
     lib = load()
     rr = np.ascontiguousarray(r, dtype=np.float64)
     m = int(rr.size)
+    r1a = None if r1 is None else np.ascontiguousarray(r1, dtype=np.float64)
+    if r1a is not None and r1a.size != m:
+        raise ValueError("r1 must have the length of r")
     width = np.zeros(max(m, 1), dtype=np.int32)
     cap = 2 * m + 2
     ev = np.zeros(2 * cap, dtype=np.int32)
@@ -214,8 +219,9 @@ def eig_strategy_trace(strategy, nes, nex, r, **opts):
             setattr(o, k, v)
         opt = C.byref(o)
     _check("eig_strategy_trace", lib.eig_strategy_trace(STRATEGIES[strategy], nes, nex, opt,
-                                                        rr.ctypes.data if m else None, m, width.ctypes.data,
-                                                        ev.ctypes.data, cap, C.byref(n_ev)))
+                                                        rr.ctypes.data if m else None,
+                                                        r1a.ctypes.data if (r1a is not None and m) else None, m,
+                                                        width.ctypes.data, ev.ctypes.data, cap, C.byref(n_ev)))
     names = {EVENT_SHRINK: "shrink", EVENT_EXPAND: "expand"}
     events = [(int(ev[2 * e]), names[int(ev[2 * e + 1])]) for e in range(min(n_ev.value, cap))]
     return events, [int(x) for x in width[:m]]

@@ -43,7 +43,9 @@ struct SEStrategy {
   int kind = EIG_NONE, nes = 0, nex = 0;
   int je = 12, js = 2, jp = 10, j_warm = 5;
   double mu = 1.1, r_warm = 1e-4;
-  std::vector<double> r;  // r[j] for j >= 1 (r[0] unused)
+  bool warm_first = false;  // warm-up gate on the first pair's residual
+  std::vector<double> r;    // r[j] for j >= 1 (r[0] unused)
+  std::vector<double> r1;   // residual of the first Ritz pair, same indexing
   bool warmed = false;
   int j0 = -1, j_exp = -1;
   bool has_cmax = false;
@@ -51,9 +53,18 @@ struct SEStrategy {
   int n_shrink = 0, n_expand = 0;
 
   static double lg(double x) { return std::log10(std::max(x, 1e-300)); }
-  void record(int j, double rj) {
-    if ((int)r.size() <= j) r.resize(j + 1, -1.0);
+  void record(int j, double rj, double r1j) {
+    if ((int)r.size() <= j) {
+      r.resize(j + 1, -1.0);
+      r1.resize(j + 1, -1.0);
+    }
     r[j] = rj;
+    r1[j] = r1j;
+  }
+  // drop the records from iteration j on
+  void forget(int j) {
+    r.resize(j);
+    r1.resize(j);
   }
   bool have(int j) const { return j >= 1 && j < (int)r.size() && r[j] >= 0.0; }
   bool slope(int j, double* c) const {
@@ -92,7 +103,7 @@ struct SEStrategy {
     if (kind == EIG_NONE || nnow <= nes) return false;
     bool go;
     if (!warmed) {
-      go = j >= j_warm && have(j) && r[j] <= r_warm;
+      go = j >= j_warm && have(j) && (warm_first ? r1[j] : r[j]) <= r_warm;
       if (go) {
         warmed = true;
         j0 = j;
@@ -587,7 +598,8 @@ struct Ops {
 
 // Eq. conv / Eq. rk from the host copies of the norms
 struct ConvInfo {
-  double r = 0.0;
+  double r = 0.0;   // r^(j) of Eq. rk (largest over the first nev pairs)
+  double r1 = 0.0;  // Eq. conv of the first Ritz pair
   int nlock = 0;
   bool breakdown = false;
 };
@@ -605,6 +617,7 @@ ConvInfo conv_test(eig_handle* h, int w) {
     const double x = std::sqrt(std::max(xn[i], 0.0));
     const double rho = std::sqrt(std::max(rn[i], 0.0)) / (nA * x + x * std::fabs(lam[i]));
     const double rr = std::isfinite(rho) ? rho : 1e300;
+    if (i == 0) ci.r1 = rr;
     r = std::max(r, rr);
     if (prefix && rr <= h->opt.tol)
       ++ci.nlock;
@@ -703,7 +716,7 @@ int lob_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switch
     ConvInfo ci = conv_test(h, L.nnow);
     if (ci.breakdown) return EIG_EBREAKDOWN;
     h->history.push_back(ci.r);
-    L.se.record(j, ci.r);
+    L.se.record(j, ci.r, ci.r1);
     L.j = j;
     h->iters = j;
     if (ci.r <= h->opt.tol) {
@@ -714,7 +727,7 @@ int lob_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switch
       // hand over before doing this iteration's update in the next form
       L.j = j - 1;
       h->history.pop_back();
-      L.se.r.resize(j);
+      L.se.forget(j);
       *switched = true;
       return EIG_OK;
     }
@@ -861,7 +874,7 @@ int cheb_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switc
     ConvInfo ci = conv_test(h, L.nnow);
     if (ci.breakdown) return EIG_EBREAKDOWN;
     h->history.push_back(ci.r);
-    L.se.record(j, ci.r);
+    L.se.record(j, ci.r, ci.r1);
     L.j = j;
     h->iters = j;
     if (ci.r <= h->opt.tol) {
@@ -871,7 +884,7 @@ int cheb_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switc
     if (switch_r > 0.0 && ci.r <= switch_r) {
       L.j = j - 1;
       h->history.pop_back();
-      L.se.r.resize(j);
+      L.se.forget(j);
       *switched = true;
       return EIG_OK;
     }
@@ -979,7 +992,7 @@ int sd_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switche
   ConvInfo ci = conv_test(h, L.nnow);
   if (ci.breakdown) return EIG_EBREAKDOWN;
   h->history.push_back(ci.r);
-  L.se.record(j, ci.r);
+  L.se.record(j, ci.r, ci.r1);
   L.j = j;
   h->iters = j;
   if (ci.r <= h->opt.tol) {
@@ -989,7 +1002,7 @@ int sd_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switche
   if (switch_r > 0.0 && ci.r <= switch_r) {
     L.j = j - 1;
     h->history.pop_back();
-    L.se.r.resize(j);
+    L.se.forget(j);
     *switched = true;
     return EIG_OK;
   }
@@ -1147,6 +1160,7 @@ struct Stepper {
     L.se.j_warm = h->opt.j_warm;
     L.se.mu = h->opt.mu;
     L.se.r_warm = h->opt.r_warm;
+    L.se.warm_first = h->opt.warm_first != 0;
     h->history.clear();
     h->widths.clear();
     h->iters = 0;
@@ -1377,8 +1391,8 @@ int eig_options_default(eig_options* o) {
   return EIG_OK;
 }
 
-int eig_strategy_trace(int strategy, int nes, int nex, const eig_options* opt, const double* r, int m, int* width,
-                       int* events, int max_events, int* n_events) {
+int eig_strategy_trace(int strategy, int nes, int nex, const eig_options* opt, const double* r, const double* r1,
+                       int m, int* width, int* events, int max_events, int* n_events) {
   if (strategy < EIG_NONE || strategy > EIG_SLOPEK || nes < 1 || nes >= nex || m < 0 || max_events < 0 ||
       !n_events || (m > 0 && !r) || (max_events > 0 && !events))
     return EIG_EINVAL;
@@ -1395,6 +1409,7 @@ int eig_strategy_trace(int strategy, int nes, int nex, const eig_options* opt, c
   se.j_warm = o->j_warm;
   se.mu = o->mu;
   se.r_warm = o->r_warm;
+  se.warm_first = o->warm_first != 0;
   if (se.je < 1 || se.js < 1 || se.jp < 1) return EIG_EINVAL;
   int nnow = nex, ne = 0;
   auto event = [&](int j, int kind) {
@@ -1406,8 +1421,9 @@ int eig_strategy_trace(int strategy, int nes, int nex, const eig_options* opt, c
   };
   // the order of the decision points in an iteration of eig_solve
   for (int j = 1; j <= m; ++j) {
-    if (!(r[j - 1] >= 0.0)) return EIG_EINVAL;
-    se.record(j, r[j - 1]);
+    const double rf = r1 ? r1[j - 1] : r[j - 1];
+    if (!(r[j - 1] >= 0.0) || !(rf >= 0.0)) return EIG_EINVAL;
+    se.record(j, r[j - 1], rf);
     if (se.ifexpand(j, nnow)) {
       nnow = nex;
       event(j, EIG_EVENT_EXPAND);

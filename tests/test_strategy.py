@@ -110,3 +110,26 @@ def test_no_decision_before_warmup(kind):
     rs = [1.0] * 30
     ev, widths = drive(Strategy(kind, NES, NEX), rs)
     assert ev == [] and set(widths) == {NEX}
+
+
+def test_aggressive_warmup_gates_on_the_first_pair():
+    """warm_first (closing remarks of the paper): the gate reads the first
+    Ritz pair's residual, not r^(j); with r_warm = 1e-1 the first shrink comes
+    at j_warm = 5 although r^(j) is still far above the threshold."""
+    r = [1.0] * 3 + [0.5] * 30           # r^(j): never below 1e-1
+    r1 = [1.0, 0.5, 0.05] + [0.01] * 30  # first pair: below 1e-1 from j = 3
+    st = Strategy("fix", NES, NEX, r_warm=1e-1, warm_first=True)
+    nnow = NEX
+    for j, (a, b) in enumerate(zip(r, r1), start=1):
+        st.record(j, a, b)
+        if st.ifexpand(j, nnow):
+            nnow = NEX
+        if st.ifshrink(j, nnow):
+            nnow = NES
+    assert st.events[:3] == [(5, "shrink"), (15, "expand"), (17, "shrink")]
+    # the same history without warm_first never opens the gate
+    st = Strategy("fix", NES, NEX, r_warm=1e-1)
+    for j, (a, b) in enumerate(zip(r, r1), start=1):
+        st.record(j, a, b)
+        assert not st.ifshrink(j, NEX)
+    assert st.events == []

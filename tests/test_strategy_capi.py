@@ -3,6 +3,7 @@
 state machine (oracle/strategy.py, pinned by the hand-worked tables of
 test_strategy.py).  On those tables and on seeded random residual histories
 the event lists and the active widths must be identical."""
+import ctypes
 import math
 import os
 
@@ -21,13 +22,14 @@ def lib():
     return _lib
 
 
-def oracle_trace(kind, nes, nex, rs, **params):
+def oracle_trace(kind, nes, nex, rs, r1=None, **params):
     """The decision points of one iteration in the solve's order: record
-    r^(j), expand?, width of iteration j, shrink?"""
+    r^(j) (and the first pair's residual), expand?, width of iteration j,
+    shrink?"""
     st = Strategy(kind, nes, nex, **params)
     nnow, widths = nex, []
     for j, r in enumerate(rs, start=1):
-        st.record(j, r)
+        st.record(j, r, None if r1 is None else r1[j - 1])
         if st.ifexpand(j, nnow):
             nnow = nex
         widths.append(nnow)
@@ -86,6 +88,25 @@ def test_trace_matches_oracle_on_random_histories(lib, seed):
         assert got_events, "the warm-up gate opened, so at least the first shrink must happen"
 
 
+@pytest.mark.parametrize("seed", range(24))
+def test_trace_matches_oracle_with_first_pair_warmup(lib, seed):
+    """warm_first: the gate reads the first pair's residual history, which
+    runs ahead of r^(j) by a random factor."""
+    rng = np.random.default_rng(1000 + seed)
+    kind = KINDS[1 + seed % 3]
+    params = dict(je=int(rng.choice([6, 12])), js=int(rng.choice([1, 2])), jp=int(rng.choice([3, 10])),
+                  mu=float(rng.choice([1.05, 1.1])), j_warm=int(rng.choice([1, 5])),
+                  r_warm=float(rng.choice([1e-1, 1e-4])), warm_first=int(seed % 2 == 0))
+    rs = random_history(rng, 120)
+    r1 = [x * 10.0 ** -rng.uniform(0.0, 3.0) for x in rs]
+    got = lib.eig_strategy_trace(kind, 69, 128, rs, r1=r1, **params)
+    want = oracle_trace(kind, 69, 128, rs, r1=r1, **params)
+    assert got == want
+    # without the option the first pair's history changes nothing
+    if not params["warm_first"]:
+        assert got == lib.eig_strategy_trace(kind, 69, 128, rs, **params)
+
+
 def test_trace_defaults_and_zero_residual(lib):
     # r^(j) = 0 is valid (log10 clamped at 1e-300 in both)
     rs = [1.0, 1e-3, 1e-5, 0.0, 0.0, 1e-9, 1e-9, 0.0] + [1e-10] * 30
@@ -103,6 +124,8 @@ def test_trace_rejects_bad_arguments(lib):
         lib.eig_strategy_trace("fix", 5, 8, [1.0, math.nan])
     with pytest.raises(lib.EigError):
         lib.eig_strategy_trace("fix", 5, 8, [1.0], je=0)
+    with pytest.raises(lib.EigError):
+        lib.eig_strategy_trace("fix", 5, 8, [1.0, 0.5], r1=[1.0, -0.5])   # negative first-pair residual
     raw = lib.load()
-    n = __import__("ctypes").c_int(0)
-    assert raw.eig_strategy_trace(7, 5, 8, None, None, 0, None, None, 0, __import__("ctypes").byref(n)) == 1
+    n = ctypes.c_int(0)
+    assert raw.eig_strategy_trace(7, 5, 8, None, None, None, 0, None, None, 0, ctypes.byref(n)) == 1
