@@ -59,17 +59,25 @@ extern "C" {
 #define EIG_ARITH_DF64 1  /* double-float blocks, FP32-pipe dd arithmetic    */
 #define EIG_ARITH_F32 2   /* float32 blocks, float32 arithmetic              */
 #define EIG_ARITH_C32 3   /* float32 blocks, compensated (Dot2) accumulation */
-/* eig_gram and eig_block_update only: double-float blocks, product on the
- * bf16 tensor cores by an exact integer splitting (Ozaki et al. 2012): each
- * value is cut into six 8-bit slices against a power-of-two scale shared by a
- * 128-index chunk of the contraction (128 rows of a column of U or V for the
- * Gram; 128 columns of a row of U and 128 rows of a column of C for the
- * update); the slice products of levels 0..5 are summed exactly and the rest
- * dropped, an error of about 2^-48 (at most about 28 * 2^-48) of the product
- * of the two chunk maxima per contraction index, i.e. normwise rather than
- * componentwise double-float accuracy.  Chunks whose maximum is below 2^-100
- * count as zero. */
+/* eig_gram and eig_block_update only: products on the bf16 tensor cores by
+ * an exact integer splitting (Ozaki et al. 2012).  Each value is cut into
+ * 8-bit slices against a power-of-two scale shared by a 128-index chunk of
+ * the contraction (128 rows of a column of U or V for the Gram; 128 columns
+ * of a row of U and 128 rows of a column of C for the update); the slice
+ * products of the kept levels are summed exactly in fp32 and the rest
+ * dropped.  The error is normwise: a bound per contraction index of a
+ * multiple of the product of the two chunk maxima.
+ *  EIG_ARITH_DF64_TC: EIG_DF64 blocks, six slices, levels 0..5: at most about
+ *    28 * 2^-48 of the chunk maxima per index (about 2^-48 on average),
+ *    double-float result; chunks whose maximum is below 2^-100 count as zero.
+ *  EIG_ARITH_F64_TC: EIG_F64 blocks, seven slices cut from the float64 bit
+ *    patterns by integer operations, levels 0..6, accumulated in
+ *    triple-float: at most about 2^-52 of the chunk maxima per index plus
+ *    2^-53 of the chunk sums per chunk -- the float64 dot-product bound with
+ *    the chunk maxima in place of the elements.  Subnormal values count as
+ *    zero; an infinite or NaN value makes the entries it touches NaN. */
 #define EIG_ARITH_DF64_TC 4
+#define EIG_ARITH_F64_TC 5
 
 /* ---- conversions ------------------------------------------------------- */
 /* dst[i] = src[i] for i < count, converting between EIG_F64 / EIG_F32 /
@@ -104,13 +112,24 @@ int eig_gram(int64_t n, int a, int b, const void *U, int64_t ldu, const void *V,
 
 /* ---- device status of the tensor-core products (no counterpart in the
  * paper) ----------------------------------------------------------------
- * The tcgen05 product kernels behind EIG_ARITH_DF64_TC bound every wait on
- * their shared-memory barriers; a wait that runs out ends the kernel early
- * (its results are then wrong) and records the fact on the device.  Returns
- * EIG_ETIMEOUT if that happened since the last call (and clears the record),
- * EIG_ECUDA if the record cannot be read, else EIG_OK.  Synchronises the
- * current device.  eig_solve() checks it itself. */
+ * The tcgen05 product kernels behind EIG_ARITH_DF64_TC and EIG_ARITH_F64_TC
+ * bound every wait on their shared-memory barriers; a wait that runs out
+ * ends the kernel early (its results are then wrong) and records the fact on
+ * the device.  Returns EIG_ETIMEOUT if that happened since the last call (and
+ * clears the record), EIG_ECUDA if the record cannot be read, else EIG_OK.
+ * Synchronises the current device.  eig_solve() checks it itself. */
 int eig_device_status(void);
+
+/* ---- self-test of the bounded waits (no counterpart in the paper) -------
+ * Launches one small tensor-core Gram product (arith EIG_ARITH_DF64_TC or
+ * EIG_ARITH_F64_TC, zero operands in temporary device memory) whose copy
+ * producer withholds the operands of its first pipeline stage, so that the
+ * MMA issuer's wait for them runs out after wait_s seconds (0 < wait_s <= 10);
+ * the kernel then frees its resources and ends, and the next
+ * eig_device_status() returns EIG_ETIMEOUT.  Synchronises the stream.  It
+ * faults nothing and leaves the context usable; the product's result is
+ * discarded. */
+int eig_tc_wait_selftest(int arith, double wait_s, void *stream);
 
 /* ---- allocation-free Gram product (no counterpart in the paper) ---------
  * Same product, arguments and result as eig_gram, for callers that cannot

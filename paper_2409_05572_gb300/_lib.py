@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(HERE, "libeig_gb300.so")
 EIG_OK, EIG_EINVAL, EIG_ENOMEM, EIG_ENOTCONV, EIG_EBREAKDOWN, EIG_ECUDA, EIG_ETIMEOUT = range(7)
 EIG_F64, EIG_F32, EIG_DF64 = 0, 1, 2
 ARITH_F64, ARITH_DF64, ARITH_F32, ARITH_C32 = 0, 1, 2, 3
-ARITH_DF64_TC = 4  # eig_gram only: double-float blocks, tensor-core product
+ARITH_DF64_TC = 4  # eig_gram / eig_block_update: double-float blocks, tensor-core product
+ARITH_F64_TC = 5   # eig_gram / eig_block_update: float64 blocks, tensor-core product
 STRATEGIES = {"none": 0, "fix": 1, "slope": 2, "slopek": 3}
 ALGOS = {"lobpcg": 0, "chebsi": 1, "sd": 2}
 FORMS = {"df64": 0, "f64": 1, "mixed": 2}
@@ -29,7 +30,7 @@ EXPORTS = ("eig_convert", "eig_spmm", "eig_gram", "eig_gram_noalloc", "eig_block
            "eig_cholqr2", "eig_syev", "eig_hl_trick", "eig_options_default", "eig_create", "eig_solve",
            "eig_query", "eig_destroy", "eig_strerror", "eig_footprint", "eig_server_create", "eig_submit",
            "eig_server_step", "eig_poll", "eig_release", "eig_server_destroy", "eig_device_status",
-           "eig_strategy_trace")
+           "eig_strategy_trace", "eig_tc_wait_selftest")
 
 
 class EigError(RuntimeError):
@@ -86,6 +87,7 @@ def load(path: str = LIB_PATH):
         "eig_gram": [i64, i32, i32, p, i64, p, i64, i32, i32, p, i64, p],
         "eig_gram_noalloc": [i64, i32, i32, p, i64, p, i64, i32, i32, p, i64, p],
         "eig_device_status": [],
+        "eig_tc_wait_selftest": [i32, d, p],
         "eig_block_update": [i64, i32, i32, p, i64, p, i64, p, i64, d, i32, p],
         "eig_residual": [i64, i32, p, i64, p, i64, p, p, p, i64, p, p, i32, p],
         "eig_cholqr2": [i64, i32, p, i64, i32, C.POINTER(C.c_int), p],
@@ -231,6 +233,13 @@ def device_status():
     """EIG_ETIMEOUT if a bounded wait inside a tensor-core product ran out
     since the last call (clears it), else 0; synchronises the device."""
     return int(load().eig_device_status())
+
+
+def eig_tc_wait_selftest(arith, wait_s, stream=None):
+    """Launch a tensor-core Gram product whose first stage is withheld, so a
+    bounded wait runs out after wait_s seconds; device_status() then reports
+    EIG_ETIMEOUT."""
+    return _check("eig_tc_wait_selftest", load().eig_tc_wait_selftest(arith, wait_s, _stream(stream)))
 
 
 def eig_gram_noalloc(n, a, b, U, ldu, V, ldv, arith, sym, G, ldg, stream=None):

@@ -41,25 +41,34 @@ cudaError_t gram_capped(int64_t n, const Blk<typename Pol<A>::T>& U, const Blk<t
 cudaError_t gram_reduce(int a, int b, int nsplit, bool sym, const double* part, double* G, int64_t ldg,
                         cudaStream_t st, const int* gate = nullptr);
 
-// Tensor-core products of double-float blocks (k_tc.cu).  A slice buffer
-// holds the exact bf16 integer slices of an operand with contraction length
-// K and M operand rows: tc_slice_bytes(K, M) bytes, 16-byte aligned.
+// Tensor-core products (k_tc.cu, k_tc5.cu) of double-float blocks (6 exact
+// bf16 slices) and float64 blocks (7 slices).  A slice buffer holds the
+// slices of an operand with contraction length K and M operand rows:
+// tc_slice_bytes(ns, K, M) bytes, 16-byte aligned.
 //  - Gram G = U^T V (n x a, n x b): tc_slice_cols() of U and V (K = n,
 //    M = width), gram_tc_product() with split-K partial tiles in scratch
 //    (gram_tc_scratch_elems() float64 elements).
 //  - Update Y = U (scale C) + beta Y (U: n x s, C: s x c float64): tc_slice_rows()
 //    of U (K = s, M = n), tc_slice_coef() of C (K = s, M = c),
 //    update_tc_product().  Y must not overlap U.
-size_t tc_slice_bytes(int64_t K, int64_t M);
-size_t gram_tc_scratch_elems(int64_t n, int a, int b, bool sym);
-cudaError_t tc_slice_cols(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t st, const int* gate = nullptr);
-cudaError_t tc_slice_rows(int64_t n, const Blk<dd>& U, void* buf, cudaStream_t st, const int* gate = nullptr);
-cudaError_t tc_slice_coef(int s, int c, const double* C, int64_t ldc, double scale, void* buf, cudaStream_t st,
-                          const int* gate = nullptr);
-cudaError_t gram_tc_product(int64_t n, int a, int b, const void* slu, const void* slv, bool sym, double* G,
+// T = dd (ns = 6) or double (ns = 7).
+size_t tc_slice_bytes(int ns, int64_t K, int64_t M);
+size_t gram_tc_scratch_elems(int ns, int64_t n, int a, int b, bool sym);
+template <typename T>
+cudaError_t tc_slice_cols(int64_t n, const Blk<T>& U, void* buf, cudaStream_t st, const int* gate = nullptr);
+template <typename T>
+cudaError_t tc_slice_rows(int64_t n, const Blk<T>& U, void* buf, cudaStream_t st, const int* gate = nullptr);
+cudaError_t tc_slice_coef(int ns, int s, int c, const double* C, int64_t ldc, double scale, void* buf,
+                          cudaStream_t st, const int* gate = nullptr);
+cudaError_t gram_tc_product(int ns, int64_t n, int a, int b, const void* slu, const void* slv, bool sym, double* G,
                             int64_t ldg, double* scratch, cudaStream_t st, const int* gate = nullptr);
-cudaError_t update_tc_product(int64_t n, int s, int c, const void* slu, const void* slc, const Blk<dd>& Y,
+template <typename T>
+cudaError_t update_tc_product(int64_t n, int s, int c, const void* slu, const void* slc, const Blk<T>& Y,
                               double beta, cudaStream_t st, const int* gate = nullptr);
+// Bounded-wait self-test: a Gram product (slices made) whose first stage is
+// withheld, so a wait of the product kernel runs out after wait_s seconds.
+cudaError_t tc_wait_selftest(int ns, int64_t n, int a, int b, const void* slu, const void* slv, double* scratch,
+                             double wait_s, cudaStream_t st);
 
 // Cs[i][j] (leading dimension ldo) = staged(scale * C[i][j]) for an s x c
 // float64 matrix.

@@ -2,6 +2,7 @@
 // the hot path, dispatched on element format / arithmetic.  Temporary device
 // memory comes from cudaMallocAsync on the caller's stream.
 #include <cstdio>
+#include <type_traits>
 
 #include "blocks.cuh"
 #include "small.cuh"
@@ -32,6 +33,7 @@ Blk<T> one(const void* p, int64_t ld, int w) {
 }
 
 bool arith_ok(int a) { return a >= EIG_ARITH_F64 && a <= EIG_ARITH_C32; }
+bool arith_tc(int a) { return a == EIG_ARITH_DF64_TC || a == EIG_ARITH_F64_TC; }
 
 template <Arith A>
 int gram_t(int64_t n, int a, int b, const void* U, int64_t ldu, const void* V, int64_t ldv, int sym,
@@ -55,37 +57,44 @@ int update_t(int64_t n, int s, int c, const void* U, int64_t ldu, const double* 
   return cuda_status(update<A>(n, one<T>(U, ldu, s), static_cast<S*>(cs.p), c, one<T>(Y, ldy, c), beta, st));
 }
 
-// double-float blocks, product on the tensor cores (k_tc.cu)
+// products on the tensor cores (k_tc.cu): T = dd (6 slices) or double (7)
+template <typename T>
 int gram_tc_t(int64_t n, int a, int b, const void* U, int64_t ldu, const void* V, int64_t ldv, int sym, double* G,
               int64_t ldg, cudaStream_t st) {
+  const int ns = std::is_same<T, dd>::value ? tc::NS_DF : tc::NS_F64;
   const bool same = U == V && ldu == ldv && a == b;
-  const size_t su = (tc_slice_bytes(n, a) + 255) / 256 * 256;
-  const size_t sv = same ? 0 : tc_slice_bytes(n, b);
+  const size_t su = (tc_slice_bytes(ns, n, a) + 255) / 256 * 256;
+  const size_t sv = same ? 0 : tc_slice_bytes(ns, n, b);
   Tmp sl(st), scr(st);
   if (sl.alloc(su + sv) != cudaSuccess) return EIG_ENOMEM;
-  if (scr.alloc(sizeof(double) * gram_tc_scratch_elems(n, a, b, sym != 0)) != cudaSuccess) return EIG_ENOMEM;
+  if (scr.alloc(sizeof(double) * gram_tc_scratch_elems(ns, n, a, b, sym != 0)) != cudaSuccess) return EIG_ENOMEM;
   char* pu = static_cast<char*>(sl.p);
   char* pv = same ? pu : pu + su;
-  cudaError_t e = tc_slice_cols(n, one<dd>(U, ldu, a), pu, st);
-  if (e == cudaSuccess && !same) e = tc_slice_cols(n, one<dd>(V, ldv, b), pv, st);
-  if (e == cudaSuccess) e = gram_tc_product(n, a, b, pu, pv, sym != 0, G, ldg, static_cast<double*>(scr.p), st);
+  cudaError_t e = tc_slice_cols<T>(n, one<T>(U, ldu, a), pu, st);
+  if (e == cudaSuccess && !same) e = tc_slice_cols<T>(n, one<T>(V, ldv, b), pv, st);
+  if (e == cudaSuccess)
+    e = gram_tc_product(ns, n, a, b, pu, pv, sym != 0, G, ldg, static_cast<double*>(scr.p), st);
   return cuda_status(e);
 }
 
+template <typename T>
 int update_tc_t(int64_t n, int s, int c, const void* U, int64_t ldu, const double* C, int64_t ldc, void* Y,
                 int64_t ldy, double beta, cudaStream_t st) {
-  if (s == 0) return update_t<Arith::DF64>(n, s, c, U, ldu, C, ldc, Y, ldy, beta, st);
-  const size_t su = (tc_slice_bytes(s, n) + 255) / 256 * 256;
+  const int ns = std::is_same<T, dd>::value ? tc::NS_DF : tc::NS_F64;
+  if (s == 0) {
+    if (std::is_same<T, dd>::value) return update_t<Arith::DF64>(n, s, c, U, ldu, C, ldc, Y, ldy, beta, st);
+    return update_t<Arith::F64>(n, s, c, U, ldu, C, ldc, Y, ldy, beta, st);
+  }
+  const size_t su = (tc_slice_bytes(ns, s, n) + 255) / 256 * 256;
   Tmp sl(st);
-  if (sl.alloc(su + tc_slice_bytes(s, c)) != cudaSuccess) return EIG_ENOMEM;
+  if (sl.alloc(su + tc_slice_bytes(ns, s, c)) != cudaSuccess) return EIG_ENOMEM;
   char* pu = static_cast<char*>(sl.p);
   char* pc = pu + su;
-  cudaError_t e = tc_slice_coef(s, c, C, ldc, 1.0, pc, st);
-  if (e == cudaSuccess) e = tc_slice_rows(n, one<dd>(U, ldu, s), pu, st);
-  if (e == cudaSuccess) e = update_tc_product(n, s, c, pu, pc, one<dd>(Y, ldy, c), beta, st);
+  cudaError_t e = tc_slice_coef(ns, s, c, C, ldc, 1.0, pc, st);
+  if (e == cudaSuccess) e = tc_slice_rows<T>(n, one<T>(U, ldu, s), pu, st);
+  if (e == cudaSuccess) e = update_tc_product<T>(n, s, c, pu, pc, one<T>(Y, ldy, c), beta, st);
   return cuda_status(e);
 }
-
 
 template <Arith A>
 int residual_t(int64_t n, int w, const void* X, int64_t ldx, const void* AX, int64_t ldax, const double* lam,
@@ -186,16 +195,34 @@ int eig_device_status(void) {
   return v < 0 ? EIG_ECUDA : (v ? EIG_ETIMEOUT : EIG_OK);
 }
 
+int eig_tc_wait_selftest(int arith, double wait_s, void* stream) {
+  if (!arith_tc(arith) || !(wait_s > 0.0) || wait_s > 10.0) return EIG_EINVAL;
+  const int ns = arith == EIG_ARITH_DF64_TC ? tc::NS_DF : tc::NS_F64;
+  constexpr int64_t n = 1024;
+  constexpr int a = 128, b = 64;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t su = (tc_slice_bytes(ns, n, a) + 255) / 256 * 256, sv = tc_slice_bytes(ns, n, b);
+  Tmp sl(st), scr(st);
+  if (sl.alloc(su + sv) != cudaSuccess) return EIG_ENOMEM;
+  if (scr.alloc(sizeof(double) * gram_tc_scratch_elems(ns, n, a, b, false)) != cudaSuccess) return EIG_ENOMEM;
+  if (cudaMemsetAsync(sl.p, 0, su + sv, st) != cudaSuccess) return EIG_ECUDA;
+  char* pu = static_cast<char*>(sl.p);
+  if (tc_wait_selftest(ns, n, a, b, pu, pu + su, static_cast<double*>(scr.p), wait_s, st) != cudaSuccess)
+    return EIG_ECUDA;
+  return cuda_status(cudaStreamSynchronize(st));
+}
+
 int eig_gram(int64_t n, int a, int b, const void* U, int64_t ldu, const void* V, int64_t ldv, int arith, int sym,
              double* G, int64_t ldg, void* stream) {
   if (n < 0 || a < 0 || b < 0 || a > 4096 || b > 4096 || ldu < a || ldv < b || ldg < b) return EIG_EINVAL;
-  if ((!arith_ok(arith) && arith != EIG_ARITH_DF64_TC) || (sym && a != b)) return EIG_EINVAL;
+  if ((!arith_ok(arith) && !arith_tc(arith)) || (sym && a != b)) return EIG_EINVAL;
   if (a == 0 || b == 0) return EIG_OK;
   if (!U || !V || !G) return EIG_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (n == 0) return cuda_status(cudaMemset2DAsync(G, sizeof(double) * ldg, 0, sizeof(double) * b, a, st));
   switch (arith) {
-    case EIG_ARITH_DF64_TC: return gram_tc_t(n, a, b, U, ldu, V, ldv, sym, G, ldg, st);
+    case EIG_ARITH_DF64_TC: return gram_tc_t<dd>(n, a, b, U, ldu, V, ldv, sym, G, ldg, st);
+    case EIG_ARITH_F64_TC: return gram_tc_t<double>(n, a, b, U, ldu, V, ldv, sym, G, ldg, st);
     case EIG_ARITH_F64: return gram_t<Arith::F64>(n, a, b, U, ldu, V, ldv, sym, G, ldg, st);
     case EIG_ARITH_DF64: return gram_t<Arith::DF64>(n, a, b, U, ldu, V, ldv, sym, G, ldg, st);
     case EIG_ARITH_F32: return gram_t<Arith::F32>(n, a, b, U, ldu, V, ldv, sym, G, ldg, st);
@@ -205,13 +232,14 @@ int eig_gram(int64_t n, int a, int b, const void* U, int64_t ldu, const void* V,
 
 int eig_block_update(int64_t n, int s, int c, const void* U, int64_t ldu, const double* C, int64_t ldc, void* Y,
                      int64_t ldy, double beta, int arith, void* stream) {
-  if (n < 0 || s < 0 || c < 0 || ldu < s || ldc < c || ldy < c || (!arith_ok(arith) && arith != EIG_ARITH_DF64_TC))
+  if (n < 0 || s < 0 || c < 0 || ldu < s || ldc < c || ldy < c || (!arith_ok(arith) && !arith_tc(arith)))
     return EIG_EINVAL;
   if (n == 0 || c == 0) return EIG_OK;
   if (!Y || (s > 0 && (!U || !C))) return EIG_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   switch (arith) {
-    case EIG_ARITH_DF64_TC: return update_tc_t(n, s, c, U, ldu, C, ldc, Y, ldy, beta, st);
+    case EIG_ARITH_DF64_TC: return update_tc_t<dd>(n, s, c, U, ldu, C, ldc, Y, ldy, beta, st);
+    case EIG_ARITH_F64_TC: return update_tc_t<double>(n, s, c, U, ldu, C, ldc, Y, ldy, beta, st);
     case EIG_ARITH_F64: return update_t<Arith::F64>(n, s, c, U, ldu, C, ldc, Y, ldy, beta, st);
     case EIG_ARITH_DF64: return update_t<Arith::DF64>(n, s, c, U, ldu, C, ldc, Y, ldy, beta, st);
     case EIG_ARITH_F32: return update_t<Arith::F32>(n, s, c, U, ldu, C, ldc, Y, ldy, beta, st);

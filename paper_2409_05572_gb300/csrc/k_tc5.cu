@@ -1,38 +1,65 @@
-// tcgen05 product kernel of the sliced double-float products (Gram G = U^T V
-// and update Y = U C + beta Y of Algorithms 1-3 of arXiv:2409.05572; the
-// exact slicing and its error bound are described in k_tc.cu, the slice
-// layout in tc.cuh).
+// tcgen05 product kernel of the sliced block products: the Gram products
+// G = U^T V and the block updates Y = U C + beta Y of the Rayleigh-Ritz,
+// orthogonalisation and update steps (Algorithms 1-3 of arXiv:2409.05572).
+// The exact slicing and the slice layout are described in tc.cuh; NS = 6
+// slices for double-float operands, NS = 7 for float64 operands.
+//
+// Output tiles are 128 x BN.  BN = 32: two sets of NS level accumulators
+// (NS x 32 TMEM columns each) alternate by chunk, so the flush of one chunk
+// runs while the MMAs of the next fill the other set.  BN = 64: one set of
+// NS x 64 columns; the MMAs of the next chunk wait until the flush warps have
+// read the levels.
 //
 // One CTA per SM, 320 threads in three roles:
-//   warp 0, one thread   producer: per 32-index K block, 6 + 6 bulk copies
+//   warp 0, one thread   producer: per 16-index K block, NS + NS bulk copies
 //                        (cp.async.bulk, the TMA engine) of the A tile
-//                        (128 rows, 8 KB per slice) and the B tile (64 rows,
-//                        4 KB per slice) into a 3-stage ring; each stage
-//                        completes an mbarrier by transaction count.
-//   warp 1, one thread   MMA issuer: per K block and 16-index half, the 21
-//                        slice pairs (i, j), i + j <= 5, as eight tcgen05.mma
-//                        (M = 128, N = 64 .. 256, K = 16, bf16 in, fp32 out)
-//                        into the TMEM accumulators of the levels i + j (6 x 64
-//                        columns); tcgen05.commit frees the stage and, after
-//                        the last K block of a 128-index chunk, hands the
-//                        six exact level sums to the flush warps.
+//                        (128 rows, 4 KB per slice) and the B tile (BN rows)
+//                        into a ring of stages; each stage completes an
+//                        mbarrier by transaction count.
+//   warp 1, one thread   MMA issuer: per K block, all slice pairs (i, j) with
+//                        i + j < NS as tcgen05.mma (M = 128, N = BN .. 256,
+//                        K = 16, bf16 in, fp32 out) into the TMEM accumulator
+//                        of level i + j; tcgen05.commit frees the stage and,
+//                        after the 8 K blocks of a 128-index chunk, hands the
+//                        exact level sums to the flush warps.
 //   warps 2..9           flush: each warp owns the 32 TMEM lanes (tile rows)
-//                        of its lane quarter and 32 of the 64 columns; per
-//                        chunk it reads the six levels (tcgen05.ld), releases
-//                        TMEM to the issuer, combines the levels into a
-//                        double-float, scales by 2^(e_a - 7) 2^(e_b - 7) and
-//                        adds to its registers; at the end of a tile it writes
-//                        the float64 partial (Gram) or Y (update).
+//                        of its lane quarter and half of the BN columns; per
+//                        chunk it reads the NS levels (tcgen05.ld), releases
+//                        the set to the issuer, combines the levels, scales
+//                        by the chunk exponents and adds to an accumulator in
+//                        registers (double-float for NS = 6, triple-float for
+//                        NS = 7); at the end of a tile it writes the float64
+//                        split-K partial (Gram) or Y (update).
 // Shared-memory operands use the no-swizzle K-major canonical layout: 8 x 16
-// byte core matrices, 128 bytes apart along K (leading byte offset) and 512
+// byte core matrices, 128 bytes apart along K (leading byte offset) and 256
 // bytes apart along M/N (stride byte offset).
+//
+// Scales.  NS = 6: the chunk value is multiplied by 2^(e_a - 7) 2^(e_b - 7)
+// in fp32 (double-float has the float32 exponent range).  NS = 7: float64
+// exponents do not fit a float, so each flush thread takes reference
+// exponents r_a (its row) and r_b (each column) as the largest chunk
+// exponents of the tile's K range, scales a chunk by 2^(e_a - r_a) 2^(e_b - r_b)
+// <= 1 in fp32 (contributions below 2^-126 of the largest chunk drop out) and
+// multiplies the float64 result by 2^(r_a + r_b - 14) at the end.
+//
+// Accuracy (NS = 7).  Per chunk, the seven level sums are combined into
+// hi + lo (exact) + small (error at most 2^-54 of the largest possible chunk
+// sum; tc.cuh, combine7); the dropped levels 7..12 and the residual of the
+// seven-digit representation add at most about 8 * 2^-56 of max|a| max|b|
+// per index.  The triple-float accumulator (m0, m1, m2) takes hi and lo by
+// error-free TwoSums and rounds only in m2, whose magnitude stays below
+// about 2^-29 of the sum, so over K = 128 m indices the error is at most
+// about 2^-52 sum_chunks 128 M_a M_b + m 2^-53 sum_chunks |c_k| -- within the
+// float64 dot-product bound gamma_K sum |a b| with the chunk maxima in place
+// of the elements.
 //
 // Every wait on an mbarrier is bounded; on expiry the kernel raises the
 // abort flag, records the expiry in the device error word, lets the other
 // roles leave their loops, waits (bounded) for its own copies and MMAs and
-// frees TMEM before returning.
+// frees TMEM before returning.  The self-test entry point withholds the
+// copies of one stage so that a wait runs out on purpose.
 #include <cstdint>
-#include <cstdlib>
+#include <type_traits>
 
 #include "blocks.cuh"
 #include "tc.cuh"
@@ -45,16 +72,22 @@ __device__ int g_tc5_error = 0;  // set when a bounded wait expired
 namespace {
 
 constexpr int BM = 128;                        // A rows per tile (MMA M)
-constexpr int BN = 64;                         // B rows per tile (MMA N)
-constexpr int NST = 3;                         // stages of one 32-index K block
-constexpr uint32_t A_SLICE = BM * KB * 2;      // 8 KB
-constexpr uint32_t B_SLICE = BN * KB * 2;      // 4 KB
-constexpr uint32_t STAGE = S * (A_SLICE + B_SLICE);
-constexpr uint32_t TMEM_COLS = 512;            // 6 levels x 64 columns used
+constexpr uint32_t A_SLICE = BM * KB * 2;      // 4 KB
+template <int NS, int BN> struct Cfg {
+  static constexpr uint32_t B_SLICE = BN * KB * 2;
+  static constexpr uint32_t STAGE = NS * (A_SLICE + B_SLICE);
+  static constexpr int NST = int((210u * 1024u) / STAGE);   // stages in about 210 KB
+  static constexpr size_t SMEM = size_t(NST) * STAGE + 1024;  // + alignment slack
+  static constexpr int NSETS = BN == 32 ? 2 : 1;             // TMEM accumulator sets
+  static constexpr uint32_t SET_COLS = uint32_t(NS * BN);
+  static constexpr int GRP = 256 / BN;                       // B slices per MMA (N <= 256)
+  static constexpr int COLS_T = BN / 2;                      // columns per flush thread
+  static_assert(NSETS * SET_COLS <= 512, "TMEM");
+};
+constexpr uint32_t TMEM_COLS = 512;
 constexpr int FLUSH_WARPS = 8;
 constexpr int THREADS = 32 * (2 + FLUSH_WARPS);
-constexpr size_t SMEM = size_t(NST) * STAGE + 1024;  // + alignment slack
-constexpr uint32_t LBO = 128, SBO = 512;
+constexpr uint32_t LBO = 128, SBO = 256;
 // instruction descriptor: D f32, A and B bf16, both K-major, N >> 3, M >> 4
 __host__ __device__ constexpr uint32_t idesc(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(BM >> 4) << 24);
@@ -90,14 +123,14 @@ __device__ __forceinline__ uint64_t now_ns() {
 }
 
 // bounded wait for the completion of the phase with the given parity; false
-// when another role aborted or WAIT_NS passed (then this one aborts)
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+// when another role aborted or wait_ns passed (then this one aborts)
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, uint64_t wait_ns) {
   const uint64_t t0 = now_ns();
   for (uint32_t i = 0;; ++i) {
     if (mbar_test(bar, parity)) return true;
     if ((i & 63) == 63) {
       if (*abort) return false;
-      if (now_ns() - t0 > WAIT_NS) break;
+      if (now_ns() - t0 > wait_ns) break;
     }
   }
   *abort = 1;
@@ -106,10 +139,10 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile i
 }
 
 // bounded wait that does not abort (draining at exit)
-__device__ __noinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+__device__ __noinline__ void mbar_drain(uint32_t bar, uint32_t parity, uint64_t wait_ns) {
   const uint64_t t0 = now_ns();
   while (!mbar_test(bar, parity))
-    if (now_ns() - t0 > WAIT_NS) {
+    if (now_ns() - t0 > wait_ns) {
       atomicExch(&g_tc5_error, 1);
       return;
     }
@@ -137,25 +170,24 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
       : "memory");
 }
 
-// All slice pairs (qi, qj), qi + qj <= 5, of one 16-index K step.  The B
-// slices lie in shared memory one after another with the same 512-byte
-// row-group stride, so B slices qj .. qj + m - 1 form one operand of
-// N = 64 m rows; with D at TMEM column 64 qi, the product of A slice qi with
-// B slice qj lands in the columns of level qi + qj.  Eight MMAs (N <= 256)
-// cover the 21 pairs.  first: the first K step of a chunk (overwrite).
-__device__ __forceinline__ void mma_kstep(uint32_t tmem, uint32_t sa, uint32_t sb, bool first) {
-  const uint32_t acc = first ? 0u : 1u;
-  // qi = 0: levels 0..3 and 4..5 (these two start every level of the chunk)
-  mma(tmem + 0 * BN, sdesc(sa + 0 * A_SLICE), sdesc(sb + 0 * B_SLICE), idesc(4 * BN), acc);
-  mma(tmem + 4 * BN, sdesc(sa + 0 * A_SLICE), sdesc(sb + 4 * B_SLICE), idesc(2 * BN), acc);
-  // qi = 1: levels 1..4 and 5
-  mma(tmem + 1 * BN, sdesc(sa + 1 * A_SLICE), sdesc(sb + 0 * B_SLICE), idesc(4 * BN), 1u);
-  mma(tmem + 5 * BN, sdesc(sa + 1 * A_SLICE), sdesc(sb + 4 * B_SLICE), idesc(1 * BN), 1u);
-  // qi = 2 .. 5: levels qi .. 5
-  mma(tmem + 2 * BN, sdesc(sa + 2 * A_SLICE), sdesc(sb), idesc(4 * BN), 1u);
-  mma(tmem + 3 * BN, sdesc(sa + 3 * A_SLICE), sdesc(sb), idesc(3 * BN), 1u);
-  mma(tmem + 4 * BN, sdesc(sa + 4 * A_SLICE), sdesc(sb), idesc(2 * BN), 1u);
-  mma(tmem + 5 * BN, sdesc(sa + 5 * A_SLICE), sdesc(sb), idesc(1 * BN), 1u);
+// All slice pairs (qi, qj), qi + qj < NS, of one 16-index K block, into the
+// accumulator set at TMEM address tset.  The B slices lie in shared memory
+// one after another at the same 256-byte row-group stride, so B slices
+// qj .. qj + m - 1 form one operand of N = BN m rows; with D at column
+// BN (qi + qj), the product of A slice qi with B slice qj lands in the
+// columns of level qi + qj.  The qi = 0 products touch every level and come
+// first: first = the first K block of a chunk (overwrite).
+template <int NS, int BN>
+__device__ __forceinline__ void mma_kstep(uint32_t tset, uint32_t sa, uint32_t sb, bool first) {
+  using C = Cfg<NS, BN>;
+#pragma unroll
+  for (int qi = 0; qi < NS; ++qi)
+#pragma unroll
+    for (int qj = 0; qj < NS - qi; qj += C::GRP) {
+      const int m = (NS - qi - qj) < C::GRP ? (NS - qi - qj) : C::GRP;
+      mma(tset + uint32_t(BN * (qi + qj)), sdesc(sa + uint32_t(qi) * A_SLICE),
+          sdesc(sb + uint32_t(qj) * C::B_SLICE), idesc(BN * m), (qi == 0 && first) ? 0u : 1u);
+    }
 }
 __device__ __forceinline__ void commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -163,34 +195,78 @@ __device__ __forceinline__ void commit(uint32_t bar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 16 consecutive TMEM columns of this thread's lane in each of the six
-// level accumulators (64 columns apart), one wait for all six loads
-__device__ __forceinline__ void tmem_ld_levels(uint32_t taddr, float (*v)[16]) {
-  uint32_t r[96];
+// 16 consecutive TMEM columns of this thread's lane of one level accumulator
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%96];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%97];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47}, [%98];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%99];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%64,%65,%66,%67,%68,%69,%70,%71,%72,%73,%74,%75,%76,%77,%78,%79}, [%100];\n"
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%80,%81,%82,%83,%84,%85,%86,%87,%88,%89,%90,%91,%92,%93,%94,%95}, [%101];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63]), "=r"(r[64]), "=r"(r[65]), "=r"(r[66]), "=r"(r[67]), "=r"(r[68]), "=r"(r[69]), "=r"(r[70]), "=r"(r[71]), "=r"(r[72]), "=r"(r[73]), "=r"(r[74]), "=r"(r[75]), "=r"(r[76]), "=r"(r[77]), "=r"(r[78]), "=r"(r[79]), "=r"(r[80]), "=r"(r[81]), "=r"(r[82]), "=r"(r[83]), "=r"(r[84]), "=r"(r[85]), "=r"(r[86]), "=r"(r[87]), "=r"(r[88]), "=r"(r[89]), "=r"(r[90]), "=r"(r[91]), "=r"(r[92]), "=r"(r[93]), "=r"(r[94]), "=r"(r[95])
-      : "r"(taddr), "r"(taddr + 64u), "r"(taddr + 128u), "r"(taddr + 192u), "r"(taddr + 256u), "r"(taddr + 320u)
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
       : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// the NS level accumulators (BN columns apart), 16 columns each, one wait
+template <int NS, int BN>
+__device__ __forceinline__ void tmem_ld_levels(uint32_t taddr, float (*v)[16]) {
+  uint32_t r[NS][16];
 #pragma unroll
-  for (int l = 0; l < 6; ++l)
+  for (int l = 0; l < NS; ++l) tmem_ld16(taddr + uint32_t(BN * l), r[l]);
+  tmem_wait_ld();
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[l][i] = __uint_as_float(r[16 * l + i]);
+  for (int l = 0; l < NS; ++l)
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[l][i] = __uint_as_float(r[l][i]);
 }
 
-// MODE 0: Gram (tile (blockIdx.y, blockIdx.x) of 128 x 64, K blocks
+// accumulators: double-float (NS = 6) and triple-float (NS = 7)
+struct tf {
+  float m0, m1, m2;
+};
+__device__ __forceinline__ void acc_zero(dd& m) { m = {0.f, 0.f}; }
+__device__ __forceinline__ void acc_zero(tf& m) { m = {0.f, 0.f, 0.f}; }
+
+// chunk value of one element from its NS prescaled level sums, added with
+// scale sc (a power of two or zero)
+__device__ __forceinline__ void flush_one(dd& m, const float* a, float sc) {
+  float hi, lo;
+  combine6(a, hi, lo);
+  add_scaled(m, hi, lo, sc);
+}
+// m0 + m1 + m2 += (hi + lo + small) sc: hi into m0 and lo into m1 by TwoSum
+// (exact), the rounding errors and small into m2
+__device__ __forceinline__ void flush_one(tf& m, const float* a, float sc) {
+  float hi, lo, small;
+  combine7(a, hi, lo, small);
+  float s0, e0, s1, e1, s2, e2;
+  two_sum(m.m0, hi * sc, s0, e0);
+  two_sum(m.m1, lo * sc, s1, e1);
+  two_sum(s1, e0, s2, e2);
+  m.m0 = s0;
+  m.m1 = s2;
+  m.m2 += (e1 + e2) + small * sc;
+}
+__device__ __forceinline__ double acc_value(const dd& m) { return double(m.hi) + double(m.lo); }
+__device__ __forceinline__ double acc_value(const tf& m) { return (double(m.m0) + double(m.m1)) + double(m.m2); }
+
+template <int NS>
+using AccT = std::conditional_t<NS == 6, dd, tf>;
+
+// MODE 0: Gram (tile (blockIdx.y, blockIdx.x) of 128 x BN, K blocks
 // [z * kb_per, (z + 1) * kb_per) of split z = blockIdx.z).
 // MODE 1: update (persistent: tiles t = blockIdx.x + i * gridDim.x of the
 // tiles_m x tiles_n output tiles, N fastest, all K blocks).
-template <int MODE>
+// withhold >= 0 (self-test only): the producer issues no copies for stage
+// position withhold, so the issuer's wait for it runs out after wait_ns.
+template <int MODE, int NS, int BN, typename T>
 __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb, int kb_per, int tiles_n,
-                                                         int nitems, GramOut go, UpdOut uo, const int* gate) {
+                                                         int nitems, GramOut go, UpdOut<T> uo, const int* gate,
+                                                         int withhold, uint64_t wait_ns) {
+  using C = Cfg<NS, BN>;
+  constexpr int NST = C::NST;
+  constexpr int NSETS = C::NSETS;
+  constexpr int CT = C::COLS_T;
+  constexpr uint32_t STAGE = C::STAGE;
   if (gate && *gate == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -220,9 +296,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb
     if (nitem_cta == 0 || nkb_item == 0) return;
   }
   const int nchunk = nkb_item / KBC;  // K blocks come in whole chunks
+  const int kc0 = kb0 / KBC;
 
   extern __shared__ uint8_t dsm[];
-  __shared__ __align__(8) uint64_t bar_full[NST], bar_empty[NST], bar_accf, bar_acce, bar_done;
+  __shared__ __align__(8) uint64_t bar_full[NST], bar_empty[NST], bar_accf[NSETS], bar_acce[NSETS], bar_done;
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
   const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
@@ -233,8 +310,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb
       mbar_init(smem_u32(&bar_full[s]), 1);
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
-    mbar_init(smem_u32(&bar_accf), 1);
-    mbar_init(smem_u32(&bar_acce), FLUSH_WARPS);
+    for (int s = 0; s < NSETS; ++s) {
+      mbar_init(smem_u32(&bar_accf[s]), 1);
+      mbar_init(smem_u32(&bar_acce[s]), FLUSH_WARPS);
+    }
     mbar_init(smem_u32(&bar_done), 1);
     abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -259,20 +338,22 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb
         const int64_t m0 = int64_t(item / tiles_n) * BM, n0 = int64_t(item % tiles_n) * BN;
         for (int kbi = 0; kbi < nkb_item; ++kbi, ++p) {
           const int s = p % NST;
-          if (p >= NST && !mbar_wait(smem_u32(&bar_empty[s]), uint32_t((p / NST - 1) & 1), abort)) break;
+          if (p >= NST && !mbar_wait(smem_u32(&bar_empty[s]), uint32_t((p / NST - 1) & 1), abort, wait_ns)) break;
+          if (p == withhold) continue;  // self-test: this stage never fills
           const uint32_t fb = smem_u32(&bar_full[s]);
           mbar_expect_tx(fb, STAGE);
           const int64_t kb = kb0 + kbi;
-          const uint32_t sa = base + uint32_t(s) * STAGE, sb = sa + S * A_SLICE;
+          const uint32_t sa = base + uint32_t(s) * STAGE, sb = sa + NS * A_SLICE;
 #pragma unroll 1
-          for (int q = 0; q < S; ++q) {
+          for (int q = 0; q < NS; ++q) {
             bulk_g2s(sa + q * A_SLICE, A.sl + (int64_t(q) * nkb + kb) * A.Mp * KB + m0 * KB, A_SLICE, fb);
-            bulk_g2s(sb + q * B_SLICE, B.sl + (int64_t(q) * nkb + kb) * B.Mp * KB + n0 * KB, B_SLICE, fb);
+            bulk_g2s(sb + q * C::B_SLICE, B.sl + (int64_t(q) * nkb + kb) * B.Mp * KB + n0 * KB, C::B_SLICE, fb);
           }
         }
       }
       // the last stages' copies have landed before the CTA may exit
-      for (int pp = max(0, p - NST); pp < p; ++pp) mbar_drain(smem_u32(&bar_full[pp % NST]), uint32_t((pp / NST) & 1));
+      for (int pp = max(0, p - NST); pp < p; ++pp)
+        if (pp != withhold) mbar_drain(smem_u32(&bar_full[pp % NST]), uint32_t((pp / NST) & 1), wait_ns);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -282,105 +363,161 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb
       bool ok = true;
       for (int it = 0; it < nitem_cta && ok; ++it) {
         for (int ch = 0; ch < nchunk && ok; ++ch, ++c) {
-          if (c > 0 && !(ok = mbar_wait(smem_u32(&bar_acce), uint32_t((c - 1) & 1), abort))) break;
+          const int set = c % NSETS, use = c / NSETS;  // use-th time this set is filled
+          if (use > 0 && !(ok = mbar_wait(smem_u32(&bar_acce[set]), uint32_t((use - 1) & 1), abort, wait_ns)))
+            break;
           fence_after();
+          const uint32_t tset = tmem + uint32_t(set) * C::SET_COLS;
           for (int h = 0; h < KBC; ++h, ++p) {
             const int s = p % NST;
-            if (!(ok = mbar_wait(smem_u32(&bar_full[s]), uint32_t((p / NST) & 1), abort))) break;
+            if (!(ok = mbar_wait(smem_u32(&bar_full[s]), uint32_t((p / NST) & 1), abort, wait_ns))) break;
             fence_after();
-            const uint32_t sa = base + uint32_t(s) * STAGE, sb = sa + S * A_SLICE;
-            mma_kstep(tmem, sa, sb, h == 0);
-            mma_kstep(tmem, sa + 256, sb + 256, false);
+            const uint32_t sa = base + uint32_t(s) * STAGE, sb = sa + NS * A_SLICE;
+            mma_kstep<NS, BN>(tset, sa, sb, h == 0);
             commit(smem_u32(&bar_empty[s]));
           }
-          if (ok) commit(smem_u32(&bar_accf));
+          if (ok) commit(smem_u32(&bar_accf[set]));
         }
       }
       // every MMA has completed before TMEM is freed
       commit(smem_u32(&bar_done));
-      mbar_drain(smem_u32(&bar_done), 0);
+      mbar_drain(smem_u32(&bar_done), 0, wait_ns);
     }
     __syncwarp();
   } else {
     // ---------------- flush warps ----------------
     const int quarter = warp & 3;                    // TMEM lanes 32 quarter .. + 31
-    const int half = (warp - 2) >> 2;                // columns 32 half .. + 31
+    const int half = (warp - 2) >> 2;                // columns CT half .. + CT - 1
     const int rloc = 32 * quarter + lane;            // tile row of this thread
-    const uint32_t trow = tmem + (uint32_t(32 * quarter) << 16);
+    const uint32_t trow = tmem + (uint32_t(32 * quarter) << 16) + uint32_t(CT * half);
     int c = 0;
     bool ok = true;
     for (int it = 0; it < nitem_cta && ok; ++it) {
       const int item = item0 + it * item_step;
       const int64_t m0 = int64_t(item / tiles_n) * BM, n0 = int64_t(item % tiles_n) * BN;
-      dd master[32];
+      const int* exa = A.ex + m0 + rloc;
+      const int* exb = B.ex + n0 + CT * half + (lane % CT);  // lane j < CT holds column j's exponents
+      // reference exponents: 7 (double-float), or the largest chunk
+      // exponents of this tile's K range (float64)
+      int ra = 7, rb = 7;
+      if constexpr (NS == 7) {
+        ra = ZERO_EXP;
+        rb = ZERO_EXP;
+        for (int ch = 0; ch < nchunk; ++ch) {
+          ra = max(ra, exa[int64_t(kc0 + ch) * A.Mp]);
+          rb = max(rb, exb[int64_t(kc0 + ch) * B.Mp]);
+        }
+      }
+      AccT<NS> master[CT];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) master[j] = {0.f, 0.f};
+      for (int j = 0; j < CT; ++j) acc_zero(master[j]);
       for (int ch = 0; ch < nchunk; ++ch, ++c) {
-        const int64_t kc = (kb0 + ch * KBC) / KBC;
-        const float fa = pow2(A.ex[kc * A.Mp + m0 + rloc] - 7);
-        const float fbl = pow2(B.ex[kc * B.Mp + n0 + 32 * half + lane] - 7);
-        if (!(ok = mbar_wait(smem_u32(&bar_accf), uint32_t(c & 1), abort))) break;
+        const int set = c % NSETS, use = c / NSETS;
+        const int64_t kc = kc0 + ch;
+        const float fa = pow2(exa[kc * A.Mp] - ra);
+        const float fbl = pow2(exb[kc * B.Mp] - rb);
+        if (!(ok = mbar_wait(smem_u32(&bar_accf[set]), uint32_t(use & 1), abort, wait_ns))) break;
         fence_after();
 #pragma unroll
-        for (int sub = 0; sub < 2; ++sub) {
-          float v[6][16];
-          tmem_ld_levels(trow + uint32_t(32 * half + 16 * sub), v);
-          if (sub == 1) {  // TMEM read: the issuer may start the next chunk
+        for (int sub = 0; sub < CT / 16; ++sub) {
+          float v[NS][16];
+          tmem_ld_levels<NS, BN>(trow + uint32_t(set) * C::SET_COLS + uint32_t(16 * sub), v);
+          if (sub == CT / 16 - 1) {  // levels read: the issuer may refill this set
             fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&bar_acce));
+            if (lane == 0) mbar_arrive(smem_u32(&bar_acce[set]));
           }
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            float hi, lo;
-            combine_levels(v[0][j], v[1][j], v[2][j], v[3][j], v[4][j], v[5][j], hi, lo);
+            float a[NS];
+#pragma unroll
+            for (int l = 0; l < NS; ++l) a[l] = v[l][j];
             const float fb = __shfl_sync(0xffffffffu, fbl, 16 * sub + j);
-            add_scaled(master[16 * sub + j], hi, lo, fa * fb);
+            flush_one(master[16 * sub + j], a, fa * fb);
           }
         }
       }
       if (!ok) break;
       const int64_t r = m0 + rloc;
-      const int64_t c0 = n0 + 32 * half;
-      if (r < A.M) {
-        // update: when the thread's 32 columns are one contiguous run of one
-        // segment of Y, 16-byte aligned, write them as 16 two-element vectors
+      const int64_t c0 = n0 + CT * half;
+      const bool live = r < A.M;
+      if (MODE == 0) {
+#pragma unroll
+        for (int j = 0; j < CT; ++j) {
+          double v = acc_value(master[j]);
+          // float64 operands: times 2^(r_a + r_b(column) - 14); every lane
+          // takes part in the shuffle
+          if constexpr (NS == 7) v = ldexp(v, ra - 14 + __shfl_sync(0xffffffffu, rb, j));
+          const int64_t col = c0 + j;
+          if (live && col < B.M) go.part[int64_t(blockIdx.z) * A.M * B.M + r * B.M + col] = v;
+        }
+      } else {
+        // when the thread's CT columns are one contiguous run of one segment
+        // of Y, 16-byte aligned, write them as 16-byte vectors
         bool fast = false;
-        dd* yrow = nullptr;
-        if (MODE == 1 && c0 + 32 <= B.M) {
+        T* yrow = nullptr;
+        if (live && c0 + CT <= B.M) {
           int sg = 0;
           while (sg + 1 < uo.Y.nseg && c0 >= uo.Y.start[sg + 1]) ++sg;
           yrow = uo.Y.ptr[sg] + r * uo.Y.ld[sg] + (c0 - uo.Y.start[sg]);
-          fast = c0 + 32 <= uo.Y.start[sg + 1] && (reinterpret_cast<uintptr_t>(yrow) & 15) == 0;
+          fast = c0 + CT <= uo.Y.start[sg + 1] && (reinterpret_cast<uintptr_t>(yrow) & 15) == 0;
         }
-        if (fast) {
-          float4* y4 = reinterpret_cast<float4*>(yrow);
+        if constexpr (NS == 6) {
+          if (live) {
+            const float bh = float(uo.beta);
+            const dd beta{bh, float(uo.beta - double(bh))};
+            if (fast) {
+              float4* y4 = reinterpret_cast<float4*>(yrow);
 #pragma unroll
-          for (int j = 0; j < 32; j += 2) {
-            dd v0 = master[j], v1 = master[j + 1];
-            if (uo.has_beta) {
-              const float4 old = y4[j / 2];
-              dd_mac(v0, dd{old.x, old.y}, uo.beta);
-              dd_mac(v1, dd{old.z, old.w}, uo.beta);
+              for (int j = 0; j < CT; j += 2) {
+                dd v0 = master[j], v1 = master[j + 1];
+                if (uo.has_beta) {
+                  const float4 old = y4[j / 2];
+                  dd_mac(v0, dd{old.x, old.y}, beta);
+                  dd_mac(v1, dd{old.z, old.w}, beta);
+                }
+                dd_renorm(v0);
+                dd_renorm(v1);
+                y4[j / 2] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < CT; ++j) {
+                const int64_t col = c0 + j;
+                if (col < B.M) {
+                  T* yp = uo.Y.at(r, int(col));
+                  dd v = master[j];
+                  if (uo.has_beta) dd_mac(v, *yp, beta);
+                  dd_renorm(v);
+                  *yp = v;
+                }
+              }
             }
-            dd_renorm(v0);
-            dd_renorm(v1);
-            y4[j / 2] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
           }
         } else {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int64_t col = c0 + j;
-            if (col < B.M) {
-              if (MODE == 0) {
-                go.part[int64_t(blockIdx.z) * A.M * B.M + r * B.M + col] =
-                    double(master[j].hi) + double(master[j].lo);
-              } else {
-                dd* yp = uo.Y.at(r, int(col));
-                dd v = master[j];
-                if (uo.has_beta) dd_mac(v, *yp, uo.beta);
-                dd_renorm(v);
-                *yp = v;
+          for (int j = 0; j < CT; j += 2) {
+            // every lane takes part in the shuffles of the column exponents
+            const int s0 = ra - 14 + __shfl_sync(0xffffffffu, rb, j);
+            const int s1 = ra - 14 + __shfl_sync(0xffffffffu, rb, j + 1);
+            double v0 = ldexp(acc_value(master[j]), s0);
+            double v1 = ldexp(acc_value(master[j + 1]), s1);
+            if (fast) {
+              double2* y2 = reinterpret_cast<double2*>(yrow) + j / 2;
+              if (uo.has_beta) {
+                const double2 old = *y2;
+                v0 = fma(uo.beta, old.x, v0);
+                v1 = fma(uo.beta, old.y, v1);
+              }
+              *y2 = make_double2(v0, v1);
+            } else if (live) {
+              if (c0 + j < B.M) {
+                T* yp = uo.Y.at(r, int(c0 + j));
+                *yp = uo.has_beta ? fma(uo.beta, *yp, v0) : v0;
+              }
+              if (c0 + j + 1 < B.M) {
+                T* yp = uo.Y.at(r, int(c0 + j + 1));
+                *yp = uo.has_beta ? fma(uo.beta, *yp, v1) : v1;
               }
             }
           }
@@ -396,59 +533,80 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
-template <int MODE>
+template <int MODE, int NS, int BN, typename T>
 cudaError_t set_smem5() {
   static thread_local int done_dev = -1;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (done_dev != dev) {
-    e = cudaFuncSetAttribute(tc5_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMEM));
+    e = cudaFuncSetAttribute(tc5_kernel<MODE, NS, BN, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(Cfg<NS, BN>::SMEM));
     if (e != cudaSuccess) return e;
     done_dev = dev;
   }
   return cudaSuccess;
 }
 
-int live_tiles(int a, int b, bool sym) {
-  const int ta = (a + BM - 1) / BM, tb = (b + BN - 1) / BN;
+int live_tiles(int a, int b, bool sym, int bn) {
+  const int ta = (a + BM - 1) / BM, tb = (b + bn - 1) / bn;
   if (!sym) return ta * tb;
   int t = 0;
   for (int i = 0; i < ta; ++i)
     for (int j = 0; j < tb; ++j)
-      if (!(j * BN + BN - 1 < i * BM)) ++t;
+      if (!(j * bn + bn - 1 < i * BM)) ++t;
   return t;
+}
+
+template <int NS>
+using ElemT = std::conditional_t<NS == 6, dd, double>;
+
+// tile width of each format's product (see the head of this file)
+template <int NS> constexpr int bn_of() { return NS == 6 ? 64 : 32; }
+
+template <int NS>
+cudaError_t gram_launch(int64_t n, int a, int b, const void* slu, const void* slv, bool sym, double* scratch, int ns,
+                        cudaStream_t st, const int* gate, int withhold, uint64_t wait_ns) {
+  using T = ElemT<NS>;
+  constexpr int BN = bn_of<NS>();
+  cudaError_t e = set_smem5<0, NS, BN, T>();
+  if (e != cudaSuccess) return e;
+  const int64_t nkb = nkb_of(n);
+  const int64_t kb_per = cdiv(cdiv(n, CH), ns) * KBC;
+  const int tm = (a + BM - 1) / BM, tn = (b + BN - 1) / BN;
+  GramOut go{scratch, sym};
+  UpdOut<T> uo{};
+  dim3 grid(tn, tm, ns);
+  tc5_kernel<0, NS, BN, T><<<grid, THREADS, Cfg<NS, BN>::SMEM, st>>>(opnd(slu, NS, n, a), opnd(slv, NS, n, b),
+                                                                      int(nkb), int(kb_per), tn, tm * tn, go, uo,
+                                                                      gate, withhold, wait_ns);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
-int tc5_gram_nsplit(int64_t n, int a, int b, bool sym) {
-  int ns = num_sms() / std::max(1, live_tiles(a, b, sym));  // one CTA per SM, one wave
+int tc5_gram_nsplit(int ns_slices, int64_t n, int a, int b, bool sym) {
+  const int bn = ns_slices == 6 ? bn_of<6>() : bn_of<7>();
+  int ns = num_sms() / std::max(1, live_tiles(a, b, sym, bn));  // one CTA per SM, one wave
   const int64_t nch = cdiv(n, CH);
   if (ns > nch) ns = int(nch);
   if (ns < 1) ns = 1;
   return ns;
 }
 
+template <int NS>
 cudaError_t tc5_gram(int64_t n, int a, int b, const void* slu, const void* slv, bool sym, double* scratch, int ns,
                      cudaStream_t st, const int* gate) {
-  cudaError_t e = set_smem5<0>();
-  if (e != cudaSuccess) return e;
-  const int64_t nkb = nkb_of(n);
-  const int64_t kb_per = cdiv(cdiv(n, CH), ns) * KBC;
-  const int tm = (a + BM - 1) / BM, tn = (b + BN - 1) / BN;
-  GramOut go{scratch, sym};
-  UpdOut uo{};
-  dim3 grid(tn, tm, ns);
-  tc5_kernel<0><<<grid, THREADS, SMEM, st>>>(opnd(slu, n, a), opnd(slv, n, b), int(nkb), int(kb_per), tn, tm * tn,
-                                             go, uo, gate);
-  count_launches(1);
-  return cudaGetLastError();
+  return gram_launch<NS>(n, a, b, slu, slv, sym, scratch, ns, st, gate, -1, WAIT_NS);
 }
 
-cudaError_t tc5_update(int64_t n, int s, int c, const void* slu, const void* slc, const Blk<dd>& Y, double beta,
+template <int NS, typename T>
+cudaError_t tc5_update(int64_t n, int s, int c, const void* slu, const void* slc, const Blk<T>& Y, double beta,
                        cudaStream_t st, const int* gate) {
-  cudaError_t e = set_smem5<1>();
+  static_assert(std::is_same<T, ElemT<NS>>::value, "slice count and element type disagree");
+  constexpr int BN = bn_of<NS>();
+  cudaError_t e = set_smem5<1, NS, BN, T>();
   if (e != cudaSuccess) return e;
   const int64_t nkb = nkb_of(s);
   const int64_t tm = cdiv(n, BM);
@@ -457,15 +615,34 @@ cudaError_t tc5_update(int64_t n, int s, int c, const void* slu, const void* slc
   int64_t grid = num_sms();
   if (grid > items) grid = items;
   GramOut go{};
-  UpdOut uo;
+  UpdOut<T> uo;
   uo.Y = Y;
-  const float bh = float(beta);
-  uo.beta = dd{bh, float(beta - double(bh))};
+  uo.beta = beta;
   uo.has_beta = beta != 0.0;
-  tc5_kernel<1><<<(unsigned)grid, THREADS, SMEM, st>>>(opnd(slu, s, n), opnd(slc, s, c), int(nkb), int(nkb), tn,
-                                                       int(items), go, uo, gate);
+  tc5_kernel<1, NS, BN, T><<<(unsigned)grid, THREADS, Cfg<NS, BN>::SMEM, st>>>(
+      opnd(slu, NS, s, n), opnd(slc, NS, s, c), int(nkb), int(nkb), tn, int(items), go, uo, gate, -1, WAIT_NS);
   count_launches(1);
   return cudaGetLastError();
+}
+
+template cudaError_t tc5_gram<6>(int64_t, int, int, const void*, const void*, bool, double*, int, cudaStream_t,
+                                 const int*);
+template cudaError_t tc5_gram<7>(int64_t, int, int, const void*, const void*, bool, double*, int, cudaStream_t,
+                                 const int*);
+template cudaError_t tc5_update<6, dd>(int64_t, int, int, const void*, const void*, const Blk<dd>&, double,
+                                       cudaStream_t, const int*);
+template cudaError_t tc5_update<7, double>(int64_t, int, int, const void*, const void*, const Blk<double>&, double,
+                                           cudaStream_t, const int*);
+
+// Self-test of the bounded waits: one Gram product (K = n, a x b, slices
+// already made) whose producer withholds the copies of its first stage, so
+// the MMA issuer's wait for that stage runs out after wait_ns and the kernel
+// ends early with the device error word set.
+cudaError_t tc5_wait_selftest(int ns_slices, int64_t n, int a, int b, const void* slu, const void* slv,
+                              double* scratch, uint64_t wait_ns, cudaStream_t st) {
+  const int ns = tc5_gram_nsplit(ns_slices, n, a, b, false);
+  if (ns_slices == 6) return gram_launch<6>(n, a, b, slu, slv, false, scratch, ns, st, nullptr, 0, wait_ns);
+  return gram_launch<7>(n, a, b, slu, slv, false, scratch, ns, st, nullptr, 0, wait_ns);
 }
 
 // status of the bounded waits since the last call (0: none expired); resets it

@@ -160,6 +160,7 @@ struct eig_handle {
   void* tcQc = nullptr;
   void* tcQr = nullptr;
   int qcmax = 0;
+  int tcns = 0;  // slices per value (6 double-float, 7 float64)
   // small float64 work
   int smax = 0;
   double *Gp = nullptr, *Rinv = nullptr, *cholw = nullptr, *Z = nullptr, *lamd = nullptr, *CP = nullptr;
@@ -287,13 +288,16 @@ bool same_blk(const Blk<T>& a, const Blk<T>& b) {
   return true;
 }
 
-// the double-float Gram products and updates run on the tensor cores (slice
-// buffers)
-bool uses_gram_tc(const eig_options& o) { return o.gram_tc != 0 && o.form != EIG_FORM_F64; }
+// the Gram products and updates of the float64 and double-float blocks run
+// on the tensor cores (slice buffers); slices per value of the form's blocks
+bool uses_gram_tc(const eig_options& o) { return o.gram_tc != 0; }
+int tc_slices(int form) { return form == EIG_FORM_F64 ? tc::NS_F64 : tc::NS_DF; }
 
 // one slice buffer: a Gram operand (K = n, up to w columns) or an update's
 // left operand (K = up to w columns, n rows)
-size_t tc_operand_bytes(int64_t n, int w) { return std::max(tc_slice_bytes(n, w), tc_slice_bytes(w, n)); }
+size_t tc_operand_bytes(int ns, int64_t n, int w) {
+  return std::max(tc_slice_bytes(ns, n, w), tc_slice_bytes(ns, w, n));
+}
 
 template <Arith A> struct FormData;
 template <> struct FormData<Arith::DF64> {
@@ -346,15 +350,15 @@ struct Ops {
     const double nn = double(h->n), a = U.width, b = V.width;
     const bool same = U.ptr[0] == V.ptr[0];
     Prof p(h, EIG_K_GRAM, sym ? nn * a * (b + 1) : 2.0 * nn * a * b, E * nn * (same ? a : a + b));
-    if constexpr (AG == Arith::DF64) {
+    if constexpr (AG == Arith::DF64 || AG == Arith::F64) {
       if (h->tcU) {  // tensor-core product on exact bf16 slices
         const bool one = same_blk(U, V);
         const bool ucached = q_cached(U);
         void* su = ucached ? h->tcQc : h->tcU;
         if (!ucached) CK(tc_slice_cols(h->n, U, h->tcU, st(), gate));
         if (!one) CK(tc_slice_cols(h->n, V, h->tcV, st(), gate));
-        CK(gram_tc_product(h->n, U.width, V.width, su, one ? su : h->tcV, sym, h->Gp, V.width, h->gscr, st(),
-                           gate));
+        CK(gram_tc_product(h->tcns, h->n, U.width, V.width, su, one ? su : h->tcV, sym, h->Gp, V.width, h->gscr,
+                           st(), gate));
         return EIG_OK;
       }
     }
@@ -364,11 +368,11 @@ struct Ops {
   // Y = U (scale * C) + beta Y with C float64 (s x c, ldc)
   int upd(const Blk<T>& U, const double* C, int64_t ldc, int c, double scale, const Blk<T>& Y, double beta,
           const int* gate = nullptr) {
-    if constexpr (AU == Arith::DF64) {
+    if constexpr (AU == Arith::DF64 || AU == Arith::F64) {
       if (h->tcU && U.width > 0 && c > 0) {  // tensor-core product on exact bf16 slices
         {
           Prof p(h, EIG_K_OTHER, 0.0, 0.0);
-          CK(tc_slice_coef(U.width, c, C, ldc, scale, h->tcC, st(), gate));
+          CK(tc_slice_coef(h->tcns, U.width, c, C, ldc, scale, h->tcC, st(), gate));
         }
         const double nn = double(h->n);
         Prof p(h, EIG_K_UPDATE, 2.0 * nn * U.width * c, E * nn * (U.width + c * (beta != 0.0 ? 2.0 : 1.0)));
@@ -489,7 +493,7 @@ struct Ops {
       bool& f;
       ~Clear() { f = false; }
     } clear{qcache};
-    if constexpr (AU == Arith::DF64 && AG == Arith::DF64) {
+    if constexpr (AU == AG && (AU == Arith::DF64 || AU == Arith::F64)) {
       if (h->tcQc && Q.width > 0 && Q.width <= h->qcmax) {
         const double nn = double(h->n);
         {
@@ -1341,9 +1345,11 @@ size_t footprint_bytes(int64_t n, int64_t nnz, int nev, int k_max, int nes, int 
   b += 8 * (size_t(2) * num_sms() * 4 * 64 * 64 + smax * smax + 4096);
   b += 8 * residual_scratch_elems(n, k_max);
   b += syev_work_bytes(int(smax)) + hl_work_bytes(int(smax), k_max, 0) + 8 * smax * smax;
-  if (gram_tc && form != EIG_FORM_F64)
-    b += 2 * tc_operand_bytes(n, int(smax)) + tc_slice_bytes(int64_t(smax), 2 * k_max + 1) +
-         2 * tc_operand_bytes(n, 2 * k_max + 1);
+  if (gram_tc) {
+    const int ns = tc_slices(form);
+    b += 2 * tc_operand_bytes(ns, n, int(smax)) + tc_slice_bytes(ns, int64_t(smax), 2 * k_max + 1) +
+         2 * tc_operand_bytes(ns, n, 2 * k_max + 1);
+  }
   return b + b / 16 + (size_t(32) << 20);        // allocator rounding and slack
 }
 
@@ -1526,12 +1532,13 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
   // S_drop and Wt are swapped when the mixed form promotes; same size
   AL(h->Sd, sizeof(double) * size_t(n) * std::max(h->wtw, nev));
   if (uses_gram_tc(h->opt)) {
-    AL(h->tcU, tc_operand_bytes(n, 3 * k_max + 1));
-    AL(h->tcV, tc_operand_bytes(n, 3 * k_max + 1));
-    AL(h->tcC, tc_slice_bytes(3 * k_max + 1, 2 * k_max + 1));
+    const int ns = h->tcns = tc_slices(opt->form);
+    AL(h->tcU, tc_operand_bytes(ns, n, 3 * k_max + 1));
+    AL(h->tcV, tc_operand_bytes(ns, n, 3 * k_max + 1));
+    AL(h->tcC, tc_slice_bytes(ns, 3 * k_max + 1, 2 * k_max + 1));
     h->qcmax = 2 * k_max + 1;  // [u0, X, P]
-    AL(h->tcQc, tc_operand_bytes(n, h->qcmax));
-    AL(h->tcQr, tc_operand_bytes(n, h->qcmax));
+    AL(h->tcQc, tc_operand_bytes(ns, n, h->qcmax));
+    AL(h->tcQr, tc_operand_bytes(ns, n, h->qcmax));
   }
   // small
   const int smax = 3 * k_max + 1;

@@ -19,7 +19,6 @@ from oracle import blocks as B
 from oracle.chebsi import chebsi as o_chebsi
 from oracle.lobpcg import lobpcg as o_lobpcg
 from paper_2409_05572_gb300 import workloads as W
-from tc_bounds import gram_bound as tc_bound, row_chunk_max
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -156,101 +155,6 @@ def test_gram_deterministic_and_empty():
 
 
 # ---------------------------------------------------------------------------
-# a4 / a5 / a8: Gram on the tensor cores (EIG_ARITH_DF64_TC)
-# Error model of the exact slicing: per row at most about 28 * 2^-48 of
-# M_u M_v (M = the column's max |x| over the row's 128-row chunk) from the
-# six-slice representation and the dropped levels, plus the double-float
-# accumulation (the DF64 tolerance above).  The test allows 32 * 2^-48.
-# ---------------------------------------------------------------------------
-def tc_gram(U, V, sym, ldu_pad=0, ldv_pad=0):
-    n, a = U.shape
-    b = V.shape[1]
-    Up = np.zeros((n, a + ldu_pad))
-    Up[:, :a] = U
-    Ud = L.to_df64(dev(Up))
-    if V is U and ldv_pad == ldu_pad:
-        Vd = Ud
-    else:
-        Vp = np.zeros((n, b + ldv_pad))
-        Vp[:, :b] = V
-        Vd = L.to_df64(dev(Vp))
-    G = torch.full((a, b + 2), 9.0, dtype=torch.float64, device="cuda")
-    L.eig_gram(n, a, b, Ud, a + ldu_pad, Vd, b + ldv_pad, L.ARITH_DF64_TC, sym, G, b + 2)
-    assert L.device_status() == 0   # no bounded wait of the product kernel ran out
-    assert torch.all(G[:, b:] == 9.0)
-    return G[:, :b].cpu().numpy()
-
-
-@pytest.mark.parametrize("n,a,b,sym", [(5017, 7, 5, False), (5017, 64, 64, True), (5017, 130, 70, False),
-                                       (5017, 150, 150, True), (1, 3, 2, False), (127, 1, 1, True),
-                                       (129, 65, 129, False), (3000, 385, 385, True)])
-def test_gram_tc_parity(n, a, b, sym):
-    rng = np.random.default_rng(n + a * 7 + b)
-    U = rng.standard_normal((n, a))
-    V = U if sym else rng.standard_normal((n, b))
-    got = tc_gram(U, V, sym, ldu_pad=3 * (not sym))
-    ref = B.gram(U, V)
-    err = np.abs(got - ref)
-    assert np.all(err <= tc_bound(U, V)), np.max(err / tc_bound(U, V))
-    if sym:
-        assert np.array_equal(got, got.T)
-
-
-def test_gram_tc_wide_range_and_structure():
-    """Columns scaled by 2^-60 .. 2^60, localized columns (exponential decay
-    over thousands of rows, like Anderson eigenvectors), a column with one
-    nonzero, a zero column, entries at powers of two with lo of both signs,
-    values just below a power of two, and a sign-alternating column."""
-    n, a = 4100, 40
-    rng = np.random.default_rng(11)
-    U = rng.standard_normal((n, a))
-    r = np.arange(n)
-    for j in range(8):
-        U[:, j] = rng.standard_normal(n) * np.exp(-np.abs(r - 500 * j) / 60.0)
-    U[:, 8] = 0.0
-    U[:, 9] = 0.0
-    U[1234, 9] = -3.75
-    U[:, 10] = 2.0 ** rng.integers(-20, 20, n) * (1 + 2.0 ** -30 * rng.choice([-1, 1], n))
-    U[:, 11] = np.nextafter(2.0 ** rng.integers(-5, 5, n), 0) * rng.choice([-1.0, 1.0], n)
-    U[:, 12] = (-1.0) ** r * (1 + 1e-9 * r)
-    for j in range(13, a):
-        U[:, j] *= 2.0 ** rng.integers(-60, 60)
-    V = rng.standard_normal((n, 24)) * 2.0 ** rng.integers(-30, 30, 24)
-    for sym, (X, Y) in ((True, (U, U)), (False, (U, V))):
-        got = tc_gram(X, Y, sym)
-        ref = B.gram(X, Y)
-        err = np.abs(got - ref)
-        bound = tc_bound(X, Y)
-        assert np.all(err <= bound), np.max(err / np.maximum(bound, 1e-300))
-    assert np.all(got[8] == 0.0)
-
-
-def test_gram_tc_tiny_chunks_are_zero_and_deterministic():
-    n, a = 3000, 20
-    rng = np.random.default_rng(5)
-    U = rng.standard_normal((n, a))
-    U[:, 3] = 1e-35 * rng.standard_normal(n)   # every chunk maximum below 2^-100
-    g1 = tc_gram(U, U, True)
-    g2 = tc_gram(U, U, True)
-    assert np.array_equal(g1, g2)
-    assert np.all(g1[3] == 0.0) and np.all(g1[:, 3] == 0.0)
-
-
-def test_gram_tc_matches_cuda_core_gram_in_solve_accuracy():
-    """Same C-ABI product through both DF64 arithmetics on orthonormal
-    columns (the CholeskyQR Gram of a converged block): both within 1e-13
-    of the identity's exact Gram."""
-    n, a = 20000, 96
-    Q, _ = np.linalg.qr(np.random.default_rng(9).standard_normal((n, a)))
-    Qd = L.to_df64(dev(Q))
-    for arith in (L.ARITH_DF64, L.ARITH_DF64_TC):
-        G = torch.empty(a, a, dtype=torch.float64, device="cuda")
-        L.eig_gram(n, a, a, Qd, a, Qd, a, arith, True, G, a)
-        ref = B.gram(Q, Q)
-        assert np.max(np.abs(G.cpu().numpy() - ref)) <= 1e-13
-
-
-# ---------------------------------------------------------------------------
 # a4 / a11: block update
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("arith", ["f64", "df64", "f32"])
@@ -271,53 +175,6 @@ def test_update_parity(arith, s, c, beta):
     scale = np.abs(Ur) @ np.abs(Cr) + abs(beta) * np.abs(Yr)
     tol = {"f64": 1e-13, "df64": 1e-12, "f32": 2e-6}[arith]
     assert np.all(np.abs(got - ref) <= tol * scale + 1e-300)
-
-
-@pytest.mark.parametrize("n,s,c,beta", [(5017, 7, 5, 0.0), (5017, 64, 64, 1.0), (5017, 130, 70, -0.37),
-                                        (3001, 385, 257, 0.0), (1, 3, 2, 2.5), (65, 1, 129, -1.0)])
-def test_update_tc_parity(n, s, c, beta):
-    """Y = U C + beta Y on the tensor cores (EIG_ARITH_DF64_TC): per output
-    at most about 28 * 2^-48 * sum over 128-column chunks k of
-    128 * max|U(row, k)| * max|C(k, col)|, plus double-float accumulation."""
-    rng = np.random.default_rng(n + s * 3 + c)
-    U = rng.standard_normal((n, s)) * 2.0 ** rng.integers(-20, 20, s)
-    Cm = rng.standard_normal((s, c))
-    Y0 = rng.standard_normal((n, c))
-    Ud = L.to_df64(dev(U))
-    Yd = L.to_df64(dev(Y0))
-    L.eig_block_update(n, s, c, Ud, s, dev(Cm), c, Yd, c, beta, L.ARITH_DF64_TC)
-    assert L.device_status() == 0
-    got = L.from_df64(Yd).cpu().numpy()
-    ref = U @ Cm + beta * Y0
-    Mu, cnt = row_chunk_max(U)
-    Mc, _ = row_chunk_max(Cm.T)
-    bound = RTOL["df64"] * (np.abs(U) @ np.abs(Cm) + abs(beta) * np.abs(Y0)) + \
-        32 * 2.0 ** -48 * ((Mu * cnt) @ Mc.T)
-    err = np.abs(got - ref)
-    assert np.all(err <= bound), np.max(err / bound)
-
-
-def test_update_tc_zero_width_and_padding():
-    """s = 0 gives beta Y; the leading dimensions larger than the widths are
-    neither read nor written."""
-    n, s, c = 300, 40, 20
-    rng = np.random.default_rng(4)
-    U = np.zeros((n, s + 5))
-    U[:, :s] = rng.standard_normal((n, s))
-    U[:, s:] = np.nan
-    Cm = np.zeros((s, c + 3))
-    Cm[:, :c] = rng.standard_normal((s, c))
-    Cm[:, c:] = np.nan
-    Y0 = rng.standard_normal((n, c + 2))
-    Yd = L.to_df64(dev(Y0))
-    L.eig_block_update(n, s, c, L.to_df64(dev(U)), s + 5, dev(Cm), c + 3, Yd, c + 2, 0.5, L.ARITH_DF64_TC)
-    got = L.from_df64(Yd).cpu().numpy()
-    ref = U[:, :s] @ Cm[:, :c] + 0.5 * Y0[:, :c]
-    assert np.all(np.abs(got[:, :c] - ref) <= 1e-12 * (np.abs(U[:, :s]) @ np.abs(Cm[:, :c]) + np.abs(Y0[:, :c])))
-    assert np.array_equal(got[:, c:], L.from_df64(L.to_df64(dev(Y0[:, c:].copy()))).cpu().numpy())
-    Yd = L.to_df64(dev(Y0))
-    L.eig_block_update(n, 0, c, L.to_df64(dev(U)), s + 5, dev(Cm), c + 3, Yd, c + 2, -2.0, L.ARITH_DF64_TC)
-    assert np.allclose(L.from_df64(Yd).cpu().numpy()[:, :c], -2.0 * Y0[:, :c], rtol=1e-14)
 
 
 # ---------------------------------------------------------------------------
@@ -488,11 +345,13 @@ def test_c1_lobpcg_parity(c1, form, strategy):
     s.close()
 
 
-def test_c1_lobpcg_cuda_core_gram(c1):
-    """The double-float form with its Gram products on the FP32 pipes
-    (gram_tc = 0) instead of the tensor cores."""
+@pytest.mark.parametrize("form", ["df64", "f64"])
+def test_c1_lobpcg_cuda_core_gram(c1, form):
+    """The double-float and float64 forms with their Gram products and
+    updates on the CUDA cores (gram_tc = 0: FP32-pipe double-float, native
+    FP64) instead of the tensor cores."""
     A, normA, X0, ex = c1
-    s = L.Solver(A, nev=10, k_max=20, strategy="fix", X0=X0, normA=normA, tol=1e-10, gram_tc=0)
+    s = L.Solver(A, nev=10, k_max=20, strategy="fix", X0=X0, normA=normA, tol=1e-10, gram_tc=0, form=form)
     out = s.solve()
     ref = o_lobpcg(A, X0, 10, 15, "fix", tol=1e-10, normA=normA)
     assert out["status"] == 0
@@ -507,18 +366,25 @@ def test_c1_lobpcg_mixed(c1):
     A, normA, X0, ex = c1
     s = L.Solver(A, nev=10, k_max=20, strategy="fix", X0=X0, normA=normA, tol=1e-10, form="mixed")
     out = s.solve()
-    assert out["status"] == 0
+    ref = o_lobpcg(A, X0, 10, 15, "fix", tol=1e-10, normA=normA)
+    assert out["status"] == 0 and ref.converged
     assert np.max(np.abs(out["lam"] - ex[:10]) / ex[:10]) <= 1e-8
+    assert np.max(np.abs(out["lam"] - ref.lam) / ref.lam) <= 1e-8
     assert out["resid"].max() <= 1e-8
+    V = s.V().cpu().numpy()
+    Qv, _ = np.linalg.qr(V)
+    Qo, _ = np.linalg.qr(ref.X)
+    assert np.linalg.norm(Qv @ Qv.T - Qo @ Qo.T, 2) < 1e-6
     s.close()
 
 
-def test_lobpcg_3d_several_tiles_closed_form():
+@pytest.mark.parametrize("form", ["df64", "f64"])
+def test_lobpcg_3d_several_tiles_closed_form(form):
     A = W.laplacian_3d(20, 22, 24)   # n = 10560
     ex = dirichlet_spectrum((20, 22, 24))
     normA = W.dirichlet_norm((20, 22, 24))
     X0 = W.gaussian_block(A.n, 40, 1)
-    s = L.Solver(A, nev=24, k_max=40, strategy="fix", X0=X0, normA=normA, tol=1e-10)
+    s = L.Solver(A, nev=24, k_max=40, strategy="fix", X0=X0, normA=normA, tol=1e-10, form=form)
     out = s.solve()
     assert out["status"] == 0
     assert np.max(np.abs(out["lam"] - ex[:24]) / ex[:24]) <= 1e-10
@@ -563,7 +429,7 @@ def test_lobpcg_graph_laplacian_jacobi_deflation():
     s.close()
 
 
-@pytest.mark.parametrize("form", ["df64", "mixed"])
+@pytest.mark.parametrize("form", ["df64", "f64", "mixed"])
 @pytest.mark.parametrize("strategy", ["none", "fix", "slopek"])
 def test_chebsi_anderson_parity(form, strategy):
     A = W.anderson_3d(12, seed=2)    # n = 1728, indefinite
@@ -577,7 +443,7 @@ def test_chebsi_anderson_parity(form, strategy):
     out = s.solve()
     ref = o_chebsi(A, X0, 16, 21, strategy, tol=1e-11, normA=normA, degree=10, upper=ub, max_iter=400, **kw)
     assert out["status"] == 0 and ref.converged
-    tol = 1e-10 if form == "df64" else 1e-8
+    tol = 1e-8 if form == "mixed" else 1e-10
     assert np.max(np.abs(out["lam"] - ev[:16]) / np.abs(ev[:16])) <= tol
     assert np.max(np.abs(out["lam"] - ref.lam) / np.abs(ref.lam)) <= tol
     assert out["resid"].max() <= 1e-8
@@ -596,7 +462,7 @@ def test_solver_reuse_gives_identical_results(c1):
 # ---------------------------------------------------------------------------
 # Algorithm 2 (SD) and the powered X_drop expansion of subspace iteration
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("form", ["df64", "mixed"])
+@pytest.mark.parametrize("form", ["df64", "f64", "mixed"])
 @pytest.mark.parametrize("strategy", ["none", "fix"])
 def test_sd_parity(form, strategy):
     from oracle.sd import sd
@@ -611,10 +477,10 @@ def test_sd_parity(form, strategy):
     out = s.solve()
     ref = sd(A, X0, 6, 8, strategy, tol=1e-10, normA=normA, max_iter=3000, **kw)
     assert out["status"] == 0 and ref.converged
-    tol = 1e-10 if form == "df64" else 1e-8
+    tol = 1e-8 if form == "mixed" else 1e-10
     assert np.max(np.abs(out["lam"] - ex[:6]) / ex[:6]) <= tol
     assert np.max(np.abs(out["lam"] - ref.lam) / ref.lam) <= tol
-    if form == "df64":
+    if form != "mixed":
         m = min(10, len(ref.history))
         assert np.allclose(out["history"][:m], ref.history[:m], rtol=1e-6)
     if strategy == "fix":
