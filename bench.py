@@ -318,6 +318,87 @@ def run_serving(args):
     return 0
 
 
+def run_kernel(args):
+    """--kernel: one hot-path kernel class through the C ABI on seeded random
+    device blocks (the operand values do not change the work), --warmup
+    launches then --steps launches between CUDA events on the current
+    stream; prints the average time and the algorithmic flops / bytes of
+    one call.  Used for the per-kernel ncu captures."""
+    import torch
+    from paper_2409_05572_gb300 import _lib as L
+    torch.cuda.set_device(0)
+    L.load()
+    ar = {"df64": L.ARITH_DF64, "df64_tc": L.ARITH_DF64_TC, "f64": L.ARITH_F64, "f64_tc": L.ARITH_F64_TC,
+          "f32": L.ARITH_F32, "c32": L.ARITH_C32}[args.arith]
+    g = torch.Generator(device="cuda").manual_seed(1234)
+
+    def block(rows, cols):
+        x = torch.randn(rows, cols, generator=g, device="cuda", dtype=torch.float64)
+        if args.arith in ("df64", "df64_tc"):
+            return L.to_df64(x)
+        if args.arith in ("f64", "f64_tc"):
+            return x
+        return x.float()
+
+    esz = 4 if args.arith in ("f32", "c32") else 8
+    n, a, b = args.n, args.a, args.b
+    if args.kernel == "gram":
+        U = block(n, a)
+        V = U if args.sym else block(n, b)
+        b = a if args.sym else b
+        G = torch.empty(a, b, dtype=torch.float64, device="cuda")
+        fn = lambda: L.eig_gram(n, a, b, U, a, V, b, ar, args.sym, G, b)  # noqa: E731
+        flops = n * a * (b + 1.0) if args.sym else 2.0 * n * a * b
+        nbytes = esz * n * (a if args.sym else a + b)
+    elif args.kernel == "update":
+        U = block(n, a)
+        Cm = torch.randn(a, b, generator=g, device="cuda", dtype=torch.float64)
+        Y = block(n, b)
+        fn = lambda: L.eig_block_update(n, a, b, U, a, Cm, b, Y, b, 0.0, ar)  # noqa: E731
+        flops = 2.0 * n * a * b
+        nbytes = esz * n * (a + b)
+    elif args.kernel == "spmm":
+        A = W.laplacian_3d(args.grid)
+        n = A.n
+        rp = torch.as_tensor(A.indptr, device="cuda")
+        ci = torch.as_tensor(A.indices, device="cuda")
+        vals = torch.as_tensor(A.data, device="cuda")
+        dt = {"df64": L.EIG_DF64, "f64": L.EIG_F64, "f32": L.EIG_F32}[args.arith]
+        if dt == L.EIG_DF64:
+            vals = L.to_df64(vals)
+        elif dt == L.EIG_F32:
+            vals = vals.float()
+        V = block(n, b)
+        Y = torch.empty_like(V)
+        fn = lambda: L.eig_spmm(n, rp, ci, vals, dt, b, V, b, Y, b)  # noqa: E731
+        flops = 2.0 * A.nnz * b
+        nbytes = (4 + esz) * A.nnz + 4 * (n + 1) + 2 * esz * n * b
+    else:
+        s = a
+        M = torch.randn(s, s, generator=g, device="cuda", dtype=torch.float64)
+        M = M + M.T
+        lam = torch.empty(s, dtype=torch.float64, device="cuda")
+        Z = torch.empty(s, s, dtype=torch.float64, device="cuda")
+        fn = lambda: L.eig_syev(s, M, s, lam, Z, s)  # noqa: E731
+        flops = (4.0 / 3.0 + 6.0) * s ** 3
+        nbytes = 0
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    status = L.device_status()
+    print(json.dumps({"kernel": args.kernel, "arith": args.arith, "n": n, "a": a, "b": b, "sym": args.sym,
+                      "ms": ms, "flops": flops, "bytes": nbytes, "tflops": flops / ms / 1e9,
+                      "gbs": nbytes / ms / 1e6 if nbytes else None, "device_status": status}), flush=True)
+    return 0 if status == 0 else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,7 +423,17 @@ def main():
                     help="iteration cap per solve (profiling runs use a small cap)")
     ap.add_argument("--ref-iters", type=int, default=315,
                     help="iterations per solve used to scale the reference arm's per-iteration time")
+    ap.add_argument("--kernel", choices=["gram", "update", "spmm", "syev"],
+                    help="time one kernel class instead of whole solves (--n, --a, --b, --sym, --arith, --grid)")
+    ap.add_argument("--n", type=int, default=2097152)
+    ap.add_argument("--a", type=int, default=384)
+    ap.add_argument("--b", type=int, default=384)
+    ap.add_argument("--sym", action="store_true")
+    ap.add_argument("--grid", type=int, default=128, help="--kernel spmm: 3D Laplacian grid side")
+    ap.add_argument("--arith", default="f64_tc", choices=["df64", "df64_tc", "f64", "f64_tc", "f32", "c32"])
     args = ap.parse_args()
+    if args.kernel:
+        return run_kernel(args)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -11,11 +11,14 @@
 // read the levels.
 //
 // One CTA per SM, 320 threads in three roles:
-//   warp 0, one thread   producer: per 16-index K block, NS + NS bulk copies
-//                        (cp.async.bulk, the TMA engine) of the A tile
-//                        (128 rows, 4 KB per slice) and the B tile (BN rows)
-//                        into a ring of stages; each stage completes an
-//                        mbarrier by transaction count.
+//   warp 0, one thread   producer: per 16-index K block, two tensor copies
+//                        (cp.async.bulk.tensor, the TMA engine; one 4-D box
+//                        of all NS slices each) of the A tile (128 rows, 4 KB
+//                        per slice) and the B tile (BN rows) into a ring of
+//                        stages; each stage completes an mbarrier by
+//                        transaction count.  (One copy per slice was measured
+//                        to cap the copy rate at about 55 GB/s per SM: the
+//                        copy engine spends a fixed time per request.)
 //   warp 1, one thread   MMA issuer: per K block, all slice pairs (i, j) with
 //                        i + j < NS as tcgen05.mma (M = 128, N = BN .. 256,
 //                        K = 16, bf16 in, fp32 out) into the TMEM accumulator
@@ -58,7 +61,10 @@
 // roles leave their loops, waits (bounded) for its own copies and MMAs and
 // frees TMEM before returning.  The self-test entry point withholds the
 // copies of one stage so that a wait runs out on purpose.
+#include <cuda.h>
+
 #include <cstdint>
+#include <mutex>
 #include <type_traits>
 
 #include "blocks.cuh"
@@ -148,10 +154,17 @@ __device__ __noinline__ void mbar_drain(uint32_t bar, uint32_t parity, uint64_t 
     }
 }
 
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
+// One tensor (TMA) copy of a box of the slice buffer described by tmap:
+// coordinates (0, first 8-row group, K block, first slice); the box is all
+// NS slices of a 16-index K block of BM (A) or BN (B) operand rows, landing
+// in shared memory as [slice][8-row group][8 x 16 core-matrix pair], i.e.
+// slice q of the tile at q * (rows * 32) bytes.
+__device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap* tmap, int rowgroup, int kb, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(0), "r"(rowgroup), "r"(kb), "r"(0), "r"(bar)
+      : "memory");
 }
 
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -259,7 +272,9 @@ using AccT = std::conditional_t<NS == 6, dd, tf>;
 // withhold >= 0 (self-test only): the producer issues no copies for stage
 // position withhold, so the issuer's wait for it runs out after wait_ns.
 template <int MODE, int NS, int BN, typename T>
-__global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb, int kb_per, int tiles_n,
+__global__ void __launch_bounds__(THREADS, 1) tc5_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                         const __grid_constant__ CUtensorMap tmB, Opnd A, Opnd B,
+                                                         int nkb, int kb_per, int tiles_n,
                                                          int nitems, GramOut go, UpdOut<T> uo, const int* gate,
                                                          int withhold, uint64_t wait_ns) {
   using C = Cfg<NS, BN>;
@@ -342,13 +357,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(Opnd A, Opnd B, int nkb
           if (p == withhold) continue;  // self-test: this stage never fills
           const uint32_t fb = smem_u32(&bar_full[s]);
           mbar_expect_tx(fb, STAGE);
-          const int64_t kb = kb0 + kbi;
+          const int kb = kb0 + kbi;
           const uint32_t sa = base + uint32_t(s) * STAGE, sb = sa + NS * A_SLICE;
-#pragma unroll 1
-          for (int q = 0; q < NS; ++q) {
-            bulk_g2s(sa + q * A_SLICE, A.sl + (int64_t(q) * nkb + kb) * A.Mp * KB + m0 * KB, A_SLICE, fb);
-            bulk_g2s(sb + q * C::B_SLICE, B.sl + (int64_t(q) * nkb + kb) * B.Mp * KB + n0 * KB, C::B_SLICE, fb);
-          }
+          tma_box(sa, &tmA, int(m0 / 8), kb, fb);
+          tma_box(sb, &tmB, int(n0 / 8), kb, fb);
         }
       }
       // the last stages' copies have landed before the CTA may exit
@@ -561,6 +573,44 @@ int live_tiles(int a, int b, bool sym, int bn) {
 template <int NS>
 using ElemT = std::conditional_t<NS == 6, dd, double>;
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  });
+  return fn;
+}
+
+// The slice buffer of an operand (ns slices, contraction length K, M rows;
+// layout in tc.cuh) as a 4-D bf16 tensor, innermost first: the 128 values of
+// one 8-row group of a K block (256 contiguous bytes), the Mp / 8 row groups
+// (256 bytes apart), the K blocks (Mp * 32 bytes apart) and the slices;
+// boxes of box_rows operand rows, one K block and all slices.
+cudaError_t slice_tmap(CUtensorMap* m, const void* buf, int ns, int64_t K, int64_t M, int box_rows) {
+  EncodeFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const Layout l = layout(buf, ns, K, M);
+  const cuuint64_t dims[4] = {128, cuuint64_t(l.Mp / 8), cuuint64_t(l.nkb), cuuint64_t(ns)};
+  const cuuint64_t strides[3] = {256, cuuint64_t(l.Mp) * 32, cuuint64_t(l.nkb) * cuuint64_t(l.Mp) * 32};
+  const cuuint32_t box[4] = {128, cuuint32_t(box_rows / 8), 1, cuuint32_t(ns)};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(buf), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // tile width of each format's product (see the head of this file)
 template <int NS> constexpr int bn_of() { return NS == 6 ? 64 : 32; }
 
@@ -576,10 +626,13 @@ cudaError_t gram_launch(int64_t n, int a, int b, const void* slu, const void* sl
   const int tm = (a + BM - 1) / BM, tn = (b + BN - 1) / BN;
   GramOut go{scratch, sym};
   UpdOut<T> uo{};
+  CUtensorMap tma, tmb;
+  if ((e = slice_tmap(&tma, slu, NS, n, a, BM)) != cudaSuccess) return e;
+  if ((e = slice_tmap(&tmb, slv, NS, n, b, BN)) != cudaSuccess) return e;
   dim3 grid(tn, tm, ns);
-  tc5_kernel<0, NS, BN, T><<<grid, THREADS, Cfg<NS, BN>::SMEM, st>>>(opnd(slu, NS, n, a), opnd(slv, NS, n, b),
-                                                                      int(nkb), int(kb_per), tn, tm * tn, go, uo,
-                                                                      gate, withhold, wait_ns);
+  tc5_kernel<0, NS, BN, T><<<grid, THREADS, Cfg<NS, BN>::SMEM, st>>>(tma, tmb, opnd(slu, NS, n, a),
+                                                                      opnd(slv, NS, n, b), int(nkb), int(kb_per), tn,
+                                                                      tm * tn, go, uo, gate, withhold, wait_ns);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -619,8 +672,12 @@ cudaError_t tc5_update(int64_t n, int s, int c, const void* slu, const void* slc
   uo.Y = Y;
   uo.beta = beta;
   uo.has_beta = beta != 0.0;
+  CUtensorMap tma, tmb;
+  if ((e = slice_tmap(&tma, slu, NS, s, n, BM)) != cudaSuccess) return e;
+  if ((e = slice_tmap(&tmb, slc, NS, s, c, BN)) != cudaSuccess) return e;
   tc5_kernel<1, NS, BN, T><<<(unsigned)grid, THREADS, Cfg<NS, BN>::SMEM, st>>>(
-      opnd(slu, NS, s, n), opnd(slc, NS, s, c), int(nkb), int(nkb), tn, int(items), go, uo, gate, -1, WAIT_NS);
+      tma, tmb, opnd(slu, NS, s, n), opnd(slc, NS, s, c), int(nkb), int(nkb), tn, int(items), go, uo, gate, -1,
+      WAIT_NS);
   count_launches(1);
   return cudaGetLastError();
 }
