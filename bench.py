@@ -5,7 +5,12 @@ LOBPCG on one GB300, against the fixed-block solver.
 Workload (default): 3D Dirichlet 7-point Laplacian on a 128^3 grid
 (n = 2,097,152, nnz = 14,581,760, int32 CSR), the 64 smallest eigenpairs,
 LOBPCG with k_max = 128 (nes = 69), Gaussian X0 (Philox seed 1), residual
-tolerance 1e-8, strategy `fix`, double-float (FP64-storage) form.
+tolerance 1e-8, strategy `fix`, float64 form: float64 blocks, float64 SpMM,
+Gram products and block updates on the tensor cores by an exact seven-slice
+splitting (float64-class accuracy), float64 small dense steps.  After the
+timed solves the same workload is solved once under each other strategy
+(`none` = the fixed block, `slope`, `slopek`), and `fixed_block` /
+`strategies` report them.
 
 A step is one whole solve: X0 -> 64 eigenpairs whose relative residual
 ||A v - lambda v|| / ||A|| is at most 1e-8 (checked in float64 after every
@@ -14,7 +19,12 @@ resident in HBM when the timed region starts; the blocks (4.3 GB each) are
 far larger than L2, so no separate L2 flush is needed.
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
-build) on the host cores on a bounded sample of the same workload.
+build) on the host cores: one step is one iteration of the oracle's own
+LOBPCG solve of the same workload (the first W iterations untimed), and the
+eigenpairs/s it reports projects the timed mean iteration onto the
+iteration count of a whole solve (labelled as a projection).
+
+--kernel times one kernel class on its own (micro-benchmark for ncu).
 """
 from __future__ import annotations
 
@@ -39,15 +49,14 @@ from paper_2409_05572_gb300 import workloads as W  # noqa: E402
 METRIC = "converged eigenpairs/s at 1e-8 residual vs fixed-block FP64; p50/p99 latency"
 UNIT = "eigenpairs/s"
 
-# DRAM traffic / algorithmic bytes of one launch, from the ncu captures of
-# the small cases (profiles/gram_kernel_df64_n262144_384x384_sym.md and
-# profiles/update_kernel_df64_n262144_384x256.md); traffic grows with n.
-TRAFFIC_RATIO = {"gram": 1.387 / 0.805, "update": 1.447 / 1.342}
-# the same for the tensor-core classes (slicing + product kernels), from ncu
-# captures at n = 262,144 (profiles/tc5_gram_*.md, profiles/tc5_update_*.md):
-# DRAM bytes of the class's kernels / the class's algorithmic bytes
-TC_TRAFFIC_RATIO = {"gram": (0.809 + 1.167 + 1.213 + 0.001) / 0.805,
-                    "update": (0.001 + 0.809 + 1.166 + 1.213 + 0.506) / 1.342}
+# DRAM traffic / algorithmic bytes of the tensor-core classes of the float64
+# form (slicing + product kernels), from one ncu capture of the current
+# kernels at n = 262,144 (384-column operands; the Gram class reads U once,
+# 0.805 GB; the update class reads U and writes Y, 1.342 GB): slicer
+# 0.806 GB read + 1.367 GB written, Gram product 1.416 GB read, update
+# product 1.414 GB read + 0.514 GB written.  Traffic grows with n.
+TC_TRAFFIC_RATIO = {"gram": (0.806 + 1.367 + 1.416) / 0.805,
+                    "update": (0.806 + 1.367 + 1.414 + 0.514) / 1.342}
 
 
 def peaks():
@@ -69,10 +78,11 @@ def bf16_sustained():
     return 1700.0, "fallback (sustained)"
 
 
-# The tensor-core Gram and update cut each double-float operand into six
-# exact bf16 slices and form the 21 slice products of levels 0..5, i.e. 21
-# bf16 multiply-adds per double-float multiply-add.
-TC_MMA_PER_MAC = 21
+# The tensor-core Gram and update cut each operand into exact bf16 slices
+# and form the slice products of the kept levels: 28 bf16 multiply-adds per
+# float64 multiply-add (seven slices, levels 0..6), 21 per double-float one
+# (six slices, levels 0..5).
+TC_MMA_PER_MAC = {"f64": 28, "df64": 21}
 
 
 # FP32 issue rate measured on this machine's GB300 (152 SMs, FFMA, 72.6 TFLOP/s
@@ -189,74 +199,78 @@ def dist_env():
     return ws, rank, local
 
 
+def oracle_iterations(wl, strategy, iters):
+    """Run the FP64 oracle's own LOBPCG solve of the workload for `iters`
+    iterations (Algorithm 3 as it stands, on the host cores, BLAS threads =
+    affinity cores) and return the wall time of the set-up plus each
+    iteration: times[0] = set-up + iteration 1, times[j] = iteration j + 1
+    (stamped by the oracle's per-iteration observer after each Rayleigh-Ritz
+    step)."""
+    from oracle.lobpcg import lobpcg as o_lobpcg
+    A, nev, k = wl["A"], wl["nev"], wl["k_max"]
+    X0 = W.gaussian_block(A.n, k, wl["seed"])
+    stamps = []
+    t0 = time.perf_counter()
+    o_lobpcg(A, X0, nev, nev + 5, strategy, tol=0.5 * wl["tol"], normA=wl["normA"], max_iter=iters,
+             observer=lambda *a: stamps.append(time.perf_counter()))
+    prev, out = t0, []
+    for t in stamps:
+        out.append(t - prev)
+        prev = t
+    return out
+
+
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle, timed on the host cores."""
+    """Reference arm: the FP64 CPU oracle, timed on the host cores.  A step
+    is one iteration of the oracle's solve of the same workload; the first
+    `warmup` iterations (the first includes the set-up) are not timed."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    from oracle import blocks as B
-    from oracle.lobpcg import lobpcg as o_lobpcg  # noqa: F401
     wl = make_workload(args.workload)
-    A, nev, k = wl["A"], wl["nev"], wl["k_max"]
-    X0 = W.gaussian_block(A.n, k, wl["seed"])
+    if wl.get("algo", "lobpcg") != "lobpcg":
+        print(json.dumps({"impl": "reference", "unavailable": "the timed oracle arm covers the LOBPCG workloads"}))
+        return 0
+    nev = wl["nev"]
     cores = len(os.sched_getaffinity(0))
-    per_iter = []
     t_all = time.perf_counter()
-    for step in range(args.warmup + args.steps):
-        t = oracle_iteration_time(A, X0, nev, wl["normA"])
-        if step >= args.warmup:
-            per_iter.append(t)
-    iters_est = args.ref_iters
-    sec = statistics.mean(per_iter) * iters_est
-    value = nev / sec
+    times = oracle_iterations(wl, args.strategy, args.warmup + args.steps)
+    timed = times[args.warmup:]
+    ms_iter = 1e3 * statistics.mean(timed)
+    sec_solve = ms_iter / 1e3 * args.ref_iters
+    value = nev / sec_solve
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_iter, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": wl["desc"], "strategy": args.strategy},
+            "config": {"workload": wl["desc"], "strategy": args.strategy,
+                       "step": "one iteration of the oracle's LOBPCG solve (iterations "
+                               f"{args.warmup + 1}..{args.warmup + args.steps} timed)"},
+            "projection": {"iterations_per_solve": args.ref_iters,
+                           "source": "iteration count of the GPU solve of the same workload",
+                           "seconds_per_solve": sec_solve,
+                           "note": "value = nev / (timed mean iteration x iterations_per_solve); the early "
+                                   "iterations run at the full width k_max, later ones are narrower after "
+                                   "shrinks and locking, so this overstates the solve time somewhat"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"one full-width LOBPCG iteration of the FP64 oracle per step "
-                                       f"(mean {statistics.mean(per_iter):.2f} s), scaled by "
-                                       f"{iters_est} iterations per solve"},
+                             "sample": f"{args.steps} timed iterations of the oracle's own solve "
+                                       f"(mean {ms_iter / 1e3:.2f} s), projected to {args.ref_iters} iterations"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t_all}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def oracle_iteration_time(A, X0, nev, normA):
-    """Wall time of one full-width LOBPCG iteration of the FP64 oracle (the
-    residual, projection, CholeskyQR2, SpMM, Rayleigh-Ritz, HL and update
-    steps), after an untimed set-up Rayleigh-Ritz."""
-    from oracle import blocks as B
-    X = B.cholqr2(X0)
-    AX = B.spmm(A, X)
-    lam, Z = B.rayleigh_ritz(X, AX)
-    X, AX = X @ Z, AX @ Z
-    t0 = time.perf_counter()
-    R, rho, r = B.residual_test(X, AX, lam, normA, nev)
-    Wb = B.orth_against(R, X)
-    AW = B.spmm(A, Wb)
-    S = np.hstack([X, Wb])
-    AS = np.hstack([AX, AW])
-    theta, Zs = B.rayleigh_ritz(S, AS)
-    CX, CP = B.hl_trick(Zs, X.shape[1], 0)
-    X2, AX2, P2, AP2 = S @ CX, AS @ CX, S @ CP, AS @ CP
-    # a steady-state iteration also carries P: add the cost of its share
-    S3 = np.hstack([X2, P2, Wb])
-    AS3 = np.hstack([AX2, AP2, AW])
-    B.gram(S3, AS3)
-    _ = S3 @ np.vstack([CX, np.zeros((S3.shape[1] - CX.shape[0], CX.shape[1]))])
-    return time.perf_counter() - t0
-
-
-def cpu_baseline(A, X0, nev, normA, iters, budget_s=30.0):
+def cpu_baseline(wl, strategy, iters):
+    """The oracle as it stands on a bounded sample: the set-up and first
+    iteration of its own solve of the workload, projected to the GPU
+    solve's iteration count."""
     cores = len(os.sched_getaffinity(0))
-    t = oracle_iteration_time(A, X0, nev, normA)
+    t = oracle_iterations(wl, strategy, 1)[0]
     sec = t * iters
-    return {"value": nev / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one full-width LOBPCG iteration of the FP64 oracle on this workload "
-                      f"({t:.2f} s, BLAS threads = affinity cores), scaled by the GPU solve's "
-                      f"{iters} iterations"}
+    return {"value": wl["nev"] / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"set-up + first iteration of the FP64 oracle's LOBPCG solve of this workload "
+                      f"({t:.2f} s, BLAS threads = affinity cores), projected to the GPU solve's {iters} "
+                      "iterations"}
 
 
 def run_serving(args):
@@ -407,15 +421,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--strategy", default="fix")
-    ap.add_argument("--form", default="df64")
-    ap.add_argument("--no-compare", action="store_true", help="skip the fixed-block comparison solve")
+    ap.add_argument("--form", default="f64", choices=["f64", "df64", "mixed"])
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the solves under the other strategies (fixed block, slope, slopek)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--requests", type=int, default=32, help="c5: requests replayed from the stream")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="c5: device memory for active solves")
     ap.add_argument("--max-active", type=int, default=64, help="c5: solves advanced per step")
     ap.add_argument("--gram-tc", type=int, default=1, choices=[0, 1],
-                    help="1: double-float Gram and update on the tensor cores; 0: on the FP32 pipes")
+                    help="1: Gram and update on the tensor cores (exact slices); 0: on the CUDA cores")
     ap.add_argument("--aggressive-warmup", action="store_true",
                     help="warm-up gate on the first pair's residual with r_warm = 1e-1 (the paper's closing "
                          "remarks) instead of r^(j) <= 1e-4")
@@ -505,13 +520,16 @@ def main():
     eig_err = (float(np.max(np.abs(last["lam"] - wl["exact"]) / np.abs(wl["exact"])))
                if wl.get("exact") is not None else None)
 
+    tc_on = extra.get("gram_tc", 1) != 0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.form, "data": "synthetic",
             "config": {"workload": wl["desc"], "nev": nev, "k_max": k, "strategy": args.strategy,
                        "form": args.form, "tol": tol, "parallelism": f"replicas x{ws}",
-                       "products": "tensor cores (tcgen05, exact bf16 slices)" if (args.gram_tc and args.form != "f64")
-                       else "CUDA cores",
+                       "products": ("tensor cores (tcgen05, exact bf16 slices: "
+                                    + ("7 slices, 28 pairs per float64 multiply-add)" if args.form == "f64"
+                                       else "6 slices, 21 pairs per double-float multiply-add)"))
+                       if tc_on else "CUDA cores",
                        "l2": "inputs larger than L2 (each n x k block is 4.3 GB); no flush",
                        "warmup_rule": "first pair, r_warm 1e-1" if args.aggressive_warmup else "r^(j), r_warm 1e-4"},
             "converged": bool(ok), "iters": last["iters"], "n_shrink": last["n_shrink"],
@@ -529,18 +547,21 @@ def main():
         ach = v["bytes"] / (v["ms"] / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "peak_source": src}
-    elif dom in ("gram", "update") and args.form != "f64" and extra.get("gram_tc", 1):
+    elif dom in ("gram", "update") and tc_on and args.form in TC_MMA_PER_MAC:
         # tensor-core products: the bf16 MMA work the sliced method performs
-        # (21 slice products per double-float multiply-add) against the
-        # sustained bf16 peak; the class time includes the slicing passes
+        # (28 or 21 slice products per multiply-add of the method) against
+        # the sustained bf16 peak; the class time includes the slicing passes
+        per = TC_MMA_PER_MAC[args.form]
         alg = v["flops"] / (v["ms"] / 1e3) / 1e12
-        ach = TC_MMA_PER_MAC * alg
+        ach = per * alg
         pk, psrc = bf16_sustained()
         roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                 "frac": ach / pk, "peak_source": psrc,
-                "df64_equivalent_tflops": alg,
-                "note": "achieved = 21 bf16 slice products per double-float multiply-add x algorithmic "
-                        "multiply-adds / class time (slicing passes included)"}
+                "method_tflops": alg,
+                "method_bytes_frac_of_hbm": v["bytes"] / (v["ms"] / 1e3) / 1e9 / hbm,
+                "note": f"achieved = {per} bf16 slice products per {args.form} multiply-add x the method's "
+                        "multiply-adds / class time (slicing passes included); method_tflops is the "
+                        f"{args.form} rate of the method itself"}
     else:
         ach = v["flops"] / (v["ms"] / 1e3) / 1e12
         pk = FP64_PEAK_TFLOPS if args.form == "f64" else DF64_PEAK_TFLOPS
@@ -550,38 +571,49 @@ def main():
                                "11.1 FP32 instructions per double-float multiply-add x 2"
                 if args.form != "f64" else "measured native FP64 FMA rate"}
     roof["avg_launch_ms"] = v["ms"] / max(v["launches"], 1)
-    tc_on = args.form != "f64" and extra.get("gram_tc", 1) != 0
-    ratios = TC_TRAFFIC_RATIO if tc_on else TRAFFIC_RATIO
-    if dom in ratios and args.form == "df64":
+    if dom in TC_TRAFFIC_RATIO and tc_on and args.form == "f64":
         # per launch, like achieved: algorithmic bytes of the class's average
         # launch x the DRAM/algorithmic ratio of the ncu capture
-        roof["traffic"] = ratios[dom] * v["bytes"] / max(v["launches"], 1)
-        roof["traffic_source"] = (f"ncu dram__bytes_read+write of the {dom} kernels at n=262144 "
-                                  f"(ratio {ratios[dom]:.2f} to algorithmic bytes), scaled")
+        roof["traffic"] = TC_TRAFFIC_RATIO[dom] * v["bytes"] / max(v["launches"], 1)
+        roof["traffic_source"] = (f"ncu dram__bytes_read+write of the {dom} class's kernels at n=262144 "
+                                  f"(ratio {TC_TRAFFIC_RATIO[dom]:.2f} to algorithmic bytes), scaled")
     else:
         roof["traffic"] = None
     line["roofline"] = roof
     sp = kst.get("spmm")
     if sp and sp["launches"]:
         a = sp["bytes"] / (sp["ms"] / 1e3) / 1e9
-        line["spmm_hbm"] = {"achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm}
+        f = sp["flops"] / (sp["ms"] / 1e3) / 1e12
+        line["spmm"] = {"hbm_gbs": a, "hbm_frac": a / hbm,
+                        "fp64_tflops": f if args.form == "f64" else None,
+                        "fp64_pipe_frac": f / FP64_PEAK_TFLOPS if args.form == "f64" else None}
 
     if rank == 0 and not args.no_compare:
-        fixed = L.Solver((rp, ci, va), nev=nev, k_max=k, strategy="none", X0=X0d, normA=normA, tol=0.5 * tol,
-                         form=args.form, stream=stream, max_iter=args.max_iter, algo=algo, **extra)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        fo = fixed.solve()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        fms = e0.elapsed_time(e1)
-        fconv = bool(fo["status"] == 0 and np.max(fo["resid"]) <= tol)
-        # a solve stopped by the iteration cap has no time-to-converged-nev:
-        # no throughput and no speed-up are derived from it
-        line["fixed_block"] = {"value": nev / (fms / 1e3) if fconv else None, "unit": UNIT, "ms": fms,
-                               "iters": fo["iters"], "converged": fconv,
-                               "speedup_of_shrink_expand": fms / ms_step if fconv else None}
-        fixed.close()
+        # every other strategy once on the same workload and form; `none` is
+        # the fixed block of k_max columns (the metric's comparison)
+        strat = {args.strategy: {"value": value, "ms": ms_step, "iters": last["iters"],
+                                 "n_shrink": last["n_shrink"], "n_expand": last["n_expand"], "converged": bool(ok)}}
+        for name in ("none", "fix", "slope", "slopek"):
+            if name in strat:
+                continue
+            other = L.Solver((rp, ci, va), nev=nev, k_max=k, strategy=name, X0=X0d, normA=normA, tol=0.5 * tol,
+                             form=args.form, stream=stream, max_iter=args.max_iter, algo=algo, **extra)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fo = other.solve()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fms = e0.elapsed_time(e1)
+            fconv = bool(fo["status"] == 0 and np.max(fo["resid"]) <= tol)
+            # a solve stopped by the iteration cap has no time-to-converged-nev
+            strat[name] = {"value": nev / (fms / 1e3) if fconv else None, "ms": fms, "iters": fo["iters"],
+                           "n_shrink": fo["n_shrink"], "n_expand": fo["n_expand"], "converged": fconv}
+            other.close()
+        line["strategies"] = strat
+        fb = strat["none"]
+        line["fixed_block"] = {"value": fb["value"], "unit": UNIT, "ms": fb["ms"], "iters": fb["iters"],
+                               "converged": fb["converged"],
+                               "speedup_of_shrink_expand": fb["ms"] / ms_step if fb["converged"] and ok else None}
 
     if rank == 0 and not args.no_e2e:
         # end to end through the public API: host CSR + pinned host X0 in,
@@ -603,7 +635,7 @@ def main():
                        "d2h_bytes_per_step": int(Vh.numel() * 8 + nev * 8), "seconds": t_e2e}
 
     if rank == 0 and ws == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(A, X0, nev, normA, last["iters"])
+        line["cpu_baseline"] = cpu_baseline(wl, args.strategy, last["iters"])
 
     solver.close()
     if rank == 0:

@@ -184,9 +184,13 @@ int eig_cholqr2(int64_t n, int w, void *W, int64_t ldw, int arith, int *status_o
 /* ---- a9: small dense symmetric eigensolver (Rayleigh-Ritz, Algorithms 1-3)
  * A (s x s float64, device, symmetric, leading dimension lda) = Z diag(lam) Z^T
  * with lam ascending.  lam: float64[s], Z: s x s float64 row-major (columns are
- * eigenvectors), both device.  Householder tridiagonalisation, implicit QL
- * with Wilkinson shifts, back-transformation; float64 throughout.  A is not
- * modified.  s <= 4096. */
+ * eigenvectors), both device.  Float64 throughout: Householder
+ * tridiagonalisation, eigenvalues by bisection on Sturm counts, eigenvectors
+ * by inverse iteration with Gram-Schmidt inside clusters of nearly equal
+ * eigenvalues, back-transformation -- the eigensolver of the float64 form
+ * (the double-float and mixed forms refine a float32 decomposition instead).
+ * A is not modified.  Returns EIG_EBREAKDOWN if the decomposition reported a
+ * failure.  s <= 4096. */
 int eig_syev(int s, const double *A, int64_t lda, double *lam, double *Z, int64_t ldz,
              void *stream);
 

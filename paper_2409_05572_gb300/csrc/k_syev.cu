@@ -40,11 +40,19 @@ namespace eig {
 template <typename R> struct RealT;
 template <> struct RealT<float> {
   static __device__ __forceinline__ float eps() { return 1.1920928955078125e-07f; }
+  static __device__ __forceinline__ float tiny() { return 1.1754944e-38f; }
+  // inverse-iteration clusters: consecutive eigenvalues closer than this
+  // fraction of ||T||_1 are orthogonalised together
+  static __device__ __forceinline__ float ortol() { return 1e-5f; }
+  static __device__ __forceinline__ float big() { return 1e20f; }
   static __device__ __forceinline__ float hyp(float a, float b) { return hypotf(a, b); }
   static constexpr float lo = 1e-35f, hi = 1e35f;
 };
 template <> struct RealT<double> {
   static __device__ __forceinline__ double eps() { return 2.220446049250313e-16; }
+  static __device__ __forceinline__ double tiny() { return 2.2250738585072014e-308; }
+  static __device__ __forceinline__ double ortol() { return 1e-3; }
+  static __device__ __forceinline__ double big() { return 1e150; }
   static __device__ __forceinline__ double hyp(double a, double b) { return hypot(a, b); }
   static constexpr double lo = 1e-280, hi = 1e280;
 };
@@ -266,61 +274,66 @@ __global__ void tql_kernel(int s, R* __restrict__ dg, R* __restrict__ eg, int* _
 // eigenvalues closer than 1e-5 ||T||_1 (one CTA per cluster).
 // No step is a sequential chain over all eigenvalues.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int sturm_count(int s, const float* d, const float* e2, float x, float pivmin) {
+template <typename R>
+__device__ __forceinline__ int sturm_count(int s, const R* d, const R* e2, R x, R pivmin) {
   int cnt = 0;
-  float q = d[0] - x;
-  if (fabsf(q) < pivmin) q = -pivmin;
-  cnt += q < 0.f;
+  R q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < R(0);
   for (int k = 1; k < s; ++k) {
     q = (d[k] - x) - e2[k - 1] / q;
-    if (fabsf(q) < pivmin) q = -pivmin;
-    cnt += q < 0.f;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < R(0);
   }
   return cnt;
 }
 
-// lam[i] = i-th smallest eigenvalue of T (d, e; e[k] = T[k+1][k])
-__global__ void __launch_bounds__(128) bisect_kernel(int s, const float* __restrict__ dg, const float* __restrict__ eg,
-                                                     float* __restrict__ lam) {
-  extern __shared__ float sh[];
-  float* d = sh;
-  float* e2 = sh + s;
-  __shared__ float bounds[4];
+// lam[i] = i-th smallest eigenvalue of T (d, e; e[k] = T[k+1][k]) by
+// bisection on Sturm counts, one thread per eigenvalue, to an absolute
+// accuracy of eps ||T|| (eps of the working precision R)
+template <typename R>
+__global__ void __launch_bounds__(128) bisect_kernel(int s, const R* __restrict__ dg, const R* __restrict__ eg,
+                                                     R* __restrict__ lam) {
+  extern __shared__ unsigned char shb[];
+  R* d = reinterpret_cast<R*>(shb);
+  R* e2 = d + s;
+  __shared__ R bounds[4];
+  const R eps = RealT<R>::eps();
   for (int k = threadIdx.x; k < s; k += blockDim.x) {
     d[k] = dg[k];
-    e2[k] = k + 1 < s ? eg[k] * eg[k] : 0.f;
+    e2[k] = k + 1 < s ? eg[k] * eg[k] : R(0);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    float gl = d[0], gu = d[0], emax = 0.f;
+    R gl = d[0], gu = d[0], emax = 0;
     for (int k = 0; k < s; ++k) {
-      const float r = (k > 0 ? fabsf(eg[k - 1]) : 0.f) + (k + 1 < s ? fabsf(eg[k]) : 0.f);
-      gl = fminf(gl, d[k] - r);
-      gu = fmaxf(gu, d[k] + r);
-      emax = fmaxf(emax, e2[k]);
+      const R r = (k > 0 ? fabs(eg[k - 1]) : R(0)) + (k + 1 < s ? fabs(eg[k]) : R(0));
+      gl = fmin(gl, d[k] - r);
+      gu = fmax(gu, d[k] + r);
+      emax = fmax(emax, e2[k]);
     }
-    const float pivmin = 1.1754944e-38f * fmaxf(1.f, emax);
-    const float tn = fmaxf(fabsf(gl), fabsf(gu));
-    bounds[0] = gl - 2.f * 1.1920929e-07f * tn - 2.f * pivmin;
-    bounds[1] = gu + 2.f * 1.1920929e-07f * tn + 2.f * pivmin;
+    const R pivmin = RealT<R>::tiny() * fmax(R(1), emax);
+    const R tn = fmax(fabs(gl), fabs(gu));
+    bounds[0] = gl - R(2) * eps * tn - R(2) * pivmin;
+    bounds[1] = gu + R(2) * eps * tn + R(2) * pivmin;
     bounds[2] = pivmin;
-    bounds[3] = 1.1920929e-07f * tn;  // absolute accuracy eps ||T|| is all the refinement needs
+    bounds[3] = eps * tn;
   }
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= s) return;
-  float lo = bounds[0], hi = bounds[1];
-  const float pivmin = bounds[2], atol = bounds[3];
-  for (int it = 0; it < 100; ++it) {
-    const float mid = 0.5f * (lo + hi);
+  R lo = bounds[0], hi = bounds[1];
+  const R pivmin = bounds[2], atol = bounds[3];
+  for (int it = 0; it < 200; ++it) {
+    const R mid = R(0.5) * (lo + hi);
     if (mid <= lo || mid >= hi) break;
-    if (hi - lo <= 2.f * 1.1920929e-07f * fmaxf(fabsf(lo), fabsf(hi)) + atol) break;
-    if (sturm_count(s, d, e2, mid, pivmin) > i)
+    if (hi - lo <= R(2) * eps * fmax(fabs(lo), fabs(hi)) + atol) break;
+    if (sturm_count<R>(s, d, e2, mid, pivmin) > i)
       hi = mid;
     else
       lo = mid;
   }
-  lam[i] = 0.5f * (lo + hi);
+  lam[i] = R(0.5) * (lo + hi);
 }
 
 // Shifts equal to the eigenvalues: every vector starts from its own
@@ -328,44 +341,55 @@ __global__ void __launch_bounds__(128) bisect_kernel(int s, const float* __restr
 // independent without the shift separation of stein (which, at about
 // 10 eps ||T|| per member, would push the shifts of a large group of equal
 // eigenvalues toward the next distinct one).  Cluster starts: gap to the
-// previous eigenvalue at most 1e-5 ||T||_1 (closer pairs can mix in float32
-// inverse iteration and are orthogonalised together; farther pairs are
-// coupled by at most (eps ||T|| / gap)^2 after two passes, which the
-// refinement removes).  Zero-pivot replacement eps ||T||_1.
-__global__ void invit_prep_kernel(int s, const float* __restrict__ d, const float* __restrict__ e,
-                                  const float* __restrict__ lam, float* __restrict__ sig, int* __restrict__ cstart,
-                                  float* __restrict__ pert) {
+// previous eigenvalue at most ortol ||T||_1.  An inverse-iteration vector
+// errs by about eps ||T|| / gap in the direction of a neighbour at distance
+// gap, so pairs closer than ortol ||T|| are orthogonalised together: 1e-3 in
+// float64 (the rule of LAPACK's stein; cross-cluster coupling then stays near
+// eps / 1e-3), 1e-5 in float32 (the double-float refinement that follows
+// removes the remaining coupling).  Zero-pivot replacement eps ||T||_1.
+//
+// Float32 cannot resolve eigenvalues whose gaps approach eps32 ||T||: when
+// three of them sit within that resolution, inverse iteration from every
+// start converges to the same one or two directions, and the Gram-Schmidt
+// remainder of the last vector is dominated by neighbouring eigenvectors
+// outside the cluster.  The float64 working precision resolves the same
+// groups with nine orders of magnitude to spare.
+template <typename R>
+__global__ void invit_prep_kernel(int s, const R* __restrict__ d, const R* __restrict__ e,
+                                  const R* __restrict__ lam, R* __restrict__ sig, int* __restrict__ cstart,
+                                  R* __restrict__ pert) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  float nrm = 0.f;
+  R nrm = 0;
   for (int k = 0; k < s; ++k)
-    nrm = fmaxf(nrm, fabsf(d[k]) + (k > 0 ? fabsf(e[k - 1]) : 0.f) + (k + 1 < s ? fabsf(e[k]) : 0.f));
-  const float ortol = 1e-5f * nrm;
+    nrm = fmax(nrm, fabs(d[k]) + (k > 0 ? fabs(e[k - 1]) : R(0)) + (k + 1 < s ? fabs(e[k]) : R(0)));
+  const R ortol = RealT<R>::ortol() * nrm;
   sig[0] = lam[0];
   cstart[0] = 0;
   for (int j = 1; j < s; ++j) {
     sig[j] = lam[j];
     cstart[j] = (lam[j] - lam[j - 1] <= ortol) ? cstart[j - 1] : j;
   }
-  *pert = fmaxf(1.1920929e-07f * nrm, 1.1754944e-38f);
+  *pert = fmax(RealT<R>::eps() * nrm, RealT<R>::tiny());
 }
 
 // One inverse-iteration solve per thread j: (T - sig_j I) x = b, b a fixed
 // pseudo-random vector (pass 0, which also factors) or column j of ZT (later
 // passes); x normalised into column j of ZT (ZT[j s + i]).  Factor arrays are
 // [k][j] so that the threads of a warp touch consecutive words.
-__global__ void __launch_bounds__(128) invit_kernel(int s, const float* __restrict__ d, const float* __restrict__ e,
-                                                    const float* __restrict__ sig, const float* __restrict__ pertp,
-                                                    float* __restrict__ dl, float* __restrict__ dg,
-                                                    float* __restrict__ du, float* __restrict__ du2,
-                                                    unsigned char* __restrict__ piv, float* __restrict__ b,
-                                                    float* __restrict__ ZT, int pass) {
+template <typename R>
+__global__ void __launch_bounds__(128) invit_kernel(int s, const R* __restrict__ d, const R* __restrict__ e,
+                                                    const R* __restrict__ sig, const R* __restrict__ pertp,
+                                                    R* __restrict__ dl, R* __restrict__ dg, R* __restrict__ du,
+                                                    R* __restrict__ du2, unsigned char* __restrict__ piv,
+                                                    R* __restrict__ b, R* __restrict__ ZT, int pass) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= s) return;
   const int64_t S = s;
-  const float pert = *pertp;
+  const R pert = *pertp;
+  const R big = RealT<R>::big();
 #define AT(a, k) a[int64_t(k) * S + j]
   if (pass == 0) {
-    const float sg = sig[j];
+    const R sg = sig[j];
     for (int k = 0; k < s; ++k) {
       AT(dg, k) = d[k] - sg;
       if (k + 1 < s) {
@@ -374,25 +398,25 @@ __global__ void __launch_bounds__(128) invit_kernel(int s, const float* __restri
       }
     }
     for (int k = 0; k + 1 < s; ++k) {
-      const float a = AT(dg, k), l = AT(dl, k);
-      if (fabsf(a) >= fabsf(l)) {  // no interchange
-        const float a2 = a != 0.f ? a : pert;
-        const float f = l / a2;
+      const R a = AT(dg, k), l = AT(dl, k);
+      if (fabs(a) >= fabs(l)) {  // no interchange
+        const R a2 = a != R(0) ? a : pert;
+        const R f = l / a2;
         AT(dl, k) = f;
         AT(dg, k) = a2;
         AT(dg, k + 1) -= f * AT(du, k);
-        if (k + 2 < s) AT(du2, k) = 0.f;
+        if (k + 2 < s) AT(du2, k) = R(0);
         AT(piv, k) = 0;
       } else {  // interchange rows k and k + 1
-        const float f = a / l;
-        const float dk1 = AT(dg, k + 1);
+        const R f = a / l;
+        const R dk1 = AT(dg, k + 1);
         AT(dg, k) = l;
         AT(dl, k) = f;
-        const float t = AT(du, k);
+        const R t = AT(du, k);
         AT(du, k) = dk1;
         AT(dg, k + 1) = t - f * dk1;
         if (k + 2 < s) {
-          const float u1 = AT(du, k + 1);
+          const R u1 = AT(du, k + 1);
           AT(du2, k) = u1;
           AT(du, k + 1) = -f * u1;
         }
@@ -400,8 +424,8 @@ __global__ void __launch_bounds__(128) invit_kernel(int s, const float* __restri
       }
     }
     for (int k = 0; k < s; ++k) {
-      const float a = AT(dg, k);
-      if (fabsf(a) < pert) AT(dg, k) = a < 0.f ? -pert : pert;
+      const R a = AT(dg, k);
+      if (fabs(a) < pert) AT(dg, k) = a < R(0) ? -pert : pert;
     }
     // fixed pseudo-random start (integer hash of (k, j)), entries in [-1, 1)
     for (int k = 0; k < s; ++k) {
@@ -411,12 +435,12 @@ __global__ void __launch_bounds__(128) invit_kernel(int s, const float* __restri
       h ^= h >> 12;
       h *= 0x297A2D39u;
       h ^= h >> 15;
-      AT(b, k) = float(int32_t(h)) * 4.656612873e-10f;
+      AT(b, k) = R(int32_t(h)) * R(4.656612873e-10);
     }
   } else {
-    float mx = 0.f;
-    for (int k = 0; k < s; ++k) mx = fmaxf(mx, fabsf(ZT[int64_t(j) * S + k]));
-    const float sc = mx > 0.f ? 1.f / mx : 1.f;
+    R mx = 0;
+    for (int k = 0; k < s; ++k) mx = fmax(mx, fabs(ZT[int64_t(j) * S + k]));
+    const R sc = mx > R(0) ? R(1) / mx : R(1);
     for (int k = 0; k < s; ++k) AT(b, k) = ZT[int64_t(j) * S + k] * sc;
   }
   // forward: L with the interchanges
@@ -424,8 +448,8 @@ __global__ void __launch_bounds__(128) invit_kernel(int s, const float* __restri
     if (AT(piv, k) == 0) {
       AT(b, k + 1) -= AT(dl, k) * AT(b, k);
     } else {
-      const float t = AT(b, k);
-      const float bk1 = AT(b, k + 1);
+      const R t = AT(b, k);
+      const R bk1 = AT(b, k + 1);
       AT(b, k) = bk1;
       AT(b, k + 1) = t - AT(dl, k) * bk1;
     }
@@ -434,49 +458,51 @@ __global__ void __launch_bounds__(128) invit_kernel(int s, const float* __restri
   // eigenvalues) has several tiny pivots, each multiplying the solution by up
   // to ||T|| / pert; the whole vector (solved part and remaining right-hand
   // side alike, x = U^{-1} b being linear) is rescaled before it can overflow.
-  float x2 = 0.f, x1 = 0.f, nrm = 0.f;
+  R x2 = 0, x1 = 0, nrm = 0;
   for (int k = s - 1; k >= 0; --k) {
-    float v = AT(b, k);
+    R v = AT(b, k);
     if (k + 1 < s) v -= AT(du, k) * x1;
     if (k + 2 < s) v -= AT(du2, k) * x2;
     v /= AT(dg, k);
-    if (fabsf(v) > 1e20f) {
-      for (int q = 0; q < s; ++q) AT(b, q) *= 1e-20f;
-      v *= 1e-20f;
-      x1 *= 1e-20f;
-      x2 *= 1e-20f;
-      nrm *= 1e-20f;
+    if (fabs(v) > big) {
+      const R sm = R(1) / big;
+      for (int q = 0; q < s; ++q) AT(b, q) *= sm;
+      v *= sm;
+      x1 *= sm;
+      x2 *= sm;
+      nrm *= sm;
     }
     AT(b, k) = v;
     x2 = x1;
     x1 = v;
-    nrm = fmaxf(nrm, fabsf(v));
+    nrm = fmax(nrm, fabs(v));
   }
   // normalise (scaled 2-norm)
-  const float inv = nrm > 0.f ? 1.f / nrm : 1.f;
-  float ss = 0.f;
+  const R inv = nrm > R(0) ? R(1) / nrm : R(1);
+  R ss = 0;
   for (int k = 0; k < s; ++k) {
-    const float v = AT(b, k) * inv;
+    const R v = AT(b, k) * inv;
     ss += v * v;
   }
-  const float f = ss > 0.f ? inv / sqrtf(ss) : 0.f;
+  const R f = ss > R(0) ? inv / sqrt(ss) : R(0);
   for (int k = 0; k < s; ++k) ZT[int64_t(j) * S + k] = AT(b, k) * f;
 #undef AT
 }
 
 // Classical Gram-Schmidt with re-orthogonalisation inside each cluster, in
 // ascending order: CTA b handles the cluster that starts at b.
+template <typename R>
 __global__ void __launch_bounds__(256) cluster_cgs_kernel(int s, const int* __restrict__ cstart,
-                                                          float* __restrict__ ZT) {
+                                                          R* __restrict__ ZT) {
   const int b = blockIdx.x;
   if (cstart[b] != b) return;
   int end = b + 1;
   while (end < s && cstart[end] == b) ++end;
   if (end - b == 1) return;
-  extern __shared__ float sh[];
-  float* x = sh;       // s
-  float* c = sh + s;   // cluster size
-  __shared__ float red[8];
+  extern __shared__ unsigned char shc[];
+  R* x = reinterpret_cast<R*>(shc);  // s
+  R* c = x + s;                      // cluster size
+  __shared__ R red[8];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int64_t S = s;
   for (int j = b + 1; j < end; ++j) {
@@ -484,29 +510,29 @@ __global__ void __launch_bounds__(256) cluster_cgs_kernel(int s, const int* __re
     __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {
       for (int i = b + warp; i < j; i += blockDim.x / 32) {
-        const float* q = ZT + int64_t(i) * S;
-        float acc = 0.f;
+        const R* q = ZT + int64_t(i) * S;
+        R acc = 0;
         for (int r = lane; r < s; r += 32) acc += q[r] * x[r];
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) c[i - b] = acc;
       }
       __syncthreads();
       for (int r = t; r < s; r += blockDim.x) {
-        float acc = 0.f;
+        R acc = 0;
         for (int i = b; i < j; ++i) acc += c[i - b] * ZT[int64_t(i) * S + r];
         x[r] -= acc;
       }
       __syncthreads();
     }
-    float part = 0.f;
+    R part = 0;
     for (int r = t; r < s; r += blockDim.x) part += x[r] * x[r];
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     if (lane == 0) red[warp] = part;
     __syncthreads();
-    float nn = 0.f;
+    R nn = 0;
     for (int w = 0; w < 8; ++w) nn += red[w];
-    if (nn > 0.f) {
-      const float f = rsqrtf(nn);
+    if (nn > R(0)) {
+      const R f = R(1) / sqrt(nn);
       for (int r = t; r < s; r += blockDim.x) ZT[int64_t(j) * S + r] = x[r] * f;
     }  // else: the vector lay in the span of the earlier ones; keep it as it was
     __syncthreads();
@@ -648,53 +674,40 @@ QLWork<R> ql_carve(int s, Carver& cv) {
   return w;
 }
 
-// EIG_TRIDIAG=ql selects the sequential QL chain for the float32 stage
-static bool use_tql() {
-  static const bool v = [] {
-    const char* e = std::getenv("EIG_TRIDIAG");
-    return e && std::strcmp(e, "ql") == 0;
-  }();
-  return v;
-}
-
-// bisection + inverse iteration for the float32 stage: eigenvectors of T into
+// bisection + inverse iteration in precision R: eigenvectors of T into
 // w.ZT (column j = eigenvector of the j-th smallest eigenvalue), ranks
 // (identity) and eigenvalues (float64, if lam)
 template <typename R>
 static cudaError_t tri_invit(int s, QLWork<R>& w, double* lam, cudaStream_t st) {
-  if constexpr (std::is_same<R, float>::value) {
-    const size_t ss = size_t(s) * s;
-    float* dl = w.rc;
-    float* dgv = w.rc + ss;
-    float* du = w.rc + 2 * ss;
-    float* du2 = w.rc + 3 * ss;
-    float* bv = w.rc + 4 * ss;
-    float* lamf = w.rs;
-    float* sig = w.rs + s;
-    float* pert = w.rs + 2 * s;
-    int* cstart = reinterpret_cast<int*>(w.rs + 2 * s + 64);
-    unsigned char* piv = reinterpret_cast<unsigned char*>(w.ri);
-    const unsigned nb = (unsigned)cdiv(s, 128);
-    bisect_kernel<<<nb, 128, 2 * size_t(s) * sizeof(float), st>>>(s, w.d, w.e, lamf); count_launches(1);
-    invit_prep_kernel<<<1, 32, 0, st>>>(s, w.d, w.e, lamf, sig, cstart, pert); count_launches(1);
-    cudaFuncSetAttribute(cluster_cgs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    for (int pass = 0; pass < 2; ++pass) {
-      invit_kernel<<<nb, 128, 0, st>>>(s, w.d, w.e, sig, pert, dl, dgv, du, du2, piv, bv, w.ZT, pass);
-      count_launches(1);
-      cluster_cgs_kernel<<<s, 256, 2 * size_t(s) * sizeof(float), st>>>(s, cstart, w.ZT); count_launches(1);
-    }
-    rank_kernel<float><<<nb, 128, 0, st>>>(s, lamf, w.rank, lam); count_launches(1);
-    return cudaGetLastError();
-  } else {
-    return cudaErrorInvalidValue;
+  const size_t ss = size_t(s) * s;
+  R* dl = w.rc;
+  R* dgv = w.rc + ss;
+  R* du = w.rc + 2 * ss;
+  R* du2 = w.rc + 3 * ss;
+  R* bv = w.rc + 4 * ss;
+  R* lamr = w.rs;
+  R* sig = w.rs + s;
+  R* pert = w.rs + 2 * s;
+  int* cstart = reinterpret_cast<int*>(w.rs + 2 * s + 64);
+  unsigned char* piv = reinterpret_cast<unsigned char*>(w.ri);
+  const unsigned nb = (unsigned)cdiv(s, 128);
+  bisect_kernel<R><<<nb, 128, 2 * size_t(s) * sizeof(R), st>>>(s, w.d, w.e, lamr); count_launches(1);
+  invit_prep_kernel<R><<<1, 32, 0, st>>>(s, w.d, w.e, lamr, sig, cstart, pert); count_launches(1);
+  cudaFuncSetAttribute(cluster_cgs_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  for (int pass = 0; pass < 2; ++pass) {
+    invit_kernel<R><<<nb, 128, 0, st>>>(s, w.d, w.e, sig, pert, dl, dgv, du, du2, piv, bv, w.ZT, pass);
+    count_launches(1);
+    cluster_cgs_kernel<R><<<s, 256, 2 * size_t(s) * sizeof(R), st>>>(s, cstart, w.ZT); count_launches(1);
   }
+  rank_kernel<R><<<nb, 128, 0, st>>>(s, lamr, w.rank, lam); count_launches(1);
+  return cudaGetLastError();
 }
 
 // Stage 1 in precision R: eigenvalues (ascending) into lam (if non-null) and
 // eigenvectors (float64, columns in ascending order) into Zd.
 template <typename R>
 cudaError_t ql_eig(int s, const double* A, int64_t lda, double* lam, double* Zd, int64_t ldz, QLWork<R>& w,
-                   int* status_dev, cudaStream_t st) {
+                   int* status_dev, cudaStream_t st, bool invit) {
   const int64_t ss = int64_t(s) * s;
   copy_sym_kernel<R><<<(unsigned)cdiv(ss, 256), 256, 0, st>>>(s, A, lda, w.Wm); count_launches(1);
   if (s >= 3) {
@@ -714,7 +727,7 @@ cudaError_t ql_eig(int s, const double* A, int64_t lda, double* lam, double* Zd,
     small_tridiag_kernel<R><<<1, 32, 0, st>>>(s, w.Wm, w.d, w.e, w.tau); count_launches(1);
   }
   cudaFuncSetAttribute(backtrans_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-  if (std::is_same<R, float>::value && !use_tql()) {
+  if (invit) {
     if (cudaError_t err = tri_invit(s, w, lam, st)) return err;
   } else {
     cudaFuncSetAttribute(tql_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
@@ -741,7 +754,19 @@ cudaError_t syev_qr64(int s, const double* A, int64_t lda, double* lam, double* 
   if (s <= 0) return cudaSuccess;
   Carver cv(work);
   QLWork<double> w = ql_carve<double>(s, cv);
-  return ql_eig<double>(s, A, lda, lam, Z, ldz, w, status_dev, st);
+  return ql_eig<double>(s, A, lda, lam, Z, ldz, w, status_dev, st, false);
+}
+
+// Float64 eigensolver of the float64 form: float64 Householder
+// tridiagonalisation (cooperative kernel), bisection, inverse iteration and
+// Gram-Schmidt inside clusters in float64, float64 back-transformation; no
+// double-float refinement (it would cap the accuracy at about 2^-48).
+cudaError_t syev64(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
+                   int* status_dev, cudaStream_t st) {
+  if (s <= 0) return cudaSuccess;
+  Carver cv(work);
+  QLWork<double> w = ql_carve<double>(s, cv);
+  return ql_eig<double>(s, A, lda, lam, Z, ldz, w, status_dev, st, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -951,7 +976,7 @@ cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, in
   const unsigned gb = (unsigned)cdiv(ss, 256);
   cudaError_t e;
   // stage 1: float32 decomposition (eigenvectors sorted ascending into Zd)
-  if ((e = ql_eig<float>(s, A, lda, nullptr, w.Zd, s, w.ql, status_dev, st))) return e;
+  if ((e = ql_eig<float>(s, A, lda, nullptr, w.Zd, s, w.ql, status_dev, st, true))) return e;
   if ((e = convert2d(s, s, w.Zd, s, EIG_F64, w.X, s, EIG_DF64, st))) return e;
   if ((e = convert2d(s, s, A, lda, EIG_F64, w.Add, s, EIG_DF64, st))) return e;
   // stage 2: Ogita-Aishima refinement.  Inside a cluster the columns of X

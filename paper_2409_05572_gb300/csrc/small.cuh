@@ -13,15 +13,20 @@ cudaError_t chol_rinv(int w, int64_t nrows, const double* G, int64_t ldg, double
                       double unit_round = 1.1102230246251565e-16);
 
 // A = Z diag(lam) Z^T, lam ascending, Z float64 (leading dimension ldz):
-// float32 Householder + implicit QL, then Ogita-Aishima refinement in
-// double-float and Jacobi on clusters (k_syev.cu).  work of syev_work_bytes(s)
-// bytes; *status_dev: 0 ok, 1 QL did not converge, 2 rotation list overflow,
-// 3 a cluster of nearly equal eigenvalues is larger than the Jacobi stage takes.
+// float32 Householder tridiagonalisation, bisection and inverse iteration,
+// then Ogita-Aishima refinement in double-float and Jacobi on clusters
+// (k_syev.cu).  work of syev_work_bytes(s) bytes; *status_dev: 0 ok, 3 a
+// cluster of nearly equal eigenvalues is larger than the Jacobi stage takes.
 size_t syev_work_bytes(int s);
 cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
                  int* status_dev, cudaStream_t st);
-// The same decomposition entirely in float64 (QL path, no refinement).
+// The same decomposition entirely in float64: Householder, bisection,
+// inverse iteration with Gram-Schmidt inside clusters (syev64), or the
+// sequential implicit QL chain (syev_qr64, a slow comparison path); work of
+// syev_qr64_work_bytes(s) bytes.
 size_t syev_qr64_work_bytes(int s);
+cudaError_t syev64(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
+                   int* status_dev, cudaStream_t st);
 cudaError_t syev_qr64(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
                       int* status_dev, cudaStream_t st);
 

@@ -202,16 +202,6 @@ namespace {
 
 constexpr int F_CHOL1 = 0, F_CHOL2 = 1, F_CHOL3 = 2, F_SYEV = 4, NFLAGS = 8;
 
-// EIG_SYEV=qr64 selects the all-float64 QL eigensolver (comparison path)
-bool use_qr64() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = std::getenv("EIG_SYEV");
-    v = (e && std::strcmp(e, "qr64") == 0) ? 1 : 0;
-  }
-  return v == 1;
-}
-
 int debug_level() {
   static int v = -1;
   if (v < 0) {
@@ -564,8 +554,10 @@ struct Ops {
     if (rc) return rc;
     const double sw = S.width;
     Prof p(h, EIG_K_SYEV, (4.0 / 3.0 + 6.0) * sw * sw * sw, 0.0);
-    if (use_qr64())
-      CK(syev_qr64(S.width, h->Gp, S.width, h->lamd, h->Z, S.width, h->syevw, h->flags + F_SYEV, st()));
+    // float64 form: the float64 eigensolver; double-float and mixed forms:
+    // the float32 decomposition refined in double-float
+    if constexpr (AU == Arith::F64)
+      CK(syev64(S.width, h->Gp, S.width, h->lamd, h->Z, S.width, h->syevw, h->flags + F_SYEV, st()));
     else
       CK(syev(S.width, h->Gp, S.width, h->lamd, h->Z, S.width, h->syevw, h->flags + F_SYEV, st()));
     if (debug_level() >= 2) compare_syev(S.width);
@@ -1344,7 +1336,8 @@ size_t footprint_bytes(int64_t n, int64_t nnz, int nev, int k_max, int nes, int 
   b += 8 * (smax * smax * 2 + cq * cq * 2 + 2 * cq + smax * k_max + smax * (2 * k_max + 1) + 4 * smax);
   b += 8 * (size_t(2) * num_sms() * 4 * 64 * 64 + smax * smax + 4096);
   b += 8 * residual_scratch_elems(n, k_max);
-  b += syev_work_bytes(int(smax)) + hl_work_bytes(int(smax), k_max, 0) + 8 * smax * smax;
+  b += std::max(syev_work_bytes(int(smax)), syev_qr64_work_bytes(int(smax))) + hl_work_bytes(int(smax), k_max, 0) +
+       8 * smax * smax;
   if (gram_tc) {
     const int ns = tc_slices(form);
     b += 2 * tc_operand_bytes(ns, n, int(smax)) + tc_slice_bytes(ns, int64_t(smax), 2 * k_max + 1) +
@@ -1558,7 +1551,7 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
   AL(h->xn, sizeof(double) * smax);
   AL(h->rn, sizeof(double) * smax);
   AL(h->Cs, sizeof(double) * size_t(smax) * (2 * k_max + 1));
-  AL(h->syevw, use_qr64() ? std::max(syev_work_bytes(smax), syev_qr64_work_bytes(smax)) : syev_work_bytes(smax));
+  AL(h->syevw, std::max(syev_work_bytes(smax), syev_qr64_work_bytes(smax)));
   AL(h->hlw, hl_work_bytes(smax, k_max, 0) + sizeof(double) * size_t(smax) * smax);
   AL(h->flags, sizeof(int) * NFLAGS);
   AL(h->V, sizeof(double) * size_t(n) * nev);

@@ -32,6 +32,12 @@ def test_reference_arm_prints_the_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # a step is a timed iteration of the oracle's own solve; the solve time is
+    # an explicit projection of it, and a step fits in the run's wall time
+    pr = d["projection"]
+    assert pr["iterations_per_solve"] > 0
+    assert abs(d["value"] - 64 / (d["ms_per_step"] / 1e3 * pr["iterations_per_solve"])) <= 1e-9 * d["value"]
+    assert d["ms_per_step"] / 1e3 * (d["steps"] + d["warmup"]) <= d["wall_s"] + 1e-6
 
 
 def test_gpu_arm_fails_loudly_without_a_gpu():

@@ -270,6 +270,48 @@ def test_syev_parity(s, kind):
     assert np.linalg.norm(A @ Z_h - Z_h * lam_h) <= 1e-13 * nA * s
 
 
+def projected_like_matrix(seed=0):
+    """A Rayleigh-Ritz matrix of the shape a float64 LOBPCG solve of the
+    128^3 Dirichlet Laplacian meets after soft locking (s = 233): a diagonal
+    block of 69 locked Ritz values equal to the lowest closed-form
+    eigenvalues (exact multiplicities 3 and 6), coupled only through a dense
+    rotation of the remaining 164 values, which contain near-degenerate
+    triples spaced at float32 resolution (3e-7 against ||A|| of 7) and a
+    spread up to 7.  Returns A and its exact eigenvalues."""
+    rng = np.random.default_rng(seed)
+    ax = 4 * np.sin(np.arange(1, 12) * np.pi / 258) ** 2
+    lap = np.sort(np.add.outer(np.add.outer(ax, ax), ax).ravel())
+    locked = lap[:69]
+    mid = list(lap[69:99])
+    for c in np.linspace(0.018, 0.03, 12):
+        mid += [c, c + 3e-7, c + 7e-7]
+    top = list(rng.uniform(0.05, 6.9, 164 - len(mid) - 1)) + [6.93]
+    rest = np.array(mid + top)
+    Q, _ = np.linalg.qr(rng.standard_normal((rest.size, rest.size)))
+    A = np.zeros((233, 233))
+    A[:69, :69] = np.diag(locked)
+    A[69:, 69:] = (Q * rest) @ Q.T
+    A = 0.5 * (A + A.T)
+    return A, np.sort(np.concatenate([locked, rest]))
+
+
+def test_syev_degenerate_and_near_degenerate_clusters():
+    """Exactly repeated locked values next to near-degenerate triples: the
+    float64 eigensolver keeps every eigenpair to float64 accuracy (the float32
+    inverse iteration cannot separate triples spaced at its resolution and
+    lost orthogonality on such matrices)."""
+    A, exact = projected_like_matrix()
+    s = A.shape[0]
+    lam = torch.empty(s, dtype=torch.float64, device="cuda")
+    Z = torch.empty(s, s, dtype=torch.float64, device="cuda")
+    L.eig_syev(s, dev(A), s, lam, Z, s)
+    lam_h, Z_h = lam.cpu().numpy(), Z.cpu().numpy()
+    nA = np.abs(exact).max()
+    assert np.abs(lam_h - exact).max() <= 1e-14 * nA
+    assert np.abs(Z_h.T @ Z_h - np.eye(s)).max() <= 1e-12
+    assert np.abs(A @ Z_h - Z_h * lam_h).max() <= 1e-13 * nA
+
+
 # ---------------------------------------------------------------------------
 # a10: improved Hetmaniuk-Lehoucq basis selection
 # ---------------------------------------------------------------------------
