@@ -280,7 +280,7 @@ int eig_syev(int s, const double* A, int64_t lda, double* lam, double* Z, int64_
   if (!A || !lam || !Z) return EIG_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Tmp work(st), flag(st);
-  if (work.alloc(syev_qr64_work_bytes(s)) || flag.alloc(16)) return EIG_ENOMEM;
+  if (work.alloc(syev64_work_bytes(s)) || flag.alloc(16)) return EIG_ENOMEM;
   if (cudaMemsetAsync(flag.p, 0, 16, st)) return EIG_ECUDA;
   if (syev64(s, A, lda, lam, Z, ldz, work.p, static_cast<int*>(flag.p), st)) return EIG_ECUDA;
   int hf = 0;

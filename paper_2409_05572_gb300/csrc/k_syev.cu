@@ -51,7 +51,7 @@ template <> struct RealT<float> {
 template <> struct RealT<double> {
   static __device__ __forceinline__ double eps() { return 2.220446049250313e-16; }
   static __device__ __forceinline__ double tiny() { return 2.2250738585072014e-308; }
-  static __device__ __forceinline__ double ortol() { return 1e-3; }
+  static __device__ __forceinline__ double ortol() { return 1e-9; }
   static __device__ __forceinline__ double big() { return 1e150; }
   static __device__ __forceinline__ double hyp(double a, double b) { return hypot(a, b); }
   static constexpr double lo = 1e-280, hi = 1e280;
@@ -289,8 +289,10 @@ __device__ __forceinline__ int sturm_count(int s, const R* d, const R* e2, R x, 
 }
 
 // lam[i] = i-th smallest eigenvalue of T (d, e; e[k] = T[k+1][k]) by
-// bisection on Sturm counts, one thread per eigenvalue, to an absolute
-// accuracy of eps ||T|| (eps of the working precision R)
+// multisection on Sturm counts: one warp per eigenvalue, the 32 lanes count
+// at 32 interior points of the current interval, which shrinks to the
+// sub-interval holding eigenvalue i (33 times shorter per round), until its
+// width is eps ||T|| (eps of the working precision R)
 template <typename R>
 __global__ void __launch_bounds__(128) bisect_kernel(int s, const R* __restrict__ dg, const R* __restrict__ eg,
                                                      R* __restrict__ lam) {
@@ -320,20 +322,26 @@ __global__ void __launch_bounds__(128) bisect_kernel(int s, const R* __restrict_
     bounds[3] = eps * tn;
   }
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= s) return;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (i >= s) return;  // whole warps leave together
   R lo = bounds[0], hi = bounds[1];
   const R pivmin = bounds[2], atol = bounds[3];
-  for (int it = 0; it < 200; ++it) {
-    const R mid = R(0.5) * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
+  for (int round = 0; round < 40; ++round) {
     if (hi - lo <= R(2) * eps * fmax(fabs(lo), fabs(hi)) + atol) break;
-    if (sturm_count<R>(s, d, e2, mid, pivmin) > i)
-      hi = mid;
-    else
-      lo = mid;
+    const R step = (hi - lo) / R(33);
+    const R x = lo + step * R(lane + 1);
+    const bool above = x < hi && sturm_count<R>(s, d, e2, x, pivmin) > i;
+    const unsigned m = __ballot_sync(0xffffffffu, above);
+    // lanes 0 .. f-1 count at most i (eigenvalue i lies above their points)
+    const int f = m ? __ffs(m) - 1 : 32;
+    const R nlo = f > 0 ? __shfl_sync(0xffffffffu, x, f - 1) : lo;
+    const R nhi = f < 32 ? __shfl_sync(0xffffffffu, x, f < 32 ? f : 0) : hi;
+    if (!(nhi - nlo < hi - lo)) break;  // no progress at this resolution
+    lo = nlo;
+    hi = nhi;
   }
-  lam[i] = R(0.5) * (lo + hi);
+  if (lane == 0) lam[i] = R(0.5) * (lo + hi);
 }
 
 // Shifts equal to the eigenvalues: every vector starts from its own
@@ -343,10 +351,10 @@ __global__ void __launch_bounds__(128) bisect_kernel(int s, const R* __restrict_
 // eigenvalues toward the next distinct one).  Cluster starts: gap to the
 // previous eigenvalue at most ortol ||T||_1.  An inverse-iteration vector
 // errs by about eps ||T|| / gap in the direction of a neighbour at distance
-// gap, so pairs closer than ortol ||T|| are orthogonalised together: 1e-3 in
-// float64 (the rule of LAPACK's stein; cross-cluster coupling then stays near
-// eps / 1e-3), 1e-5 in float32 (the double-float refinement that follows
-// removes the remaining coupling).  Zero-pivot replacement eps ||T||_1.
+// gap: pairs closer than ortol ||T|| (1e-9 in float64, 1e-5 in float32) are
+// orthogonalised together, and the Ogita-Aishima refinement that follows
+// removes the coupling of the farther pairs.  Zero-pivot replacement
+// eps ||T||_1.
 //
 // Float32 cannot resolve eigenvalues whose gaps approach eps32 ||T||: when
 // three of them sit within that resolution, inverse iteration from every
@@ -691,7 +699,8 @@ static cudaError_t tri_invit(int s, QLWork<R>& w, double* lam, cudaStream_t st) 
   int* cstart = reinterpret_cast<int*>(w.rs + 2 * s + 64);
   unsigned char* piv = reinterpret_cast<unsigned char*>(w.ri);
   const unsigned nb = (unsigned)cdiv(s, 128);
-  bisect_kernel<R><<<nb, 128, 2 * size_t(s) * sizeof(R), st>>>(s, w.d, w.e, lamr); count_launches(1);
+  bisect_kernel<R><<<(unsigned)cdiv(s, 4), 128, 2 * size_t(s) * sizeof(R), st>>>(s, w.d, w.e, lamr);
+  count_launches(1);
   invit_prep_kernel<R><<<1, 32, 0, st>>>(s, w.d, w.e, lamr, sig, cstart, pert); count_launches(1);
   cudaFuncSetAttribute(cluster_cgs_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   for (int pass = 0; pass < 2; ++pass) {
@@ -757,17 +766,6 @@ cudaError_t syev_qr64(int s, const double* A, int64_t lda, double* lam, double* 
   return ql_eig<double>(s, A, lda, lam, Z, ldz, w, status_dev, st, false);
 }
 
-// Float64 eigensolver of the float64 form: float64 Householder
-// tridiagonalisation (cooperative kernel), bisection, inverse iteration and
-// Gram-Schmidt inside clusters in float64, float64 back-transformation; no
-// double-float refinement (it would cap the accuracy at about 2^-48).
-cudaError_t syev64(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
-                   int* status_dev, cudaStream_t st) {
-  if (s <= 0) return cudaSuccess;
-  Carver cv(work);
-  QLWork<double> w = ql_carve<double>(s, cv);
-  return ql_eig<double>(s, A, lda, lam, Z, ldz, w, status_dev, st, true);
-}
 
 // ---------------------------------------------------------------------------
 // stage 2: Ogita-Aishima refinement in double-float arithmetic
@@ -901,39 +899,42 @@ __global__ void eye_kernel(int s, double* __restrict__ Q) {
   if (idx < int64_t(s) * s) Q[idx] = (idx / s == idx % s) ? 1.0 : 0.0;
 }
 
+
+__device__ __forceinline__ double elem_value(const dd& x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ double elem_value(const double& x) { return x; }
+
 // Z(:, rank[j]) = X(:, j), lam_out[rank[j]] = lam[j]
-__global__ void permute_kernel(int s, const dd* __restrict__ X, const int* __restrict__ rank,
+template <typename T>
+__global__ void permute_kernel(int s, const T* __restrict__ X, const int* __restrict__ rank,
                                const double* __restrict__ lam, double* __restrict__ Z, int64_t ldz,
                                double* __restrict__ lam_out) {
   const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= int64_t(s) * s) return;
   const int i = int(idx / s), j = int(idx % s);
-  const dd x = X[idx];
-  Z[int64_t(i) * ldz + rank[j]] = (double)x.hi + (double)x.lo;
+  Z[int64_t(i) * ldz + rank[j]] = elem_value(X[idx]);
   if (i == 0) lam_out[rank[j]] = lam[j];
 }
 
+// refinement work for blocks of element type T (double-float or float64)
+template <typename T>
 struct RefWork {
-  QLWork<float> ql;
   double *Zd, *G, *S, *E, *Q, *lam, *scr;
-  dd *Add, *X, *X2, *AX, *Cs;
+  T *Add, *X, *X2, *AX, *Cs;
   int* cid;
   int* rank;
 };
 
+template <typename T>
 static size_t ref_bytes(int s) {
   const size_t ss = size_t(s) * s;
   const size_t scr = gram_scratch_elems(s, s, s, true);
-  return ql_work_bytes<float>(s) + 5 * (ss * 8 + 256) + (size_t(s) * 8 + 256) + (scr * 8 + 256) +
-         5 * (ss * sizeof(dd) + 256) + 2 * (size_t(s) * 4 + 256) + 1024;
+  return 5 * (ss * 8 + 256) + (size_t(s) * 8 + 256) + (scr * 8 + 256) + 5 * (ss * sizeof(T) + 256) +
+         2 * (size_t(s) * 4 + 256) + 1024;
 }
 
-size_t syev_work_bytes(int s) { return ref_bytes(s); }
-
-static RefWork ref_carve(int s, void* base) {
-  Carver cv(base);
-  RefWork w;
-  w.ql = ql_carve<float>(s, cv);
+template <typename T>
+static RefWork<T> ref_carve(int s, Carver& cv) {
+  RefWork<T> w;
   const size_t ss = size_t(s) * s;
   w.Zd = cv.take<double>(ss);
   w.G = cv.take<double>(ss);
@@ -942,82 +943,125 @@ static RefWork ref_carve(int s, void* base) {
   w.Q = cv.take<double>(ss);
   w.lam = cv.take<double>(s);
   w.scr = cv.take<double>(gram_scratch_elems(s, s, s, true));
-  w.Add = cv.take<dd>(ss);
-  w.X = cv.take<dd>(ss);
-  w.X2 = cv.take<dd>(ss);
-  w.AX = cv.take<dd>(ss);
-  w.Cs = cv.take<dd>(ss);
+  w.Add = cv.take<T>(ss);
+  w.X = cv.take<T>(ss);
+  w.X2 = cv.take<T>(ss);
+  w.AX = cv.take<T>(ss);
+  w.Cs = cv.take<T>(ss);
   w.cid = cv.take<int>(s);
   w.rank = cv.take<int>(s);
   return w;
 }
 
-static Blk<dd> sq(dd* p, int s) {
-  Blk<dd> b;
+size_t syev_work_bytes(int s) { return ql_work_bytes<float>(s) + ref_bytes<dd>(s) + 512; }
+size_t syev64_work_bytes(int s) { return ql_work_bytes<double>(s) + ref_bytes<double>(s) + 512; }
+
+template <typename T>
+static Blk<T> sq(T* p, int s) {
+  Blk<T> b;
   b.add(p, s, s);
   return b;
 }
 
-// G = X^T X, AX = A X, S = X^T A X for the current X (double-float)
-static cudaError_t oa_products(int s, RefWork& w, cudaStream_t st) {
+constexpr int dtype_of(Arith A) { return A == Arith::DF64 ? EIG_DF64 : EIG_F64; }
+
+// G = X^T X, AX = A X, S = X^T A X for the current X (arithmetic A)
+template <Arith A, typename T>
+static cudaError_t oa_products(int s, RefWork<T>& w, cudaStream_t st) {
   cudaError_t e;
-  if ((e = gram<Arith::DF64>(s, sq(w.X, s), sq(w.X, s), true, w.G, s, w.scr, st))) return e;
-  if ((e = convert2d(s, s, w.X, s, EIG_DF64, w.Zd, s, EIG_F64, st))) return e;
-  if ((e = stage_coef<Arith::DF64>(s, s, w.Zd, s, w.Cs, s, 1.0, st))) return e;
-  if ((e = update<Arith::DF64>(s, sq(w.Add, s), w.Cs, s, sq(w.AX, s), 0.0, st))) return e;
-  return gram<Arith::DF64>(s, sq(w.X, s), sq(w.AX, s), true, w.S, s, w.scr, st);
+  if ((e = gram<A>(s, sq(w.X, s), sq(w.X, s), true, w.G, s, w.scr, st))) return e;
+  if ((e = convert2d(s, s, w.X, s, dtype_of(A), w.Zd, s, EIG_F64, st))) return e;
+  if ((e = stage_coef<A>(s, s, w.Zd, s, w.Cs, s, 1.0, st))) return e;
+  if ((e = update<A>(s, sq(w.Add, s), w.Cs, s, sq(w.AX, s), 0.0, st))) return e;
+  return gram<A>(s, sq(w.X, s), sq(w.AX, s), true, w.S, s, w.scr, st);
 }
 
-cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
-                 int* status_dev, cudaStream_t st) {
-  if (s <= 0) return cudaSuccess;
-  RefWork w = ref_carve(s, work);
+// Ogita-Aishima refinement of the eigenvector estimate in w.X (s x s,
+// arithmetic A): `iters` corrections, clusters of Rayleigh quotients closer
+// than tau_rel max |lam| diagonalised by Jacobi before each correction and at
+// the end; eigenvalues ascending into lam, vectors into Z.  Inside a cluster
+// the columns of X only span an approximate invariant subspace, so before
+// each correction the cluster blocks of X^T A X are diagonalised and X
+// rotated: otherwise the off-cluster corrections use Rayleigh quotients that
+// are not eigenvalue estimates and the cluster subspace stops converging.
+template <Arith A, typename T>
+static cudaError_t refine(int s, RefWork<T>& w, int iters, double tau_rel, double* lam, double* Z, int64_t ldz,
+                          int* status_dev, cudaStream_t st) {
   const int64_t ss = int64_t(s) * s;
   const unsigned gb = (unsigned)cdiv(ss, 256);
   cudaError_t e;
-  // stage 1: float32 decomposition (eigenvectors sorted ascending into Zd)
-  if ((e = ql_eig<float>(s, A, lda, nullptr, w.Zd, s, w.ql, status_dev, st, true))) return e;
-  if ((e = convert2d(s, s, w.Zd, s, EIG_F64, w.X, s, EIG_DF64, st))) return e;
-  if ((e = convert2d(s, s, A, lda, EIG_F64, w.Add, s, EIG_DF64, st))) return e;
-  // stage 2: Ogita-Aishima refinement.  Inside a cluster the columns of X
-  // only span an approximate invariant subspace, so before each correction
-  // the cluster blocks of X^T A X are diagonalised (Jacobi) and X rotated:
-  // otherwise the off-cluster corrections use Rayleigh quotients that are not
-  // eigenvalue estimates and the cluster subspace stops converging.
-  const double tau_rel = 3e-6;
-  static int n_iters = -1;
-  if (n_iters < 0) {
-    const char* ev = std::getenv("EIG_OA_ITERS");  // debugging override
-    n_iters = ev ? std::atoi(ev) : OA_ITERS;
-  }
-  for (int it = 0; it < n_iters; ++it) {
-    if ((e = oa_products(s, w, st))) return e;
+  for (int it = 0; it < iters; ++it) {
+    if ((e = oa_products<A>(s, w, st))) return e;
     oa_lambda_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.G, w.S, w.lam); count_launches(1);
-    if (it == 0) cluster_kernel<<<1, 32, 0, st>>>(s, w.lam, tau_rel, w.cid, status_dev ? status_dev : w.ql.status); count_launches(1);
+    if (it == 0) {
+      cluster_kernel<<<1, 32, 0, st>>>(s, w.lam, tau_rel, w.cid, status_dev);
+      count_launches(1);
+    }
     eye_kernel<<<gb, 256, 0, st>>>(s, w.Q); count_launches(1);
     cluster_jacobi_kernel<<<s, 32, 0, st>>>(s, w.S, w.cid, w.Q, w.lam); count_launches(1);
-    if ((e = stage_coef<Arith::DF64>(s, s, w.Q, s, w.Cs, s, 1.0, st))) return e;
-    if ((e = update<Arith::DF64>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 0.0, st))) return e;
+    if ((e = stage_coef<A>(s, s, w.Q, s, w.Cs, s, 1.0, st))) return e;
+    if ((e = update<A>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 0.0, st))) return e;
     std::swap(w.X, w.X2);
-    if ((e = oa_products(s, w, st))) return e;
+    if ((e = oa_products<A>(s, w, st))) return e;
     oa_lambda_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.G, w.S, w.lam); count_launches(1);
     oa_e_kernel<<<gb, 256, 0, st>>>(s, w.G, w.S, w.lam, w.cid, w.E); count_launches(1);
     // X2 = X + X E
-    if ((e = cudaMemcpyAsync(w.X2, w.X, sizeof(dd) * ss, cudaMemcpyDeviceToDevice, st))) return e;
-    if ((e = stage_coef<Arith::DF64>(s, s, w.E, s, w.Cs, s, 1.0, st))) return e;
-    if ((e = update<Arith::DF64>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 1.0, st))) return e;
+    if ((e = cudaMemcpyAsync(w.X2, w.X, sizeof(T) * ss, cudaMemcpyDeviceToDevice, st))) return e;
+    if ((e = stage_coef<A>(s, s, w.E, s, w.Cs, s, 1.0, st))) return e;
+    if ((e = update<A>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 1.0, st))) return e;
     std::swap(w.X, w.X2);
   }
   // final: eigenvalues, cluster diagonalisation, ascending order
-  if ((e = oa_products(s, w, st))) return e;
+  if ((e = oa_products<A>(s, w, st))) return e;
   oa_lambda_kernel<<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.G, w.S, w.lam); count_launches(1);
+  if (iters == 0) {
+    cluster_kernel<<<1, 32, 0, st>>>(s, w.lam, tau_rel, w.cid, status_dev);
+    count_launches(1);
+  }
   eye_kernel<<<gb, 256, 0, st>>>(s, w.Q); count_launches(1);
   cluster_jacobi_kernel<<<s, 32, 0, st>>>(s, w.S, w.cid, w.Q, w.lam); count_launches(1);
-  if ((e = stage_coef<Arith::DF64>(s, s, w.Q, s, w.Cs, s, 1.0, st))) return e;
-  if ((e = update<Arith::DF64>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 0.0, st))) return e;
+  if ((e = stage_coef<A>(s, s, w.Q, s, w.Cs, s, 1.0, st))) return e;
+  if ((e = update<A>(s, sq(w.X, s), w.Cs, s, sq(w.X2, s), 0.0, st))) return e;
   rank_kernel<double><<<(unsigned)cdiv(s, 128), 128, 0, st>>>(s, w.lam, w.rank, nullptr); count_launches(1);
-  permute_kernel<<<gb, 256, 0, st>>>(s, w.X2, w.rank, w.lam, Z, ldz, lam); count_launches(1);
+  permute_kernel<T><<<gb, 256, 0, st>>>(s, w.X2, w.rank, w.lam, Z, ldz, lam); count_launches(1);
   return cudaGetLastError();
+}
+
+// Double-float and mixed forms: float32 decomposition, OA_ITERS double-float
+// refinement steps (clusters at 3e-6 max |lam|).
+cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
+                 int* status_dev, cudaStream_t st) {
+  if (s <= 0) return cudaSuccess;
+  Carver cv(work);
+  QLWork<float> ql = ql_carve<float>(s, cv);
+  RefWork<dd> w = ref_carve<dd>(s, cv);
+  int* stat = status_dev ? status_dev : ql.status;
+  cudaError_t e;
+  if ((e = ql_eig<float>(s, A, lda, nullptr, w.Zd, s, ql, stat, st, true))) return e;
+  if ((e = convert2d(s, s, w.Zd, s, EIG_F64, w.X, s, EIG_DF64, st))) return e;
+  if ((e = convert2d(s, s, A, lda, EIG_F64, w.Add, s, EIG_DF64, st))) return e;
+  return refine<Arith::DF64>(s, w, OA_ITERS, 3e-6, lam, Z, ldz, stat, st);
+}
+
+// Float64 form: float64 Householder tridiagonalisation, multisection
+// bisection, inverse iteration with Gram-Schmidt inside clusters of nearly
+// equal eigenvalues, back-transformation -- vectors accurate to about
+// eps ||A|| / gap -- then one float64 Ogita-Aishima step on the library's
+// float64 products, which squares that coupling away (clusters at 1e-10
+// max |lam| diagonalised by Jacobi).
+cudaError_t syev64(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
+                   int* status_dev, cudaStream_t st) {
+  if (s <= 0) return cudaSuccess;
+  Carver cv(work);
+  QLWork<double> ql = ql_carve<double>(s, cv);
+  RefWork<double> w = ref_carve<double>(s, cv);
+  int* stat = status_dev ? status_dev : ql.status;
+  cudaError_t e;
+  if ((e = ql_eig<double>(s, A, lda, nullptr, w.X, s, ql, stat, st, true))) return e;
+  if ((e = cudaMemcpy2DAsync(w.Add, sizeof(double) * s, A, sizeof(double) * lda, sizeof(double) * s, s,
+                             cudaMemcpyDeviceToDevice, st)))
+    return e;
+  return refine<Arith::F64>(s, w, 1, 1e-10, lam, Z, ldz, stat, st);
 }
 
 }  // namespace eig

@@ -20,11 +20,13 @@ cudaError_t chol_rinv(int w, int64_t nrows, const double* G, int64_t ldg, double
 size_t syev_work_bytes(int s);
 cudaError_t syev(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
                  int* status_dev, cudaStream_t st);
-// The same decomposition entirely in float64: Householder, bisection,
-// inverse iteration with Gram-Schmidt inside clusters (syev64), or the
-// sequential implicit QL chain (syev_qr64, a slow comparison path); work of
-// syev_qr64_work_bytes(s) bytes.
+// The same decomposition in float64: Householder, multisection bisection,
+// inverse iteration with Gram-Schmidt inside clusters and one float64
+// Ogita-Aishima step (syev64, work of syev64_work_bytes(s) bytes), or the
+// sequential implicit QL chain (syev_qr64, a slow comparison path, work of
+// syev_qr64_work_bytes(s) bytes).
 size_t syev_qr64_work_bytes(int s);
+size_t syev64_work_bytes(int s);
 cudaError_t syev64(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,
                    int* status_dev, cudaStream_t st);
 cudaError_t syev_qr64(int s, const double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* work,

@@ -783,7 +783,7 @@ int lob_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switch
       using SU = typename Pol<AU>::S;
       const int c = L.nnow + npn;
       Blk<T> Yn = cat(view<T>(Sn, ld, 0, L.nnow), view<T>(Sn, ld, k, npn));
-      if (AU == Arith::DF64 && h->tcU) {
+      if ((AU == Arith::DF64 || AU == Arith::F64) && h->tcU) {
         // tensor-core update: C = [Z(:, :nnow) | C_P] as one float64 s x c
         // matrix (the staging buffer holds smax x (2 k_max + 1) 8-byte values)
         double* Cm = static_cast<double*>(h->Cs);
@@ -1336,7 +1336,7 @@ size_t footprint_bytes(int64_t n, int64_t nnz, int nev, int k_max, int nes, int 
   b += 8 * (smax * smax * 2 + cq * cq * 2 + 2 * cq + smax * k_max + smax * (2 * k_max + 1) + 4 * smax);
   b += 8 * (size_t(2) * num_sms() * 4 * 64 * 64 + smax * smax + 4096);
   b += 8 * residual_scratch_elems(n, k_max);
-  b += std::max(syev_work_bytes(int(smax)), syev_qr64_work_bytes(int(smax))) + hl_work_bytes(int(smax), k_max, 0) +
+  b += std::max(syev_work_bytes(int(smax)), syev64_work_bytes(int(smax))) + hl_work_bytes(int(smax), k_max, 0) +
        8 * smax * smax;
   if (gram_tc) {
     const int ns = tc_slices(form);
@@ -1551,7 +1551,7 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
   AL(h->xn, sizeof(double) * smax);
   AL(h->rn, sizeof(double) * smax);
   AL(h->Cs, sizeof(double) * size_t(smax) * (2 * k_max + 1));
-  AL(h->syevw, std::max(syev_work_bytes(smax), syev_qr64_work_bytes(smax)));
+  AL(h->syevw, std::max(syev_work_bytes(smax), syev64_work_bytes(smax)));
   AL(h->hlw, hl_work_bytes(smax, k_max, 0) + sizeof(double) * size_t(smax) * smax);
   AL(h->flags, sizeof(int) * NFLAGS);
   AL(h->V, sizeof(double) * size_t(n) * nev);
