@@ -42,35 +42,42 @@ __device__ __forceinline__ float small_int_float(int d) {  // exact for |d| < 2^
 
 // the NS prescaled slices s[q] = d_q 2^(-8 q) of one float64 bit pattern
 // against a chunk whose largest biased exponent is emax (emax == 0: zero
-// chunk).  Generic in NS: F = x 2^(8 NS - 1 - e).
+// chunk).  Generic in NS: F = x 2^(8 NS - 1 - e), |F| < 2^(8 NS - 1).  The
+// balanced base-256 digits of F are read off G = F + 0x80...80 (0x80 in each
+// of the NS - 1 low bytes): low byte q of G is d + 128 for the balanced digit
+// d at that position (the carries of the balanced representation are exactly
+// those of the biased sum), and G >> 8 (NS - 1) is the top digit.
 template <int NS>
 __device__ __forceinline__ void cut_bits(unsigned long long bits, int emax, float* s) {
+  static_assert(NS >= 2 && NS <= 7, "digit positions within 64 bits");
+  // branch-free (selects only), so that the independent cuts of a thread
+  // interleave
   const int E = int((bits >> 52) & 0x7FF);
+  const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = E - emax + 8 * NS - 54;      // <= 2
+  const int ls = sh > 0 ? sh : 0;             // left shift
+  const int rs = sh < 0 ? min(-sh, 63) : 0;   // right shift, rounding half away from zero
+  const unsigned long long half = rs > 0 ? (1ull << max(rs - 1, 0)) : 0ull;
+  unsigned long long u = ((m + half) >> rs) << ls;
+  u = (E == 0 || emax == 0 || sh <= -60) ? 0ull : u;
+  const long long F = (bits >> 63) ? -static_cast<long long>(u) : static_cast<long long>(u);
+  constexpr unsigned long long BIAS = 0x8080808080808080ull >> (8 * (9 - NS));  // NS - 1 bytes of 0x80
+  const unsigned long long G = static_cast<unsigned long long>(F) + BIAS;
+  const uint32_t lo = static_cast<uint32_t>(G), hi = static_cast<uint32_t>(G >> 32);
+#pragma unroll
+  for (int q = NS - 1; q >= 1; --q) {
+    const int pos = NS - 1 - q;  // byte position of digit q
+    const uint32_t byte = pos < 4 ? (lo >> (8 * pos)) & 255u : (hi >> (8 * (pos - 4))) & 255u;
+    // (2^23 + 2^22 + byte - 128) - (2^23 + 2^22) = d, exact; times 2^(-8 q)
+    const float sc = __int_as_float((127 - 8 * q) << 23);
+    s[q] = fmaf(__int_as_float(0x4B400000 - 128 + int(byte)), sc, -12582912.0f * sc);
+  }
+  const int top = static_cast<int>(static_cast<long long>(G) >> (8 * (NS - 1)));
+  s[0] = small_int_float(top);
   if (E == 0x7FF) {  // infinity or NaN: poison the product
 #pragma unroll
     for (int q = 0; q < NS; ++q) s[q] = __int_as_float(0x7fc00000);
-    return;
   }
-  long long F = 0;
-  if (E != 0 && emax != 0) {
-    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = E - emax + 8 * NS - 54;
-    unsigned long long u;
-    if (sh >= 0)
-      u = m << sh;  // sh <= 2 (NS = 7)
-    else if (sh > -60)
-      u = (m + (1ull << (-sh - 1))) >> (-sh);
-    else
-      u = 0;
-    F = (bits >> 63) ? -static_cast<long long>(u) : static_cast<long long>(u);
-  }
-#pragma unroll
-  for (int q = NS - 1; q >= 1; --q) {
-    const int d = ((static_cast<int>(F) + 128) & 255) - 128;
-    s[q] = small_int_float(d) * pow2(-8 * q);
-    F = (F - d) >> 8;
-  }
-  s[0] = small_int_float(static_cast<int>(F));
 }
 
 // the six prescaled slices of one double-float value times `scale` (a power

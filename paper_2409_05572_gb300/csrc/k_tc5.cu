@@ -88,6 +88,9 @@ template <int NS, int BN> struct Cfg {
   static constexpr uint32_t SET_COLS = uint32_t(NS * BN);
   static constexpr int GRP = 256 / BN;                       // B slices per MMA (N <= 256)
   static constexpr int COLS_T = BN / 2;                      // columns per flush thread
+  // columns per TMEM read of a flush thread: 8 when the triple-float
+  // accumulators of 32 columns leave no room for 16-column reads
+  static constexpr int SUBW = (NS == 7 && BN == 64) ? 8 : 16;
   static_assert(NSETS * SET_COLS <= 512, "TMEM");
 };
 constexpr uint32_t TMEM_COLS = 512;
@@ -217,19 +220,32 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
       : "r"(taddr)
       : "memory");
 }
+// 8 consecutive TMEM columns of this thread's lane of one level accumulator
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// the NS level accumulators (BN columns apart), 16 columns each, one wait
-template <int NS, int BN>
-__device__ __forceinline__ void tmem_ld_levels(uint32_t taddr, float (*v)[16]) {
-  uint32_t r[NS][16];
+// the NS level accumulators (BN columns apart), SW = 16 or 8 columns each,
+// one wait
+template <int NS, int BN, int SW>
+__device__ __forceinline__ void tmem_ld_levels(uint32_t taddr, float (*v)[SW]) {
+  uint32_t r[NS][SW];
 #pragma unroll
-  for (int l = 0; l < NS; ++l) tmem_ld16(taddr + uint32_t(BN * l), r[l]);
+  for (int l = 0; l < NS; ++l) {
+    if constexpr (SW == 16)
+      tmem_ld16(taddr + uint32_t(BN * l), r[l]);
+    else
+      tmem_ld8(taddr + uint32_t(BN * l), r[l]);
+  }
   tmem_wait_ld();
 #pragma unroll
   for (int l = 0; l < NS; ++l)
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[l][i] = __uint_as_float(r[l][i]);
+    for (int i = 0; i < SW; ++i) v[l][i] = __uint_as_float(r[l][i]);
 }
 
 // accumulators: double-float (NS = 6) and triple-float (NS = 7)
@@ -431,21 +447,22 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(const __grid_constant__
         if (!(ok = mbar_wait(smem_u32(&bar_accf[set]), uint32_t(use & 1), abort, wait_ns))) break;
         fence_after();
 #pragma unroll
-        for (int sub = 0; sub < CT / 16; ++sub) {
-          float v[NS][16];
-          tmem_ld_levels<NS, BN>(trow + uint32_t(set) * C::SET_COLS + uint32_t(16 * sub), v);
-          if (sub == CT / 16 - 1) {  // levels read: the issuer may refill this set
+        constexpr int SW = C::SUBW;
+        for (int sub = 0; sub < CT / SW; ++sub) {
+          float v[NS][SW];
+          tmem_ld_levels<NS, BN, SW>(trow + uint32_t(set) * C::SET_COLS + uint32_t(SW * sub), v);
+          if (sub == CT / SW - 1) {  // levels read: the issuer may refill this set
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&bar_acce[set]));
           }
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
+          for (int j = 0; j < SW; ++j) {
             float a[NS];
 #pragma unroll
             for (int l = 0; l < NS; ++l) a[l] = v[l][j];
-            const float fb = __shfl_sync(0xffffffffu, fbl, 16 * sub + j);
-            flush_one(master[16 * sub + j], a, fa * fb);
+            const float fb = __shfl_sync(0xffffffffu, fbl, SW * sub + j);
+            flush_one(master[SW * sub + j], a, fa * fb);
           }
         }
       }
@@ -611,14 +628,18 @@ cudaError_t slice_tmap(CUtensorMap* m, const void* buf, int ns, int64_t K, int64
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// tile width of each format's product (see the head of this file)
-template <int NS> constexpr int bn_of() { return NS == 6 ? 64 : 32; }
+// tile width of each product (see the head of this file): 128 x 64 for the
+// double-float products and the float64 Grams, 128 x 32 with two alternating
+// TMEM sets for the float64 updates (measured at n = 2^21: the float64 Gram
+// 384 x 384 takes 16.5 ms with 64-wide tiles against 19.8 ms, the update
+// 384 -> 256 24.4 ms against 23.4 ms)
+template <int MODE, int NS> constexpr int bn_of() { return (NS == 6 || MODE == 0) ? 64 : 32; }
 
 template <int NS>
 cudaError_t gram_launch(int64_t n, int a, int b, const void* slu, const void* slv, bool sym, double* scratch, int ns,
                         cudaStream_t st, const int* gate, int withhold, uint64_t wait_ns) {
   using T = ElemT<NS>;
-  constexpr int BN = bn_of<NS>();
+  constexpr int BN = bn_of<0, NS>();
   cudaError_t e = set_smem5<0, NS, BN, T>();
   if (e != cudaSuccess) return e;
   const int64_t nkb = nkb_of(n);
@@ -640,7 +661,7 @@ cudaError_t gram_launch(int64_t n, int a, int b, const void* slu, const void* sl
 }  // namespace
 
 int tc5_gram_nsplit(int ns_slices, int64_t n, int a, int b, bool sym) {
-  const int bn = ns_slices == 6 ? bn_of<6>() : bn_of<7>();
+  const int bn = ns_slices == 6 ? bn_of<0, 6>() : bn_of<0, 7>();
   int ns = num_sms() / std::max(1, live_tiles(a, b, sym, bn));  // one CTA per SM, one wave
   const int64_t nch = cdiv(n, CH);
   if (ns > nch) ns = int(nch);
@@ -658,7 +679,7 @@ template <int NS, typename T>
 cudaError_t tc5_update(int64_t n, int s, int c, const void* slu, const void* slc, const Blk<T>& Y, double beta,
                        cudaStream_t st, const int* gate) {
   static_assert(std::is_same<T, ElemT<NS>>::value, "slice count and element type disagree");
-  constexpr int BN = bn_of<NS>();
+  constexpr int BN = bn_of<1, NS>();
   cudaError_t e = set_smem5<1, NS, BN, T>();
   if (e != cudaSuccess) return e;
   const int64_t nkb = nkb_of(s);
