@@ -21,8 +21,8 @@
  *    dimension ld (in elements, ld >= w) is at p[i*ld + j].
  *  - Element formats (dtype): EIG_F64 float64; EIG_F32 float32; EIG_DF64
  *    "double-float": each element is a pair {float hi, float lo} (8 bytes,
- *    value hi + lo, |lo| <= ulp(hi)/2), the format the FP64 form keeps its
- *    blocks in so that all block arithmetic runs on the FP32 pipes.
+ *    value hi + lo, |lo| <= ulp(hi)/2), the block format of the double-float
+ *    form, whose block arithmetic runs on the FP32 pipes.
  *  - stream: a cudaStream_t (NULL = legacy default stream).  Low-level
  *    kernels are asynchronous on it; eig_solve() blocks until the solve ends.
  *  - Low-level entry points allocate their temporary device memory with
@@ -103,10 +103,10 @@ int eig_spmm(int64_t n, const int32_t *rowptr, const int32_t *colind, const void
  * only the upper tile triangle is computed and mirrored.  The reduction over
  * n is split across CTAs into float64 partial tiles held in temporary device
  * memory and summed in a fixed order (deterministic).  a, b <= 4096.
- * arith EIG_ARITH_DF64_TC takes EIG_DF64 blocks (U, V 8-byte aligned, any
- * leading dimension) and also holds the bf16 slices of U and V (12 bytes per
- * element) in temporary device memory; U == V with equal ldu, ldv and a == b
- * is sliced once. */
+ * arith EIG_ARITH_DF64_TC takes EIG_DF64 blocks and EIG_ARITH_F64_TC EIG_F64
+ * blocks (U, V 8-byte aligned, any leading dimension); both also hold the
+ * bf16 slices of U and V (12 / 14 bytes per element) in temporary device
+ * memory; U == V with equal ldu, ldv and a == b is sliced once. */
 int eig_gram(int64_t n, int a, int b, const void *U, int64_t ldu, const void *V, int64_t ldv,
              int arith, int sym, double *G, int64_t ldg, void *stream);
 
@@ -132,9 +132,11 @@ int eig_device_status(void);
 int eig_tc_wait_selftest(int arith, double wait_s, void *stream);
 
 /* ---- allocation-free Gram product (no counterpart in the paper) ---------
- * Same product, arguments and result as eig_gram, for callers that cannot
- * allocate device memory while they run: a serving process that gave all of
- * HBM to its own memory pool at start-up, or host code running where a
+ * The product of eig_gram for the CUDA-core arithmetics (EIG_ARITH_F64,
+ * _DF64, _F32, _C32; the tensor-core arithmetics, which need slice buffers,
+ * are rejected with EIG_EINVAL), same arguments and result, for callers that
+ * cannot allocate device memory while they run: a serving process that gave
+ * all of HBM to its own memory pool at start-up, or host code running where a
  * cudaMalloc / cudaFree (which can synchronise the device or fail under
  * memory pressure) is not allowed.  Instead of cudaMallocAsync it uses one
  * fixed scratch array of EIG_NOALLOC_SCRATCH_DOUBLES float64 elements
@@ -157,9 +159,9 @@ int eig_gram_noalloc(int64_t n, int a, int b, const void *U, int64_t ldu, const 
 /* ---- a4 / a11: block update (X <- S C_X, P <- S C_P, W <- W - Q C) ------
  * Y = U C + beta * Y.  U: n x s block, C: s x c float64 row-major (device,
  * leading dimension ldc), Y: n x c block; U and Y use the element format of
- * arith (EIG_DF64 blocks for EIG_ARITH_DF64_TC, which also holds the bf16
- * slices of U and C, 12 bytes per element, in temporary device memory).  Y
- * must not overlap U. */
+ * arith (EIG_DF64 blocks for EIG_ARITH_DF64_TC, EIG_F64 blocks for
+ * EIG_ARITH_F64_TC; both also hold the bf16 slices of U and C, 12 / 14 bytes
+ * per element, in temporary device memory).  Y must not overlap U. */
 int eig_block_update(int64_t n, int s, int c, const void *U, int64_t ldu, const double *C,
                      int64_t ldc, void *Y, int64_t ldy, double beta, int arith, void *stream);
 
@@ -208,9 +210,12 @@ typedef struct {
   int64_t n, nnz;
   const int32_t *rowptr;  /* n + 1 */
   const int32_t *colind;  /* nnz   */
-  const double *val;      /* nnz, float64 */
-  int on_device;          /* 1: the three arrays are device pointers (borrowed,
-                             must outlive the handle); 0: host (copied)     */
+  const void *val;        /* nnz values, float64 or float32 (val_dtype)   */
+  int on_device;          /* 1: the three arrays are device pointers (rowptr
+                             and colind borrowed, must outlive the handle;
+                             values copied); 0: host (copied)              */
+  int val_dtype;          /* EIG_F64 (0) or EIG_F32 (1): float32 values are
+                             widened to float64 once, at eig_create        */
 } eig_csr;
 
 #define EIG_NONE 0     /* fixed block width                                  */
@@ -222,13 +227,26 @@ typedef struct {
 #define EIG_CHEB_SI 1  /* Algorithm 1, Chebyshev filter for the solve         */
 #define EIG_SD 2       /* Algorithm 2 (steepest descent, no locking)          */
 
-#define EIG_FORM_DF64 0   /* blocks in double-float, FP32-pipe arithmetic      */
-#define EIG_FORM_F64 1    /* blocks in float64, native FP64 arithmetic          */
-#define EIG_FORM_MIXED 2  /* float32 blocks until r <= mixed_switch, then DF64 */
+/* Forms of a solve.  In every form the Cholesky factors, the projected
+ * eigenproblems and the final residual test run in float64, and the solve
+ * ends with a float64 Rayleigh-Ritz pass on the nev converged vectors.
+ *  EIG_FORM_F64:   float64 blocks; float64 SpMM and residuals; Gram products
+ *                  and block updates on the tensor cores (EIG_ARITH_F64_TC,
+ *                  gram_tc = 1) or on the float64 CUDA cores (gram_tc = 0);
+ *                  the float64 eigensolver of eig_syev.
+ *  EIG_FORM_DF64:  double-float blocks (about 48 significant bits); SpMM and
+ *                  residuals on the FP32 pipes; Gram and update on the tensor
+ *                  cores (EIG_ARITH_DF64_TC) or the FP32 pipes (gram_tc = 0);
+ *                  a float32 eigendecomposition refined in double-float.
+ *  EIG_FORM_MIXED: float32 blocks (compensated Gram) until r <= mixed_switch,
+ *                  then the double-float form. */
+#define EIG_FORM_DF64 0
+#define EIG_FORM_F64 1
+#define EIG_FORM_MIXED 2
 
 typedef struct {
   int algo;            /* EIG_LOBPCG                                          */
-  int form;            /* EIG_FORM_DF64                                       */
+  int form;            /* EIG_FORM_F64                                        */
   double tol;          /* 1e-10: stop when r^(j) <= tol (Eq. rk)              */
   int max_iter;        /* 1000                                                */
   int nes;             /* nev + 5; 0 = default                                */
@@ -248,12 +266,13 @@ typedef struct {
   int profile;         /* 1: time every kernel class with CUDA events          */
   int expand_powered;  /* EIG_CHEB_SI: 1 = "Powered X_drop" (Sec. 6.4): apply
                           the filter to the saved columns every iteration     */
-  int gram_tc;         /* 1 (default): double-float Gram products and block
-                          updates on the tensor cores (EIG_ARITH_DF64_TC,
-                          normwise ~2^-48 accuracy; slice buffers of 12 bytes
-                          per element for two n x (3 k_max + 1) and two
-                          n x (2 k_max + 1) operands); 0: FP32-pipe
-                          double-float products (componentwise ~2^-48)        */
+  int gram_tc;         /* 1 (default): Gram products and block updates of the
+                          float64 and double-float blocks on the tensor cores
+                          (EIG_ARITH_F64_TC / EIG_ARITH_DF64_TC; slice buffers
+                          of 14 / 12 bytes per element for two
+                          n x (3 k_max + 1) and two n x (2 k_max + 1)
+                          operands, see eig_footprint); 0: on the CUDA cores
+                          (float64 FMA / FP32-pipe double-float)             */
   int warm_first;      /* 0 (default): the warm-up gate (end of Sec. 3.2)
                           compares r^(j), the largest Eq. conv residual of the
                           first nev pairs, with r_warm; 1: it compares the
@@ -300,8 +319,9 @@ int eig_options_default(eig_options *opt);
 
 /* Validate and allocate a solver for the nev smallest eigenpairs with
  * initial/expanded width k_max (nex).  Requires 1 <= nev <= nes < k_max <= n,
- * opt->X0 != NULL and opt->normA > 0.  Device memory: about
- * (8 + 4 k_max) n 8-byte words plus the CSR (DF64 and F64 forms). */
+ * opt->X0 != NULL and opt->normA > 0.  Device memory: eig_footprint() bytes
+ * (for the 128^3 Laplacian with k_max = 128, about 90 GB in the float64 form
+ * with the tensor-core products); EIG_ENOMEM if it does not fit. */
 int eig_create(const eig_csr *A, int nev, int k_max, int strategy, const eig_options *opt,
                eig_handle **out);
 /* Run the solve from X0; blocks until done.  Returns EIG_OK or EIG_ENOTCONV

@@ -78,8 +78,8 @@ def cholqr_pass(W: np.ndarray):
 
 
 def cholqr2(W: np.ndarray) -> np.ndarray:
-    """"Orthogonalize" of Algorithms 1-3 (the paper names no method):
-    CholeskyQR2, i.e. two CholeskyQR passes; if the first pass needed the
+    """The orthogonalisation step of Algorithms 1-3, for which the paper
+    names no method: CholeskyQR2, i.e. two CholeskyQR passes; if the first pass needed the
     shift, a third pass follows (shifted CholeskyQR3)."""
     W1, shifted = cholqr_pass(W)
     if shifted:
@@ -89,9 +89,9 @@ def cholqr2(W: np.ndarray) -> np.ndarray:
 
 
 def orth_against(W: np.ndarray, Q: np.ndarray) -> np.ndarray:
-    """W <- W - Q (Q^T W) followed by orthogonalisation, as in
-    Algorithm 3 ("W <- W - [X,P]([X,P]^H W) and orthogonalize W"; the
-    expansion step does the same for S_drop against S).
+    """W <- W - Q (Q^T W) followed by orthogonalisation: Algorithm 3 projects
+    the residual block out of span([X, P]) and then orthonormalises it; the
+    expansion step treats S_drop against S the same way.
 
     Done twice (block classical Gram-Schmidt with reorthogonalisation, one
     CholeskyQR2 per pass) so that W is orthogonal to Q to working accuracy

@@ -6,7 +6,7 @@ Chebyshev filter X <- p_m(A) X (``blocks.cheb_filter``); the theory of the
 paper's Sec. 5 is stated for a power step X <- B X, which p_m(A) is.
 
 Readings: Ritz values are sorted algebraically ascending (the Anderson
-Hamiltonian is indefinite, so "ascending magnitude" would pick interior
+Hamiltonian is indefinite, so an ordering by magnitude would pick interior
 eigenvalues); the filter damps [a, b] with a = the largest Ritz value of the
 active block, b = an upper bound on the spectrum supplied by the caller,
 scaled to 1 at a0 = the smallest Ritz value.
@@ -23,11 +23,17 @@ from .strategy import Strategy
 def chebsi(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none",
            tol: float = 1e-10, max_iter: int = 1000, normA: float = 1.0,
            degree: int = 12, upper: float | None = None,
-           keep_ritz: bool = False, expand: str = "drop", **strategy_params) -> Result:
+           keep_ritz: bool = False, expand: str = "drop", observer=None,
+           **strategy_params) -> Result:
     """``expand``: "drop" appends the columns dropped at the last shrink;
-    "powered" (Sec. 6.4, "Powered X_drop") also applies the iteration's
+    "powered" (the powered X_drop variant of Sec. 6.4) also applies the iteration's
     operator -- here the same Chebyshev filter -- to the saved columns every
-    iteration, without orthogonalising them."""
+    iteration, without orthogonalising them.
+
+    ``observer(j, lam, nnow, drop_before, drop_after)``, if given, is called
+    after the filter step of iteration j with the Ritz values the filter was
+    built from, the active width, and copies of the saved columns before and
+    after that step (None while nothing is saved)."""
     n, nex = X0.shape
     assert nev <= nes < nex
     if upper is None:
@@ -53,8 +59,11 @@ def chebsi(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none",
         # X <- p_m(A) X replaces X <- (A - zeta I)^{-1} X.
         a, a0 = float(lam[nnow - 1]), float(lam[0])
         X = B.cheb_filter(A, X, degree, a, upper, a0)
+        before = None if (observer is None or Xdrop is None) else Xdrop.copy()
         if expand == "powered" and Xdrop is not None:
             Xdrop = B.cheb_filter(A, Xdrop, degree, a, upper, a0)
+        if observer is not None:
+            observer(j, lam.copy(), nnow, before, None if Xdrop is None else Xdrop.copy())
         if strat.ifexpand(j, nnow):
             X = np.hstack([X, Xdrop])
             nnow = nex

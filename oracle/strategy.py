@@ -12,9 +12,10 @@ Readings taken where the paper is silent or garbled:
   so an expansion happens when mod(j - j0 + js, je) = 0 and nnow = nes, and a
   shrink when mod(j - j0, je) = 0 and nnow > nes (js iterations after each
   expansion).
-* slope/slopek shrink: Algorithm 7 prints "j_l = j_e" but the text says a
-  fixed js after each expansion decides the shrink; the shrink fires when
-  j_l = js, j_l counting iterations since the last expansion.
+* slope/slopek shrink: the condition printed in Algorithm 7 compares j_l
+  with j_e, while the text ties the shrink to a fixed js after each
+  expansion; the shrink fires when j_l = js, j_l counting iterations since
+  the last expansion.
 * slope/slopek expand: Algorithm 7's test c_max / c > mu misbehaves for
   c <= 0, while the text expands when the residual grows; the test used is
   mu * c < c_max (same as c_max/c > mu for c > 0), with c_max the largest slope

@@ -41,7 +41,7 @@ class EigError(RuntimeError):
 
 class eig_csr(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("colind", C.c_void_p),
-                ("val", C.c_void_p), ("on_device", C.c_int)]
+                ("val", C.c_void_p), ("on_device", C.c_int), ("val_dtype", C.c_int)]
 
 
 class eig_options(C.Structure):
@@ -286,7 +286,7 @@ class Solver:
     the device) or a tuple of CUDA tensors (rowptr int32, colind int32,
     val float64) that must outlive the solver."""
 
-    def __init__(self, A, nev, k_max, strategy="fix", X0=None, normA=None, algo="lobpcg", form="df64",
+    def __init__(self, A, nev, k_max, strategy="fix", X0=None, normA=None, algo="lobpcg", form="f64",
                  tol=1e-10, max_iter=1000, nes=0, stream=None, **kw):
         lib = load()
         self._keep = []
@@ -296,15 +296,18 @@ class Solver:
             csr.n, csr.nnz = rp.numel() - 1, ci.numel()
             csr.rowptr, csr.colind, csr.val = rp.data_ptr(), ci.data_ptr(), va.data_ptr()
             csr.on_device = 1
+            csr.val_dtype = EIG_F32 if str(va.dtype) == "torch.float32" else EIG_F64
             self._keep += [rp, ci, va]
         else:
             rp = np.ascontiguousarray(A.indptr, dtype=np.int32)
             ci = np.ascontiguousarray(A.indices, dtype=np.int32)
-            va = np.ascontiguousarray(A.data, dtype=np.float64)
+            vdt = np.float32 if np.asarray(A.data).dtype == np.float32 else np.float64
+            va = np.ascontiguousarray(A.data, dtype=vdt)
             self._keep += [rp, ci, va]
             csr.n, csr.nnz = A.n, ci.size
             csr.rowptr, csr.colind, csr.val = rp.ctypes.data, ci.ctypes.data, va.ctypes.data
             csr.on_device = 0
+            csr.val_dtype = EIG_F32 if vdt == np.float32 else EIG_F64
         opt = eig_options()
         lib.eig_options_default(C.byref(opt))
         opt.algo = ALGOS[algo]
@@ -399,7 +402,7 @@ def _cuda_copy_d2d(dst, src, nbytes):
                                              _stream(None)))
 
 
-def make_options(algo="lobpcg", form="df64", tol=1e-10, max_iter=1000, nes=0, normA=None, **kw):
+def make_options(algo="lobpcg", form="f64", tol=1e-10, max_iter=1000, nes=0, normA=None, **kw):
     opt = eig_options()
     load().eig_options_default(C.byref(opt))
     opt.algo = ALGOS[algo]
@@ -433,9 +436,11 @@ class Server:
     def submit(self, A, X0, nev, k_max, strategy="fix", normA=None, **opts):
         rp = np.ascontiguousarray(A.indptr, dtype=np.int32)
         ci = np.ascontiguousarray(A.indices, dtype=np.int32)
-        va = np.ascontiguousarray(A.data, dtype=np.float64)
+        vdt = np.float32 if np.asarray(A.data).dtype == np.float32 else np.float64
+        va = np.ascontiguousarray(A.data, dtype=vdt)
         x0 = np.ascontiguousarray(X0, dtype=np.float64)
-        csr = eig_csr(A.n, ci.size, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0)
+        csr = eig_csr(A.n, ci.size, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0,
+                      EIG_F32 if vdt == np.float32 else EIG_F64)
         opt = make_options(normA=normA, **opts)
         opt.X0 = x0.ctypes.data
         opt.x0_on_device = 0

@@ -202,15 +202,16 @@ namespace {
 
 constexpr int F_CHOL1 = 0, F_CHOL2 = 1, F_CHOL3 = 2, F_SYEV = 4, NFLAGS = 8;
 
-int debug_level() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = std::getenv("EIG_DEBUG");
-    v = (e && e[0] >= '1' && e[0] <= '9') ? e[0] - '0' : 0;
-  }
-  return v;
-}
-bool debug_on() { return debug_level() >= 1; }
+// Diagnostics of a debug build (compiled with -DEIG_DEBUG_LEVEL=1 or 2;
+// the shipped library has level 0 and no diagnostic path): 1 prints the
+// block norms of every step and the residual test of every iteration, 2 also
+// re-solves every projected eigenproblem with the float64 QL path and prints
+// the largest eigenvalue difference.
+#ifndef EIG_DEBUG_LEVEL
+#define EIG_DEBUG_LEVEL 0
+#endif
+constexpr int debug_level() { return EIG_DEBUG_LEVEL; }
+constexpr bool debug_on() { return EIG_DEBUG_LEVEL >= 1; }
 
 // CUDA-event bracket of one kernel class when profiling is on
 cudaEvent_t ev_get(eig_handle* h) {
@@ -426,16 +427,6 @@ struct Ops {
                  worst / nrm, wi, l1[wi], l2[wi]);
     bool finite = true;
     for (int i = 0; i < s; ++i) finite = finite && std::isfinite(l1[i]);
-    static bool dumped = false;  // the first projected matrix that disagrees
-    if ((!finite || !(worst / nrm <= 1e-11)) && std::getenv("EIG_DUMP_AP") && !dumped) {
-      dumped = true;
-      FILE* f = std::fopen(std::getenv("EIG_DUMP_AP"), "wb");
-      if (f) {
-        std::fwrite(&s, sizeof(int), 1, f);
-        std::fwrite(ap.data(), sizeof(double), ap.size(), f);
-        std::fclose(f);
-      }
-    }
     cudaFree(dA);
     cudaFree(dl);
     cudaFree(dZ);
@@ -560,7 +551,7 @@ struct Ops {
       CK(syev64(S.width, h->Gp, S.width, h->lamd, h->Z, S.width, h->syevw, h->flags + F_SYEV, st()));
     else
       CK(syev(S.width, h->Gp, S.width, h->lamd, h->Z, S.width, h->syevw, h->flags + F_SYEV, st()));
-    if (debug_level() >= 2) compare_syev(S.width);
+    if constexpr (debug_level() >= 2) compare_syev(S.width);
     return EIG_OK;
   }
   int hl(int s, int nnow, int nlock, int npn) {
@@ -1105,25 +1096,59 @@ int promote(eig_handle* h, LState& L, int algo) {
   return EIG_OK;
 }
 
-// final float64 residual pass on V = X(:, :nev)
+// Final float64 pass of every form (the mixed form wins its accuracy back
+// here): V = X(:, 1:nev) in float64, orthonormalised by CholeskyQR2 in
+// float64, AV = A V by the float64 SpMM, a float64 Rayleigh-Ritz on span(V)
+// (V^T A V by the float64 Gram, the float64 eigensolver, V <- V Z and
+// AV <- AV Z by the float64 update), and the float64 residual norms of
+// Eq. conv with its Ritz values.  All on the CUDA cores in float64; the
+// work is n nev^2 per product, once per solve.
 int final_pass(eig_handle* h, const void* Xsrc, int src_dt) {
   const int nev = h->nev;
-  CK(convert2d(h->n, nev, Xsrc, h->LDS, src_dt, h->V, nev, EIG_F64, h->st));
-  // A V in float64 into the Wt buffer, residual norms with the Ritz values
-  double* AV = static_cast<double*>(h->Wt);
+  const int64_t n = h->n;
+  double* V = h->V;
+  double* tmp = static_cast<double*>(h->Sd);   // n x nev float64 (S_drop is free now)
+  double* AV = static_cast<double*>(h->Wt);    // n x nev float64
+  CK(cudaMemsetAsync(h->flags, 0, sizeof(int) * NFLAGS, h->st));
+  CK(convert2d(n, nev, Xsrc, h->LDS, src_dt, V, nev, EIG_F64, h->st));
+  auto blk = [&](double* p) {
+    Blk<double> b;
+    b.add(p, nev, nev);
+    return b;
+  };
+  // CholeskyQR2: V <- V R^{-1} twice
+  for (int pass = 0; pass < 2; ++pass) {
+    CK(eig::gram<Arith::F64>(n, blk(V), blk(V), true, h->Gp, nev, h->gscr, h->st));
+    CK(chol_rinv(nev, n, h->Gp, nev, h->Rinv, h->cholw, h->flags + F_CHOL1, h->st, nullptr,
+                 1.1102230246251565e-16));
+    CK(stage_coef<Arith::F64>(nev, nev, h->Rinv, nev, static_cast<double*>(h->Cs), nev, 1.0, h->st));
+    CK(eig::update<Arith::F64>(n, blk(V), static_cast<double*>(h->Cs), nev, blk(tmp), 0.0, h->st));
+    CK(cudaMemcpyAsync(V, tmp, sizeof(double) * size_t(n) * nev, cudaMemcpyDeviceToDevice, h->st));
+  }
   Csr<Arith::F64> c;
-  c.n = h->n;
+  c.n = n;
   c.rowptr = h->rowptr;
   c.colind = h->colind;
   c.val = h->val64;
-  CK(eig::spmm<Arith::F64>(c, nev, h->V, nev, AV, nev, 1.0, 0.0, nullptr, 0, 0.0, h->st));
-  CK(eig::residual<Arith::F64>(h->n, nev, h->V, nev, AV, nev, h->lamd, nullptr, nullptr, 0, h->xn, h->rn, h->rscr,
+  CK(eig::spmm<Arith::F64>(c, nev, V, nev, AV, nev, 1.0, 0.0, nullptr, 0, 0.0, h->st));
+  // Rayleigh-Ritz in float64: V^T A V = Z diag(lam) Z^T, V <- V Z, AV <- AV Z
+  CK(eig::gram<Arith::F64>(n, blk(V), blk(AV), true, h->Gp, nev, h->gscr, h->st));
+  CK(syev64(nev, h->Gp, nev, h->lamd, h->Z, nev, h->syevw, h->flags + F_SYEV, h->st));
+  CK(stage_coef<Arith::F64>(nev, nev, h->Z, nev, static_cast<double*>(h->Cs), nev, 1.0, h->st));
+  CK(eig::update<Arith::F64>(n, blk(V), static_cast<double*>(h->Cs), nev, blk(tmp), 0.0, h->st));
+  CK(cudaMemcpyAsync(V, tmp, sizeof(double) * size_t(n) * nev, cudaMemcpyDeviceToDevice, h->st));
+  CK(eig::update<Arith::F64>(n, blk(AV), static_cast<double*>(h->Cs), nev, blk(tmp), 0.0, h->st));
+  CK(eig::residual<Arith::F64>(n, nev, V, nev, tmp, nev, h->lamd, nullptr, nullptr, 0, h->xn, h->rn, h->rscr,
                                h->st));
   std::vector<double> xn(nev), rn(nev), lam(nev);
+  int fl[NFLAGS];
   CK(cudaMemcpyAsync(xn.data(), h->xn, sizeof(double) * nev, cudaMemcpyDeviceToHost, h->st));
   CK(cudaMemcpyAsync(rn.data(), h->rn, sizeof(double) * nev, cudaMemcpyDeviceToHost, h->st));
   CK(cudaMemcpyAsync(lam.data(), h->lamd, sizeof(double) * nev, cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(fl, h->flags, sizeof(fl), cudaMemcpyDeviceToHost, h->st));
   CK(cudaStreamSynchronize(h->st));
+  CK(cudaMemsetAsync(h->flags, 0, sizeof(int) * NFLAGS, h->st));
+  if (fl[F_CHOL1] == 2 || fl[F_SYEV] != 0) return EIG_EBREAKDOWN;
   h->lam = lam;
   h->resid.resize(nev);
   for (int i = 0; i < nev; ++i) h->resid[i] = std::sqrt(rn[i]) / (h->opt.normA * std::sqrt(xn[i]));
@@ -1186,7 +1211,7 @@ struct Stepper {
   int end(int st) {
     h->n_shrink = L.se.n_shrink;
     h->n_expand = L.se.n_expand;
-    int frc = final_pass(h, h->S[L.cur], phase == PH_F64 ? EIG_F64 : EIG_DF64);
+    int frc = final_pass(h, h->S[L.cur], phase == PH_F64 ? EIG_F64 : phase == PH_MIX32 ? EIG_F32 : EIG_DF64);
     finished = true;
     status = frc ? frc : st;
     return status;
@@ -1370,7 +1395,7 @@ int eig_options_default(eig_options* o) {
   if (!o) return EIG_EINVAL;
   std::memset(o, 0, sizeof(*o));
   o->algo = EIG_LOBPCG;
-  o->form = EIG_FORM_DF64;
+  o->form = EIG_FORM_F64;
   o->tol = 1e-10;
   o->max_iter = 1000;
   o->nes = 0;
@@ -1442,6 +1467,7 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
   *out = nullptr;
   const int nes = opt->nes > 0 ? opt->nes : nev + 5;
   if (A->n <= 0 || A->nnz < 0 || !A->rowptr || !A->colind || !A->val) return EIG_EINVAL;
+  if (A->val_dtype != EIG_F64 && A->val_dtype != EIG_F32) return EIG_EINVAL;
   if (nev < 1 || nes < nev || nes >= k_max || k_max > A->n) return EIG_EINVAL;
   if (strategy < EIG_NONE || strategy > EIG_SLOPEK) return EIG_EINVAL;
   if (!opt->X0 || !(opt->normA > 0.0) || opt->max_iter < 1 || !(opt->tol > 0.0)) return EIG_EINVAL;
@@ -1476,28 +1502,41 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
       return fail(EIG_ENOMEM);                                                    \
     }                                                                             \
   } while (0)
-  // CSR
+  // CSR; float32 values are staged in val32 and widened into val64
+  const bool v32 = A->val_dtype == EIG_F32;
+  void* vdst = nullptr;
+  if (v32) {
+    AL(h->val32, sizeof(float) * nnz);
+    vdst = h->val32;
+  }
+  AL(h->val64, sizeof(double) * nnz);
+  if (!v32) vdst = h->val64;
+  const size_t vbytes = (v32 ? sizeof(float) : sizeof(double)) * nnz;
   if (A->on_device) {
     h->rowptr = const_cast<int32_t*>(A->rowptr);
     h->colind = const_cast<int32_t*>(A->colind);
-    AL(h->val64, sizeof(double) * nnz);
-    if (cudaMemcpyAsync(h->val64, A->val, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess)
+    if (cudaMemcpyAsync(vdst, A->val, vbytes, cudaMemcpyDeviceToDevice, h->st) != cudaSuccess)
       return fail(EIG_ECUDA);
   } else {
     h->own_idx = true;
     AL(h->rowptr, sizeof(int32_t) * (n + 1));
     AL(h->colind, sizeof(int32_t) * nnz);
-    AL(h->val64, sizeof(double) * nnz);
     if (cudaMemcpyAsync(h->rowptr, A->rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, h->st) ||
         cudaMemcpyAsync(h->colind, A->colind, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, h->st) ||
-        cudaMemcpyAsync(h->val64, A->val, sizeof(double) * nnz, cudaMemcpyHostToDevice, h->st))
+        cudaMemcpyAsync(vdst, A->val, vbytes, cudaMemcpyHostToDevice, h->st))
       return fail(EIG_ECUDA);
   }
+  if (v32 && convert2d(1, nnz, h->val32, nnz, EIG_F32, h->val64, nnz, EIG_F64, h->st)) return fail(EIG_ECUDA);
   AL(h->valdd, sizeof(dd) * nnz);
   if (convert2d(1, nnz, h->val64, nnz, EIG_F64, h->valdd, nnz, EIG_DF64, h->st)) return fail(EIG_ECUDA);
-  if (opt->form == EIG_FORM_MIXED) {
+  if (opt->form == EIG_FORM_MIXED && !v32) {
     AL(h->val32, sizeof(float) * nnz);
     if (convert2d(1, nnz, h->val64, nnz, EIG_F64, h->val32, nnz, EIG_F32, h->st)) return fail(EIG_ECUDA);
+  } else if (opt->form != EIG_FORM_MIXED && v32) {
+    // the float32 staging copy is not part of the handle's footprint
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(EIG_ECUDA);
+    cudaFree(h->val32);
+    h->val32 = nullptr;
   }
   if (opt->precond) {
     AL(h->t64, sizeof(double) * n);
@@ -1678,7 +1717,7 @@ Request* find_req(eig_server* s, uint64_t t) {
 
 int admit(eig_server* s, Request* r) {
   if (cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking) != cudaSuccess) return EIG_ECUDA;
-  eig_csr A{r->n, r->nnz, r->rowptr.data(), r->colind.data(), r->val.data(), 0};
+  eig_csr A{r->n, r->nnz, r->rowptr.data(), r->colind.data(), r->val.data(), 0, EIG_F64};
   eig_options o = r->opt;
   o.X0 = r->X0.data();
   o.x0_on_device = 0;
@@ -1743,6 +1782,7 @@ int eig_server_create(const eig_server_opts* opts, eig_server** out) {
 int eig_submit(eig_server* s, const eig_csr* A, int nev, int k_max, int strategy, const eig_options* opt,
                uint64_t* ticket) {
   if (!s || !A || !opt || !ticket || A->on_device || !opt->X0 || opt->x0_on_device) return EIG_EINVAL;
+  if (A->val_dtype != EIG_F64 && A->val_dtype != EIG_F32) return EIG_EINVAL;
   const int nes = opt->nes > 0 ? opt->nes : nev + 5;
   if (A->n <= 0 || nev < 1 || nes < nev || nes >= k_max || k_max > A->n || !(opt->normA > 0.0)) return EIG_EINVAL;
   Request* r = new Request();
@@ -1751,7 +1791,13 @@ int eig_submit(eig_server* s, const eig_csr* A, int nev, int k_max, int strategy
   r->nnz = A->nnz;
   r->rowptr.assign(A->rowptr, A->rowptr + A->n + 1);
   r->colind.assign(A->colind, A->colind + A->nnz);
-  r->val.assign(A->val, A->val + A->nnz);
+  if (A->val_dtype == EIG_F32) {
+    const float* v = static_cast<const float*>(A->val);
+    r->val.assign(v, v + A->nnz);
+  } else {
+    const double* v = static_cast<const double*>(A->val);
+    r->val.assign(v, v + A->nnz);
+  }
   r->X0.assign(opt->X0, opt->X0 + size_t(A->n) * k_max);
   r->nev = nev;
   r->k_max = k_max;

@@ -492,6 +492,43 @@ def test_chebsi_anderson_parity(form, strategy):
     s.close()
 
 
+@pytest.fixture(scope="module")
+def c3_40():
+    """The Anderson workload's solver shape (nev = 128, k_max = 256,
+    Chebyshev degree 12, default strategy parameters) on a 40^3 lattice
+    (n = 64000) the oracle solves in about a minute."""
+    A = W.anderson_3d(40, seed=2)
+    X0 = W.gaussian_block(A.n, 256, 2)
+    ub, normA = W.gershgorin_bound(A), W.norm_estimate(A)
+    ref = o_chebsi(A, X0, 128, 133, "fix", tol=1e-9, normA=normA, degree=12, upper=ub, max_iter=400)
+    assert ref.converged
+    return A, X0, ub, normA, ref
+
+
+@pytest.mark.parametrize("form", ["f64", "mixed"])
+def test_c3_shape_chebsi_parity(c3_40, form):
+    A, X0, ub, normA, ref = c3_40
+    s = L.Solver(A, nev=128, k_max=256, strategy="fix", X0=X0, normA=normA, tol=1e-9, algo="chebsi",
+                 form=form, cheb_degree=12, cheb_upper=ub, max_iter=400)
+    out = s.solve()
+    V = s.V().cpu().numpy()
+    s.close()
+    assert out["status"] == 0
+    tol = 1e-8 if form == "mixed" else 1e-10
+    assert np.max(np.abs(out["lam"] - ref.lam) / np.abs(ref.lam)) <= tol
+    # Eq. conv at 1e-9 bounds ||Av - lam v|| / ||A|| by 2e-9 (|lam| <= ||A||)
+    R = B.spmm(A, V) - V * out["lam"]
+    rel = np.linalg.norm(R, axis=0) / (normA * np.linalg.norm(V, axis=0))
+    assert rel.max() <= 2e-9
+    assert np.max(np.abs(B.gram(V, V) - np.eye(128))) <= 1e-12
+    n_sh = sum(1 for _, e in ref.events if e == "shrink")
+    assert n_sh >= 1 and out["n_shrink"] >= 1
+    if form == "f64":
+        m = min(10, len(ref.history), len(out["history"]))
+        assert np.allclose(out["history"][:m], ref.history[:m], rtol=1e-6)
+        assert abs(out["iters"] - ref.iters) <= 1 and out["n_shrink"] == n_sh
+
+
 def test_solver_reuse_gives_identical_results(c1):
     A, normA, X0, _ = c1
     s = L.Solver(A, nev=10, k_max=20, strategy="fix", X0=X0, normA=normA, tol=1e-10)
@@ -499,6 +536,50 @@ def test_solver_reuse_gives_identical_results(c1):
     b = s.solve()
     assert np.array_equal(a["lam"], b["lam"]) and a["iters"] == b["iters"]
     s.close()
+
+
+def test_float32_csr_values_are_widened_exactly(c1):
+    """eig_csr.val_dtype = EIG_F32: the 2-D Laplacian's values are exact in
+    float32, so host and device float32 CSR give the float64 solve bit for
+    bit."""
+    A, normA, X0, _ = c1
+    ref = L.Solver(A, nev=10, k_max=20, strategy="fix", X0=X0, normA=normA, tol=1e-10)
+    r = ref.solve()
+    ref.close()
+    A32 = W.CSR(A.n, A.indptr, A.indices, A.data.astype(np.float32))
+    s = L.Solver(A32, nev=10, k_max=20, strategy="fix", X0=X0, normA=normA, tol=1e-10)
+    a = s.solve()
+    s.close()
+    dv = (torch.as_tensor(A.indptr, device="cuda"), torch.as_tensor(A.indices, device="cuda"),
+          torch.as_tensor(A.data.astype(np.float32), device="cuda"))
+    d = L.Solver(dv, nev=10, k_max=20, strategy="fix", X0=X0, normA=normA, tol=1e-10)
+    b = d.solve()
+    d.close()
+    for out in (a, b):
+        assert out["status"] == 0 and out["iters"] == r["iters"]
+        assert np.array_equal(out["lam"], r["lam"])
+
+
+@pytest.mark.parametrize("form", ["df64", "f64", "mixed"])
+def test_final_pass_is_a_float64_rayleigh_ritz(c1, form):
+    """Every form ends with float64 CholeskyQR2 of the converged block and a
+    float64 Rayleigh-Ritz on it: the returned vectors are orthonormal and the
+    returned values are the Ritz values of A on them, to float64 round-off,
+    whatever precision the iteration ran in."""
+    A, normA, X0, ex = c1
+    s = L.Solver(A, nev=10, k_max=20, strategy="fix", X0=X0, normA=normA, tol=1e-10, form=form)
+    out = s.solve()
+    assert out["status"] == 0
+    V = s.V().cpu().numpy()
+    s.close()
+    assert np.linalg.norm(V.T @ V - np.eye(10), 2) <= 1e-13
+    H = V.T @ (A.to_scipy() @ V)
+    H = (H + H.T) / 2
+    assert np.max(np.abs(np.linalg.eigvalsh(H) - out["lam"])) <= 1e-14 * normA
+    assert np.max(np.abs(H - np.diag(out["lam"]))) <= 1e-13 * normA
+    R = A.to_scipy() @ V - V * out["lam"]
+    want = np.linalg.norm(R, axis=0) / (normA * np.linalg.norm(V, axis=0))
+    assert np.allclose(want, out["resid"], rtol=1e-6, atol=1e-15)
 
 
 # ---------------------------------------------------------------------------

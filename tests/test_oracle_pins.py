@@ -493,6 +493,43 @@ def test_sd_matches_closed_form(strategy):
         assert any(e == "expand" for _, e in r.events)
 
 
+@pytest.mark.parametrize("expand", ["powered", "drop"])
+def test_chebsi_powered_drop_step_closed_form(expand):
+    """Sec. 6.4, powered X_drop: on a diagonal A every saved column is
+    multiplied, once per iteration, by the filter p_m(d_i) of that iteration
+    (the closed form T_m((d - c)/e) / T_m((a0 - c)/e) with a, a0 the largest
+    active and the smallest Ritz value); the plain variant leaves the saved
+    columns untouched.  Between two shrinks the saved block of an iteration is
+    the previous iteration's result, so the product of the filters is applied
+    without orthogonalisation."""
+    rng = np.random.default_rng(7)
+    d = np.sort(rng.uniform(0.0, 10.0, 60))
+    A = W.CSR(60, np.arange(61, dtype=np.int32), np.arange(60, dtype=np.int32), d)
+    X0 = rng.standard_normal((60, 12))
+    seen = []
+    r = chebsi(A, X0, 4, 8, "fix", tol=1e-12, normA=10.0, degree=6, upper=10.5, max_iter=40,
+               j_warm=2, r_warm=1e-1, je=5, js=1, expand=expand,
+               observer=lambda *a: seen.append(a))
+    shrinks = {j for j, e in r.events if e == "shrink"}
+    assert shrinks, r.events
+    steps = [t for t in seen if t[3] is not None]
+    assert len(steps) >= 3
+    m = 6
+    for j, lam, nnow, before, after in steps:
+        if expand == "drop":
+            assert np.array_equal(before, after)
+            continue
+        a, a0 = lam[nnow - 1], lam[0]
+        c, e = (a + 10.5) / 2, (10.5 - a) / 2
+        p = _cheb_T(m, (d - c) / e) / _cheb_T(m, np.array([(a0 - c) / e]))[0]
+        ref = p[:, None] * before
+        assert np.allclose(after, ref, rtol=1e-11, atol=1e-13 * np.abs(ref).max())
+    # chaining: without a shrink in between, a step starts from the last result
+    for (j0, _, _, _, after0), (j1, _, _, before1, _) in zip(steps, steps[1:]):
+        if j1 == j0 + 1 and j0 not in shrinks:
+            assert np.array_equal(before1, after0)
+
+
 def test_chebsi_powered_drop_matches_and_expands():
     A = W.anderson_3d(6, seed=2)
     ev = np.linalg.eigvalsh(A.to_scipy().toarray())
