@@ -80,6 +80,50 @@ __device__ __forceinline__ void cut_bits(unsigned long long bits, int emax, floa
   }
 }
 
+// Seven slices of two float64 values against a chunk with largest biased
+// exponent emax, packed as bf16 pairs: word[q] holds slice q of the first
+// value in its low half and of the second in its high half.  The same digits
+// as cut_bits<7>, computed with 32-bit pieces: t = mantissa 2^2 is shifted
+// right by emax - E >= 0 with rounding half away from zero (on the
+// magnitude), F = +- that, G = F + 0x808080808080.  A digit's float is
+// assembled from its byte with one byte permute (0x4B4000bb = 1.5 2^23 + bb),
+// then scaled and offset by one exact FMA; the bf16 halves are the high 16
+// bits of those exactly representable floats.  Infinite and NaN values are
+// handled per chunk by the caller.
+__device__ __forceinline__ uint32_t bf16_pair(float a, float b) {
+  return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+}
+__device__ __forceinline__ unsigned long long f64_biased_digits(unsigned long long bits, int emax) {
+  const uint32_t hi = static_cast<uint32_t>(bits >> 32);
+  const int E = int((hi >> 20) & 0x7FFu);
+  const int r2 = emax - E;                               // >= 0 inside the chunk
+  const unsigned long long t = ((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 2;
+  const int r1 = min(max(r2 - 1, 0), 63);
+  const unsigned long long v = t >> r1;
+  unsigned long long u = r2 > 0 ? (v + 1ull) >> 1 : v;  // |x| 2^(E - emax + 2 + 52 - 52) rounded
+  u = E == 0 ? 0ull : u;                                 // zero or subnormal
+  const unsigned long long F = (hi >> 31) ? 0ull - u : u;
+  return F + 0x808080808080ull;
+}
+__device__ __forceinline__ void cut2_f64(unsigned long long b0, unsigned long long b1, int emax, uint32_t* word) {
+  const unsigned long long G0 = f64_biased_digits(b0, emax), G1 = f64_biased_digits(b1, emax);
+  const uint32_t l0 = static_cast<uint32_t>(G0), h0 = static_cast<uint32_t>(G0 >> 32);
+  const uint32_t l1 = static_cast<uint32_t>(G1), h1 = static_cast<uint32_t>(G1 >> 32);
+  // digit q = 1 .. 6 sits in byte 6 - q of G: bytes 0..3 in the low word
+#pragma unroll
+  for (int q = 1; q < 7; ++q) {
+    const int pos = 6 - q;
+    const uint32_t sel = 0x7650u | uint32_t(pos & 3);
+    const float c1 = __int_as_float((127 - 8 * q) << 23);  // 2^(-8 q)
+    const float c2 = -12583040.0f * c1;                     // -(1.5 2^23 + 128) 2^(-8 q)
+    const float f0 = __int_as_float(int(__byte_perm(pos < 4 ? l0 : h0, 0x4B400000u, sel)));
+    const float f1 = __int_as_float(int(__byte_perm(pos < 4 ? l1 : h1, 0x4B400000u, sel)));
+    word[q] = bf16_pair(fmaf(f0, c1, c2), fmaf(f1, c1, c2));
+  }
+  const int t0 = int(h0) >> 16, t1 = int(h1) >> 16;      // top digits, |d| <= 128
+  word[0] = bf16_pair(small_int_float(t0), small_int_float(t1));
+}
+
 // the six prescaled slices of one double-float value times `scale` (a power
 // of two): rint of the scaled value, the remainder (exact by Sterbenz)
 // TwoSum-ed with the low part, times 256, six times
@@ -152,6 +196,15 @@ template <> struct SliceFmt<dd> {
   static __device__ __forceinline__ void cut(unsigned long long raw, float scale, float* s) {
     cut_dd(__uint_as_float(static_cast<uint32_t>(raw)), __uint_as_float(static_cast<uint32_t>(raw >> 32)), scale, s);
   }
+  static __device__ __forceinline__ void cut2(unsigned long long r0, unsigned long long r1, float scale,
+                                              uint32_t* word) {
+    float s0[NS], s1[NS];
+    cut(r0, scale, s0);
+    cut(r1, scale, s1);
+#pragma unroll
+    for (int q = 0; q < NS; ++q) word[q] = bf16_pair(s0[q], s1[q]);
+  }
+  static __device__ __forceinline__ bool poisoned(float) { return false; }
 };
 template <> struct SliceFmt<double> {
   static constexpr int NS = NS_F64;
@@ -170,6 +223,13 @@ template <> struct SliceFmt<double> {
   static __device__ __forceinline__ void cut(unsigned long long raw, int emax, float* s) {
     cut_bits<NS_F64>(raw, emax, s);
   }
+  static __device__ __forceinline__ void cut2(unsigned long long r0, unsigned long long r1, int emax,
+                                              uint32_t* word) {
+    cut2_f64(r0, r1, emax, word);
+  }
+  // a chunk holding an infinity or a NaN (largest exponent field all ones):
+  // its slices are NaN so that the products show it
+  static __device__ __forceinline__ bool poisoned(int emax) { return emax == 0x7FF; }
 };
 
 // Slicer squares: one 128-index chunk of K x 32 operand rows, 256 threads,
@@ -271,16 +331,29 @@ __global__ void __launch_bounds__(256) tc_slice_kernel(int64_t n, Blk<T> U, Layo
       }
     }
     __syncthreads();
-    // thread -> (K block g of 16 indices, operand row idx of the square)
+    // thread -> (K block g of 16 indices, operand row idx of the square);
+    // two halves of 8 K indices, each one 16-byte core-matrix row per slice
     const int g = t >> 5, idx = t & 31;
     const typename F::Prep pe = F::prep(sexp[idx]);
-    float v[16][NS];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) F::cut(COLS ? sd[(16 * g + i) * P + idx] : sd[idx * P + 16 * g + i], pe, v[i]);
+    const bool poison = F::poisoned(pe);
     const int64_t kb = (COLS ? a : b) * KBC + g;
     const int64_t orow = (COLS ? b : a) * SQ_M + idx;
 #pragma unroll
-    for (int q = 0; q < NS; ++q) store16<NS>(o.sl + o.block(q, kb), orow, v, q);
+    for (int h = 0; h < 2; ++h) {
+      uint32_t w[4][NS];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = 16 * g + 8 * h + 2 * i;
+        F::cut2(COLS ? sd[k * P + idx] : sd[idx * P + k], COLS ? sd[(k + 1) * P + idx] : sd[idx * P + k + 1], pe,
+                w[i]);
+      }
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        uint4 v = make_uint4(w[0][q], w[1][q], w[2][q], w[3][q]);
+        if (poison) v = make_uint4(0x7FC07FC0u, 0x7FC07FC0u, 0x7FC07FC0u, 0x7FC07FC0u);
+        *reinterpret_cast<uint4*>(o.sl + o.block(q, kb) + in_block(orow, 8 * h)) = v;
+      }
+    }
     __syncthreads();  // the buffer is refilled by the next issue
     buf ^= 1;
   }
