@@ -50,13 +50,10 @@ METRIC = "converged eigenpairs/s at 1e-8 residual vs fixed-block FP64; p50/p99 l
 UNIT = "eigenpairs/s"
 
 # DRAM traffic / algorithmic bytes of the tensor-core classes of the float64
-# form (slicing + product kernels), from one ncu capture of the current
-# kernels at n = 262,144 (384-column operands; the Gram class reads U once,
-# 0.805 GB; the update class reads U and writes Y, 1.342 GB): slicer
-# 0.806 GB read + 1.367 GB written, Gram product 1.416 GB read, update
-# product 1.414 GB read + 0.514 GB written.  Traffic grows with n.
-TC_TRAFFIC_RATIO = {"gram": (0.806 + 1.367 + 1.416) / 0.805,
-                    "update": (0.806 + 1.367 + 1.414 + 0.514) / 1.342}
+# form (slicing + product kernels), from an ncu capture of the current
+# kernels at n = 262,144; empty (traffic reported as null) until the
+# kernels that changed have been captured again.
+TC_TRAFFIC_RATIO = {}
 
 
 def peaks():
@@ -137,6 +134,10 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# options of the expansion variants of Sec. 6.4
+EXPAND_OPTS = {"drop": {}, "powered": {"expand_powered": 1}, "random": {"expand_random": 1, "seed": 2024}}
+
+
 def make_workload(name):
     if name == "c2":
         L = 128
@@ -155,7 +156,7 @@ def make_workload(name):
     if name == "c4":
         A = W.graph_laplacian(4_000_000, seed=3)
         return dict(A=A, nev=200, k_max=400, normA=W.norm_estimate(A), seed=3, tol=1e-8, algo="lobpcg",
-                    extra=dict(precond=1, deflate_ones=1),
+                    extra=dict(precond=1, deflate_ones=1, gram_tc=0),
                     desc=f"graph Laplacian, power-law degrees (exponent 2.5, mean 10), n={A.n}, nnz={A.nnz}, "
                          "nev=200 above the null vector, LOBPCG k_max=400 + Jacobi, residual 1e-8",
                     exact=None)
@@ -275,9 +276,12 @@ def cpu_baseline(wl, strategy, iters):
 
 def run_serving(args):
     """c5: open-loop replay of the Poisson request stream (seed 4) through the
-    serving loop (mixed form, strategy fix, residual 1e-8).  Requests are
-    submitted when their arrival time has passed; value = sum of nev /
-    makespan (first arrival to last completion); latency = completion - arrival."""
+    serving loop (mixed form by default, strategy fix, residual 1e-8).
+    Requests are submitted when their arrival time has passed; value = sum of
+    nev / makespan (first arrival to last completion); latency = completion -
+    arrival.  Unless --no-compare, the same requests are then solved one at a
+    time in the plain float64 form (eig_solve per request, in arrival order)
+    and reported beside it as `one_at_a_time_f64`."""
     import torch
     from paper_2409_05572_gb300 import _lib as L
     torch.cuda.set_device(0)
@@ -288,7 +292,7 @@ def run_serving(args):
         A = r.matrix()
         normA = W.dirichlet_norm(r.dims) + float(r.diag_shift.max())
         prepared.append((r, A, normA, W.gaussian_block(A.n, r.k_max, r.seed)))
-    opts = dict(form="mixed", tol=0.5e-8, max_iter=args.max_iter)
+    opts = dict(form=args.form, tol=0.5e-8, max_iter=args.max_iter)
     srv = L.Server(int(args.budget_gb * 2**30), args.max_active)
     clocks = Clocks(0)
     torch.cuda.synchronize()
@@ -319,15 +323,31 @@ def run_serving(args):
     ok = all(g["status"] == 0 and float(np.max(g["resid"])) <= 1e-8 for g, _ in done.values())
     line = {"metric": METRIC, "value": pairs / makespan, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
             "ms_per_step": makespan * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "mixed(f32->df64)", "data": "synthetic",
+            "dtype": "mixed(f32->df64)" if args.form == "mixed" else args.form, "data": "synthetic",
             "config": {"workload": f"serving stream: first {len(prepared)} of the Poisson(200/s) stream, seed 4; "
                                    "2D/3D Dirichlet Laplacian + U[0,1] diagonal, n log-uniform [1e4,1e6], "
-                                   "nev U{8..128}, k_max=2 nev; mixed LOBPCG + fix, residual 1e-8",
+                                   f"nev U{{8..128}}, k_max=2 nev; {args.form} LOBPCG + fix, residual 1e-8",
                        "budget_gb": args.budget_gb, "max_active": args.max_active},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
             "all_converged": bool(ok), "requests": len(done), "eigenpairs": int(pairs), "clocks": clk}
     srv.close()
+    if not args.no_compare:
+        # the same requests one at a time, plain float64, each solve on its own
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        per = []
+        for r, A, normA, X0 in prepared:
+            ts = time.perf_counter()
+            s = L.Solver(A, nev=r.nev, k_max=r.k_max, strategy="fix", X0=X0, normA=normA, form="f64",
+                         tol=0.5e-8, max_iter=args.max_iter)
+            o = s.solve()
+            s.close()
+            per.append((time.perf_counter() - ts, o["status"]))
+        tot = time.perf_counter() - t1
+        line["one_at_a_time_f64"] = {"value": pairs / tot, "unit": UNIT, "seconds": tot,
+                                     "all_converged": all(st == 0 for _, st in per),
+                                     "serving_speedup": (pairs / makespan) / (pairs / tot)}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -372,7 +392,7 @@ def run_kernel(args):
         flops = 2.0 * n * a * b
         nbytes = esz * n * (a + b)
     elif args.kernel == "spmm":
-        A = W.laplacian_3d(args.grid)
+        A = W.laplacian_3d(args.grid) if args.matrix == "laplacian" else W.graph_laplacian(args.n, seed=3)
         n = A.n
         rp = torch.as_tensor(A.indptr, device="cuda")
         ci = torch.as_tensor(A.indices, device="cuda")
@@ -421,7 +441,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--strategy", default="fix")
-    ap.add_argument("--form", default="f64", choices=["f64", "df64", "mixed"])
+    ap.add_argument("--form", default=None, choices=["f64", "df64", "mixed"],
+                    help="block format (default: f64; mixed for the serving stream c5)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the solves under the other strategies (fixed block, slope, slopek)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -429,8 +450,14 @@ def main():
     ap.add_argument("--requests", type=int, default=32, help="c5: requests replayed from the stream")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="c5: device memory for active solves")
     ap.add_argument("--max-active", type=int, default=64, help="c5: solves advanced per step")
-    ap.add_argument("--gram-tc", type=int, default=1, choices=[0, 1],
-                    help="1: Gram and update on the tensor cores (exact slices); 0: on the CUDA cores")
+    ap.add_argument("--gram-tc", type=int, default=None, choices=[0, 1],
+                    help="1: Gram and update on the tensor cores (exact slices); 0: on the CUDA cores "
+                         "(default 1, and 0 for c4, whose slice buffers would not fit in HBM)")
+    ap.add_argument("--expand", default="drop", choices=["drop", "powered", "random"],
+                    help="vectors appended at an expansion (Sec. 6.4): the saved ones, the saved ones "
+                         "filtered every iteration (Chebyshev SI only), fresh Gaussian ones")
+    ap.add_argument("--ablate-expand", action="store_true",
+                    help="also solve once with each other expansion variant of Sec. 6.4")
     ap.add_argument("--aggressive-warmup", action="store_true",
                     help="warm-up gate on the first pair's residual with r_warm = 1e-1 (the paper's closing "
                          "remarks) instead of r^(j) <= 1e-4")
@@ -445,10 +472,15 @@ def main():
     ap.add_argument("--b", type=int, default=384)
     ap.add_argument("--sym", action="store_true")
     ap.add_argument("--grid", type=int, default=128, help="--kernel spmm: 3D Laplacian grid side")
+    ap.add_argument("--matrix", default="laplacian", choices=["laplacian", "graph"],
+                    help="--kernel spmm: the 3D Laplacian (--grid) or the power-law graph Laplacian of "
+                         "the c4 workload with --n rows")
     ap.add_argument("--arith", default="f64_tc", choices=["df64", "df64_tc", "f64", "f64_tc", "f32", "c32"])
     args = ap.parse_args()
     if args.kernel:
         return run_kernel(args)
+    if args.form is None:
+        args.form = "mixed" if args.workload == "c5" else "f64"
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
@@ -478,9 +510,11 @@ def main():
     # stopping test of Eq. conv at tol/2 so that ||Av - lv|| / ||A|| <= tol holds
     algo = wl.get("algo", "lobpcg")
     extra = dict(wl.get("extra", {}))
-    extra["gram_tc"] = args.gram_tc
+    if args.gram_tc is not None:
+        extra["gram_tc"] = args.gram_tc
     if args.aggressive_warmup:
         extra.update(warm_first=1, r_warm=1e-1)
+    extra.update(EXPAND_OPTS[args.expand])
     solver = L.Solver((rp, ci, va), nev=nev, k_max=k, strategy=args.strategy, X0=X0d, normA=normA,
                       tol=0.5 * tol, form=args.form, stream=stream, profile=1, max_iter=args.max_iter,
                       algo=algo, **extra)
@@ -531,7 +565,8 @@ def main():
                                        else "6 slices, 21 pairs per double-float multiply-add)"))
                        if tc_on else "CUDA cores",
                        "l2": "inputs larger than L2 (each n x k block is 4.3 GB); no flush",
-                       "warmup_rule": "first pair, r_warm 1e-1" if args.aggressive_warmup else "r^(j), r_warm 1e-4"},
+                       "warmup_rule": "first pair, r_warm 1e-1" if args.aggressive_warmup else "r^(j), r_warm 1e-4",
+                       "expand": args.expand},
             "converged": bool(ok), "iters": last["iters"], "n_shrink": last["n_shrink"],
             "n_expand": last["n_expand"], "max_resid": float(np.max(last["resid"])),
             "max_rel_eig_err_vs_closed_form": eig_err, "clocks": clk}
@@ -614,6 +649,28 @@ def main():
         line["fixed_block"] = {"value": fb["value"], "unit": UNIT, "ms": fb["ms"], "iters": fb["iters"],
                                "converged": fb["converged"],
                                "speedup_of_shrink_expand": fb["ms"] / ms_step if fb["converged"] and ok else None}
+
+    if rank == 0 and args.ablate_expand:
+        # the vectors appended at an expansion (Sec. 6.4): each other variant
+        # once, same workload, strategy and form
+        var = {args.expand: {"ms": ms_step, "iters": last["iters"], "n_expand": last["n_expand"],
+                             "converged": bool(ok)}}
+        for name in ("drop", "powered", "random"):
+            if name in var or (name == "powered" and algo != "chebsi"):
+                continue
+            ex2 = dict(extra, expand_powered=0, expand_random=0, **EXPAND_OPTS[name])
+            other = L.Solver((rp, ci, va), nev=nev, k_max=k, strategy=args.strategy, X0=X0d, normA=normA,
+                             tol=0.5 * tol, form=args.form, stream=stream, max_iter=args.max_iter, algo=algo,
+                             **ex2)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fo = other.solve()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            var[name] = {"ms": e0.elapsed_time(e1), "iters": fo["iters"], "n_expand": fo["n_expand"],
+                         "converged": bool(fo["status"] == 0 and np.max(fo["resid"]) <= tol)}
+            other.close()
+        line["expand_variants"] = var
 
     if rank == 0 and not args.no_e2e:
         # end to end through the public API: host CSR + pinned host X0 in,

@@ -279,6 +279,17 @@ typedef struct {
                           residual of the first pair instead (the more
                           aggressive warm-up of the paper's closing remarks,
                           there with r_warm = 1e-1)                          */
+  int expand_random;   /* 0 (default): an expansion appends the columns saved
+                          at the last shrink (X_drop / S_drop); 1: the
+                          'Random' variant of Sec. 6.4 -- it appends as many
+                          fresh standard-normal columns instead, entry (i, j)
+                          of the e-th expansion's block drawn by
+                          Philox4x32-10 (counter (i mod 2^32, i / 2^32,
+                          j / 2, e), key = seed) and Box-Muller (cos for even
+                          j, sin for odd j) from the float64 uniforms
+                          (w0 2^21 + w1 / 2^11 + 1/2) 2^-53 and
+                          (w2 2^21 + w3 / 2^11) 2^-53 of its four words    */
+  uint64_t seed;       /* key of the 'Random' draws                          */
 } eig_options;
 
 /* kernel classes of the per-class statistics (eig_result.kstats) */

@@ -16,6 +16,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import blocks as B
+from .philox import gaussian_columns
 from .lobpcg import Result
 from .strategy import Strategy
 
@@ -23,12 +24,14 @@ from .strategy import Strategy
 def chebsi(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none",
            tol: float = 1e-10, max_iter: int = 1000, normA: float = 1.0,
            degree: int = 12, upper: float | None = None,
-           keep_ritz: bool = False, expand: str = "drop", observer=None,
+           keep_ritz: bool = False, expand: str = "drop", observer=None, seed: int = 0,
            **strategy_params) -> Result:
     """``expand``: "drop" appends the columns dropped at the last shrink;
     "powered" (the powered X_drop variant of Sec. 6.4) also applies the iteration's
     operator -- here the same Chebyshev filter -- to the saved columns every
-    iteration, without orthogonalising them.
+    iteration, without orthogonalising them; "random" (the 'Random' variant)
+    appends freshly drawn Gaussian columns (``philox.gaussian_columns`` with
+    ``seed``, block e at the e-th expansion) instead of the saved ones.
 
     ``observer(j, lam, nnow, drop_before, drop_after)``, if given, is called
     after the filter step of iteration j with the Ritz values the filter was
@@ -46,6 +49,7 @@ def chebsi(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none",
     X, AX = X @ Z, AX @ Z
     nnow = nex
     Xdrop = None
+    n_exp = 0
     res = Result(lam[:nev], X[:, :nev], False, 0)
 
     for j in range(1, max_iter + 1):
@@ -65,6 +69,9 @@ def chebsi(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none",
         if observer is not None:
             observer(j, lam.copy(), nnow, before, None if Xdrop is None else Xdrop.copy())
         if strat.ifexpand(j, nnow):
+            if expand == "random":
+                Xdrop = gaussian_columns(n, Xdrop.shape[1], seed, n_exp)
+            n_exp += 1
             X = np.hstack([X, Xdrop])
             nnow = nex
         X = B.cholqr2(X)

@@ -26,6 +26,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import blocks as B
+from .philox import gaussian_columns
 from .strategy import Strategy
 
 
@@ -51,9 +52,16 @@ def _deflate(V, u0):
 def lobpcg(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none",
            tol: float = 1e-10, max_iter: int = 1000, normA: float = 1.0,
            precond: np.ndarray | None = None, u0: np.ndarray | None = None,
-           keep_ritz: bool = False, observer=None, **strategy_params) -> Result:
+           keep_ritz: bool = False, observer=None, expand: str = "drop", seed: int = 0,
+           **strategy_params) -> Result:
     """``observer(j, S, theta, X, P, expanded)``, if given, is called after
-    the Rayleigh-Ritz step of every iteration (used by the invariant tests)."""
+    the Rayleigh-Ritz step of every iteration (used by the invariant tests).
+
+    ``expand``: "drop" appends the columns saved at the last shrink (S_drop);
+    "random" (the 'Random' variant of Sec. 6.4) appends as many freshly drawn
+    Gaussian columns instead (``philox.gaussian_columns`` with ``seed``, the
+    e-th expansion of the solve drawing block e), treated exactly as S_drop
+    would be."""
     n, nex = X0.shape
     assert nev <= nes < nex
     strat = Strategy(strategy, nes, nex, **strategy_params)
@@ -67,6 +75,7 @@ def lobpcg(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none",
     AP = np.zeros((n, 0))
     nnow, nlock = nex, 0
     Sdrop = None
+    n_exp = 0
     res = Result(lam[:nev], X[:, :nev], False, 0)
 
     for j in range(1, max_iter + 1):
@@ -94,6 +103,9 @@ def lobpcg(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none",
         # Expansion: re-orthogonalise S_drop against S and split it.
         expanded = strat.ifexpand(j, nnow)
         if expanded:
+            if expand == "random":
+                Sdrop = _deflate(gaussian_columns(n, Sdrop.shape[1], seed, n_exp), u0)
+            n_exp += 1
             S = np.hstack([X, P, W])
             Sd = B.orth_against(Sdrop, S)
             h = Sd.shape[1] // 2

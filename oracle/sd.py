@@ -16,13 +16,17 @@ from __future__ import annotations
 import numpy as np
 
 from . import blocks as B
+from .philox import gaussian_columns
 from .lobpcg import Result
 from .strategy import Strategy
 
 
 def sd(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none", tol: float = 1e-10,
        max_iter: int = 1000, normA: float = 1.0, precond: np.ndarray | None = None,
-       **strategy_params) -> Result:
+       expand: str = "drop", seed: int = 0, **strategy_params) -> Result:
+    """``expand`` = "random": fresh Gaussian columns (``philox.gaussian_columns``,
+    block e at the e-th expansion) replace the saved X_drop, as for LOBPCG and
+    subspace iteration (the 'Random' variant of Sec. 6.4)."""
     n, nex = X0.shape
     assert nev <= nes < nex
     strat = Strategy(strategy, nes, nex, **strategy_params)
@@ -32,6 +36,7 @@ def sd(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none", tol: float
     X, AX = X @ Z, AX @ Z
     nnow = nex
     Xdrop = None
+    n_exp = 0
     res = Result(lam[:nev], X[:, :nev], False, 0)
     for j in range(1, max_iter + 1):
         R, rho, r = B.residual_test(X, AX, lam, normA, nev)
@@ -42,6 +47,9 @@ def sd(A, X0: np.ndarray, nev: int, nes: int, strategy: str = "none", tol: float
             res.lam, res.X, res.converged, res.rho = lam[:nev].copy(), X[:, :nev].copy(), True, rho[:nev]
             break
         if strat.ifexpand(j, nnow):
+            if expand == "random":
+                Xdrop = gaussian_columns(n, Xdrop.shape[1], seed, n_exp)
+            n_exp += 1
             Xd = B.orth_against(Xdrop, X)
             X = np.hstack([X, Xd])
             AX = np.hstack([AX, B.spmm(A, Xd)])

@@ -51,7 +51,8 @@ class eig_options(C.Structure):
                 ("cheb_upper", C.c_double), ("precond", C.c_int), ("deflate_ones", C.c_int),
                 ("normA", C.c_double), ("mixed_switch", C.c_double), ("X0", C.c_void_p),
                 ("x0_on_device", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int),
-                ("expand_powered", C.c_int), ("gram_tc", C.c_int), ("warm_first", C.c_int)]
+                ("expand_powered", C.c_int), ("gram_tc", C.c_int), ("warm_first", C.c_int),
+                ("expand_random", C.c_int), ("seed", C.c_uint64)]
 
 
 class eig_server_opts(C.Structure):

@@ -11,6 +11,12 @@ struct Csr {
   const int32_t* rowptr = nullptr;
   const int32_t* colind = nullptr;
   const typename Pol<A>::T* val = nullptr;
+  // rows with more than heavy_min nonzeros (the nheavy row indices in
+  // heavy, device memory) are split over the warps of one CTA each instead
+  // of one lane group; heavy_min = 0: no split
+  const int32_t* heavy = nullptr;
+  int nheavy = 0;
+  int heavy_min = 0;
 };
 
 // Y = alpha A V + beta V + gamma U (single-segment n x w views)
@@ -108,5 +114,10 @@ cudaError_t residual(int64_t n, int w, const typename Pol<A>::T* X, int64_t ldx,
 // for a rows x cols block (row-major, own leading dimensions).
 cudaError_t convert2d(int64_t rows, int64_t cols, const void* src, int64_t lds, int sdt, void* dst,
                       int64_t ldd, int ddt, cudaStream_t st);
+
+// n x w Gaussian columns of the 'Random' expansion (Sec. 6.4) in element
+// format dt (EIG_F64, EIG_DF64, EIG_F32): a counter-based draw, entry (i, j)
+// a function of (seed, e, i, j) only (k_blocks.cu)
+cudaError_t gauss_fill(int64_t n, int w, void* dst, int64_t ld, int dt, uint64_t seed, int e, cudaStream_t st);
 
 }  // namespace eig

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) spmm_kernel(
     const typename Pol<A>::T* __restrict__ val, int w, const typename Pol<A>::T* __restrict__ V,
     int64_t ldv, typename Pol<A>::T* __restrict__ Y, int64_t ldy, typename Pol<A>::S alpha,
     bool scale, typename Pol<A>::S beta, bool has_beta, const typename Pol<A>::T* __restrict__ U,
-    int64_t ldu, typename Pol<A>::S gamma, bool has_gamma) {
+    int64_t ldu, typename Pol<A>::S gamma, bool has_gamma, int heavy_min) {
   using P = Pol<A>;
   using T = typename P::T;
   using S = typename P::S;
@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(256) spmm_kernel(
 #pragma unroll
       for (int v = 0; v < VEC; ++v) acc[t][v] = P::zero();
     const int start = rowptr[row], end = rowptr[row + 1];
+    if (heavy_min > 0 && end - start > heavy_min) continue;  // spmm_heavy_kernel's row
     for (int base = start; base < end; base += G) {
       const int my = base + g;
       int cj = 0;
@@ -213,6 +214,122 @@ __global__ void __launch_bounds__(256) spmm_kernel(
   }
 }
 
+// Power-law rows: a row with more than heavy_min nonzeros would keep one lane
+// group busy for its whole length while the rest of the grid idles.  Such
+// rows (listed once per matrix) get one CTA each: warp q of HV (8, or fewer
+// for wide rows) takes the row's nonzeros in blocks of 32 starting at block q
+// (stride HV blocks),
+// each lane its column vectors as in spmm_kernel; the HV partial rows are
+// summed in warp order through shared memory (deterministic), then the
+// epilogue of spmm_kernel.
+__device__ __forceinline__ void acc_add(double& c, double x) { c += x; }
+__device__ __forceinline__ void acc_add(float& c, float x) { c += x; }
+__device__ __forceinline__ void acc_add(dd& c, dd x) {
+  const float s = c.hi + x.hi;
+  const float z = s - c.hi;
+  const float t = (c.hi - (s - z)) + (x.hi - z);
+  c.hi = s;
+  c.lo += t + x.lo;
+}
+
+// warps per split row: 8, fewer when their partial rows would not fit in
+// 48 KB of shared memory
+template <Arith A, int VEC, int MAXT>
+constexpr int hv_warps() {
+  constexpr int per_warp = MAXT * VEC * 32 * int(sizeof(typename Pol<A>::Acc));
+  return 49152 / per_warp < 8 ? 49152 / per_warp : 8;
+}
+
+template <Arith A, int VEC, int MAXT>
+__global__ void __launch_bounds__(256) spmm_heavy_kernel(
+    const int32_t* __restrict__ heavy, int nheavy, const int32_t* __restrict__ rowptr,
+    const int32_t* __restrict__ colind, const typename Pol<A>::T* __restrict__ val, int w,
+    const typename Pol<A>::T* __restrict__ V, int64_t ldv, typename Pol<A>::T* __restrict__ Y, int64_t ldy,
+    typename Pol<A>::S alpha, bool scale, typename Pol<A>::S beta, bool has_beta,
+    const typename Pol<A>::T* __restrict__ U, int64_t ldu, typename Pol<A>::S gamma, bool has_gamma) {
+  using P = Pol<A>;
+  using T = typename P::T;
+  using S = typename P::S;
+  using Acc = typename P::Acc;
+  constexpr int G = 32;
+  constexpr int HV_WARPS = hv_warps<A, VEC, MAXT>();
+  __shared__ Acc red[HV_WARPS][MAXT * VEC][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int hrow = blockIdx.x; hrow < nheavy; hrow += gridDim.x) {
+    const int64_t row = heavy[hrow];
+    Acc acc[MAXT][VEC];
+#pragma unroll
+    for (int t = 0; t < MAXT; ++t)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) acc[t][v] = P::zero();
+    const int start = rowptr[row], end = rowptr[row + 1];
+    for (int base = start + G * warp; base < end; base += G * HV_WARPS) {
+      const int my = base + lane;
+      int cj = 0;
+      S aj{};
+      if (my < end) {
+        cj = colind[my];
+        T v = val[my];
+        aj = scale ? scale_val<A>(v, alpha) : P::stage(v);
+      }
+      const int cnt = min(G, end - base);
+      for (int tt = 0; tt < cnt; ++tt) {
+        const int c = __shfl_sync(0xffffffffu, cj, tt);
+        const S a = shfl_t<S>(0xffffffffu, aj, tt, 32);
+        const T* vrow = V + int64_t(c) * ldv;
+#pragma unroll
+        for (int s = 0; s < MAXT; ++s) {
+          const int col = (lane + s * G) * VEC;
+          if (col < w) {
+            T x[VEC];
+            if (col + VEC <= w) {
+              VecIO<T, VEC>::load(vrow + col, x);
+            } else {
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) x[v] = (col + v < w) ? vrow[col + v] : T{};
+            }
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) P::mac(acc[s][v], a, P::stage(x[v]));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < MAXT; ++s)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) red[warp][s * VEC + v][lane] = acc[s][v];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+      for (int s = 0; s < MAXT; ++s) {
+        const int col = (lane + s * G) * VEC;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v)
+#pragma unroll
+          for (int q = 1; q < HV_WARPS; ++q) acc_add(acc[s][v], red[q][s * VEC + v][lane]);
+        if (col >= w) continue;
+        if (has_beta || has_gamma) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            if (col + v >= w) continue;
+            if (has_beta) P::mac(acc[s][v], beta, P::stage(V[row * ldv + col + v]));
+            if (has_gamma) P::mac(acc[s][v], gamma, P::stage(U[row * ldu + col + v]));
+          }
+        }
+        T out[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) out[v] = P::store(acc[s][v]);
+        if (col + VEC <= w) {
+          VecIO<T, VEC>::store(Y + row * ldy + col, out);
+        } else {
+          for (int v = 0; v < VEC && col + v < w; ++v) Y[row * ldy + col + v] = out[v];
+        }
+      }
+    }
+    __syncthreads();  // red is reused by the next row
+  }
+}
+
 template <Arith A, int VEC, int G, int MAXT>
 static void launch_spmm(const Csr<A>& M, int w, const typename Pol<A>::T* V, int64_t ldv,
                         typename Pol<A>::T* Y, int64_t ldy, double alpha, double beta,
@@ -223,9 +340,20 @@ static void launch_spmm(const Csr<A>& M, int w, const typename Pol<A>::T* V, int
   const int64_t cap = int64_t(num_sms()) * 16;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
+  const int hmin = (M.heavy && M.nheavy > 0) ? M.heavy_min : 0;
   spmm_kernel<A, VEC, G, MAXT><<<(unsigned)blocks, threads, 0, st>>>(
       M.n, M.rowptr, M.colind, M.val, w, V, ldv, Y, ldy, host_coef<A>(alpha), alpha != 1.0,
-      host_coef<A>(beta), beta != 0.0, U, ldu, host_coef<A>(gamma), gamma != 0.0); count_launches(1);
+      host_coef<A>(beta), beta != 0.0, U, ldu, host_coef<A>(gamma), gamma != 0.0, hmin); count_launches(1);
+  if (hmin > 0) {
+    // the split rows need every lane of a warp per row: 32 lanes x VEC x
+    // HMAXT column vectors cover the same columns as the G x MAXT of the
+    // main kernel
+    constexpr int HMAXT = (G * MAXT + 31) / 32;
+    const int hb = M.nheavy < num_sms() * 8 ? M.nheavy : num_sms() * 8;
+    spmm_heavy_kernel<A, VEC, HMAXT><<<(unsigned)hb, 32 * hv_warps<A, VEC, HMAXT>(), 0, st>>>(
+        M.heavy, M.nheavy, M.rowptr, M.colind, M.val, w, V, ldv, Y, ldy, host_coef<A>(alpha), alpha != 1.0,
+        host_coef<A>(beta), beta != 0.0, U, ldu, host_coef<A>(gamma), gamma != 0.0); count_launches(1);
+  }
 }
 
 template <Arith A, int VEC>
@@ -759,6 +887,58 @@ cudaError_t convert2d(int64_t rows, int64_t cols, const void* src, int64_t lds, 
   const int64_t cap = int64_t(num_sms()) * 32;
   if (blocks > cap) blocks = cap;
   convert2d_kernel<<<(unsigned)blocks, 256, 0, st>>>(rows, cols, src, lds, sdt, dst, ldd, ddt); count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Gaussian columns of the 'Random' expansion (Sec. 6.4), drawn from a
+// counter-based generator so that every entry is a function of (seed,
+// expansion e, row i, column j): Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
+// SC'11; multipliers 0xD2511F53 and 0xCD9E8D57, Weyl key increments
+// 0x9E3779B9 and 0xBB67AE85, ten rounds) on the counter
+// (i mod 2^32, i / 2^32, j / 2, e) with key (seed mod 2^32, seed / 2^32);
+// its words give two float64 uniforms u1 = (w0 2^21 + w1 / 2^11 + 1/2) 2^-53
+// in (0, 1) and u2 = (w2 2^21 + w3 / 2^11) 2^-53, and Box-Muller gives
+// sqrt(-2 ln u1) times cos(2 pi u2) (even j) or sin(2 pi u2) (odd j).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+__global__ void gauss_fill_kernel(int64_t n, int w, void* dst, int64_t ld, int dt, uint64_t seed, uint32_t e) {
+  const int64_t tot = n * w;
+  for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < tot;
+       idx += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = idx / w;
+    const int j = int(idx % w);
+    uint32_t c[4] = {uint32_t(uint64_t(i)), uint32_t(uint64_t(i) >> 32), uint32_t(j >> 1), e};
+    philox4x32_10(c, uint32_t(seed), uint32_t(seed >> 32));
+    const double u1 = (double(c[0]) * 2097152.0 + double(c[1] >> 11) + 0.5) * 0x1p-53;
+    const double u2 = (double(c[2]) * 2097152.0 + double(c[3] >> 11)) * 0x1p-53;
+    const double r = sqrt(-2.0 * log(u1));
+    const double ang = 6.283185307179586 * u2;  // 2 pi rounded to float64, as 2.0 * pi
+    store_from_double(dst, dt, i * ld + j, (j & 1) ? r * sin(ang) : r * cos(ang));
+  }
+}
+
+cudaError_t gauss_fill(int64_t n, int w, void* dst, int64_t ld, int dt, uint64_t seed, int e, cudaStream_t st) {
+  const int64_t tot = n * w;
+  if (tot <= 0) return cudaSuccess;
+  int64_t blocks = cdiv(tot, 256);
+  const int64_t cap = int64_t(num_sms()) * 32;
+  if (blocks > cap) blocks = cap;
+  gauss_fill_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, w, dst, ld, dt, seed, uint32_t(e)); count_launches(1);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -126,6 +127,9 @@ struct SEStrategy {
 // ---------------------------------------------------------------------------
 // handle
 // ---------------------------------------------------------------------------
+// SpMM rows longer than this are split over the warps of a CTA
+constexpr int HEAVY_MIN = 512;
+
 struct eig_handle {
   int64_t n = 0, nnz = 0;
   int nev = 0, kmax = 0, nes = 0, strategy = 0;
@@ -139,6 +143,8 @@ struct eig_handle {
   dd* valdd = nullptr;
   float* val32 = nullptr;
   bool own_idx = false;
+  int32_t* heavy = nullptr;  // rows with more than HEAVY_MIN nonzeros (device)
+  int nheavy = 0;
   // Jacobi diagonal and null vector, per storage format
   double* t64 = nullptr;
   dd* tdd = nullptr;
@@ -322,6 +328,9 @@ struct Ops {
     c.rowptr = h->rowptr;
     c.colind = h->colind;
     c.val = FormData<AU>::val(h);
+    c.heavy = h->heavy;
+    c.nheavy = h->nheavy;
+    c.heavy_min = HEAVY_MIN;
     return c;
   }
   int64_t ld() const { return h->LDS; }
@@ -632,9 +641,15 @@ struct LState {
   int poff = 0;      // column offset of P inside its slot
   int nlock = 0;
   bool have_drop = false;
+  int n_exp = 0;     // expansions so far (block index of the 'Random' draws)
   int j = 0;         // last iteration done
   SEStrategy se;
 };
+
+// element format code of a block type
+template <typename T> constexpr int fmt_of() {
+  return sizeof(T) == 4 ? EIG_F32 : (std::is_same<T, dd>::value ? EIG_DF64 : EIG_F64);
+}
 
 template <Arith AU, Arith AG>
 int lobpcg_init(eig_handle* h, LState& L) {
@@ -738,6 +753,10 @@ int lob_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switch
     if (L.se.ifexpand(j, L.nnow)) {
       if (!L.have_drop) return EIG_EINVAL;
       const int hd = h->hdrop;
+      // 'Random' variant (Sec. 6.4): fresh Gaussian columns replace S_drop
+      if (h->opt.expand_random)
+        CK(gauss_fill(h->n, 2 * hd, h->Sd, 2 * hd, fmt_of<T>(), h->opt.seed, L.n_exp, h->st));
+      ++L.n_exp;
       // P must be contiguous from the slot start for the append: move it if offset
       Blk<T> Dsrc = view<T>(h->Sd, 2 * hd, 0, 2 * hd);
       Blk<T> Dmid = view<T>(h->Wt, h->wtw, 0, 2 * hd);
@@ -925,6 +944,9 @@ int cheb_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switc
     Blk<T> Y = view<T>(bufs[iy], ld, 0, L.nnow);
     if (L.se.ifexpand(j, L.nnow)) {
       if (!L.have_drop) return EIG_EINVAL;
+      if (h->opt.expand_random)  // 'Random' variant (Sec. 6.4)
+        CK(gauss_fill(h->n, h->hdrop, h->Sd, h->hdrop, fmt_of<T>(), h->opt.seed, L.n_exp, h->st));
+      ++L.n_exp;
       Y.add(static_cast<T*>(h->Sd), h->hdrop, h->hdrop);
       L.nnow += h->hdrop;
       L.have_drop = false;
@@ -997,6 +1019,9 @@ int sd_post(eig_handle* h, LState& L, double switch_r, bool* done, bool* switche
   if (L.se.ifexpand(j, L.nnow)) {
     if (!L.have_drop) return EIG_EINVAL;
     const int hd = h->hdrop;
+    if (h->opt.expand_random)  // 'Random' variant (Sec. 6.4)
+      CK(gauss_fill(h->n, hd, h->Sd, hd, fmt_of<T>(), h->opt.seed, L.n_exp, h->st));
+    ++L.n_exp;
     Blk<T> Q;
     if (h->opt.deflate_ones) Q.add(FormData<AU>::u0(h), 1, 1);
     Q = cat(Q, view<T>(Sc, ld, 0, L.nnow));
@@ -1130,6 +1155,9 @@ int final_pass(eig_handle* h, const void* Xsrc, int src_dt) {
   c.rowptr = h->rowptr;
   c.colind = h->colind;
   c.val = h->val64;
+  c.heavy = h->heavy;
+  c.nheavy = h->nheavy;
+  c.heavy_min = HEAVY_MIN;
   CK(eig::spmm<Arith::F64>(c, nev, V, nev, AV, nev, 1.0, 0.0, nullptr, 0, 0.0, h->st));
   // Rayleigh-Ritz in float64: V^T A V = Z diag(lam) Z^T, V <- V Z, AV <- AV Z
   CK(eig::gram<Arith::F64>(n, blk(V), blk(AV), true, h->Gp, nev, h->gscr, h->st));
@@ -1273,11 +1301,6 @@ int solve_impl(eig_handle* h) {
   return st.status;
 }
 
-int finish(eig_handle* h, int status) {
-  h->status = status;
-  return status;
-}
-
 void free_all(eig_handle* h) {
   auto F = [](void* p) {
     if (p) cudaFree(p);
@@ -1286,6 +1309,7 @@ void free_all(eig_handle* h) {
     F(h->rowptr);
     F(h->colind);
   }
+  F(h->heavy);
   F(h->val64);
   F(h->valdd);
   F(h->val32);
@@ -1475,6 +1499,8 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
   if (opt->form < EIG_FORM_DF64 || opt->form > EIG_FORM_MIXED) return EIG_EINVAL;
   if (opt->algo == EIG_CHEB_SI && opt->cheb_degree < 2) return EIG_EINVAL;
   if (opt->je < 1 || opt->js < 0 || opt->jp < 1) return EIG_EINVAL;
+  if (opt->expand_random != 0 && opt->expand_random != 1) return EIG_EINVAL;
+  if (opt->expand_random && opt->expand_powered) return EIG_EINVAL;
   if (k_max > 1400) return EIG_EINVAL;
   eig_handle* h = new eig_handle();
   h->n = A->n;
@@ -1527,6 +1553,29 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
       return fail(EIG_ECUDA);
   }
   if (v32 && convert2d(1, nnz, h->val32, nnz, EIG_F32, h->val64, nnz, EIG_F64, h->st)) return fail(EIG_ECUDA);
+  {
+    // power-law rows for the split SpMM path (read from the host copy of
+    // rowptr, or once from the device)
+    std::vector<int32_t> rp;
+    const int32_t* hrp = A->rowptr;
+    if (A->on_device) {
+      rp.resize(size_t(n) + 1);
+      if (cudaMemcpyAsync(rp.data(), A->rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, h->st) ||
+          cudaStreamSynchronize(h->st))
+        return fail(EIG_ECUDA);
+      hrp = rp.data();
+    }
+    std::vector<int32_t> hv;
+    for (int64_t i = 0; i < n; ++i)
+      if (hrp[i + 1] - hrp[i] > HEAVY_MIN) hv.push_back(int32_t(i));
+    if (!hv.empty()) {
+      AL(h->heavy, sizeof(int32_t) * hv.size());
+      if (cudaMemcpyAsync(h->heavy, hv.data(), sizeof(int32_t) * hv.size(), cudaMemcpyHostToDevice, h->st) ||
+          cudaStreamSynchronize(h->st))
+        return fail(EIG_ECUDA);
+      h->nheavy = int(hv.size());
+    }
+  }
   AL(h->valdd, sizeof(dd) * nnz);
   if (convert2d(1, nnz, h->val64, nnz, EIG_F64, h->valdd, nnz, EIG_DF64, h->st)) return fail(EIG_ECUDA);
   if (opt->form == EIG_FORM_MIXED && !v32) {
@@ -1817,48 +1866,77 @@ int eig_submit(eig_server* s, const eig_csr* A, int nev, int k_max, int strategy
 
 int eig_server_step(eig_server* s, int* n_active, int* n_queued) {
   if (!s) return EIG_EINVAL;
-  // admission in arrival order
-  while (!s->queue.empty() && int(s->active.size()) < s->opt.max_active &&
-         s->in_use + s->queue.front()->footprint <= s->opt.mem_budget_bytes) {
-    Request* r = s->queue.front();
-    s->queue.erase(s->queue.begin());
-    int rc = admit(s, r);
-    if (rc) {
-      r->status = rc;
-      r->done = true;
-      r->t_done = std::chrono::steady_clock::now();
-      if (r->h) eig_destroy(r->h);
-      if (r->st) cudaStreamDestroy(r->st);
-      r->h = nullptr;
-      r->st = nullptr;
-      s->finished.push_back(r);
-      continue;
-    }
-    s->active.push_back(r);
-  }
-  // one iteration of every active solve
-  for (auto* r : s->active) {
+  std::vector<Request*> pending;
+  // the device part of r's next iteration, up to the copy of its residual
+  // norms
+  auto launch_one = [&](Request* r) {
     int rc = r->stp.pre();
     if (rc) {
       r->stp.finished = true;
       r->stp.status = rc;
     }
-  }
-  std::vector<Request*> still;
-  for (auto* r : s->active) {
-    if (!r->stp.finished) {
-      cudaStreamSynchronize(r->st);
-      prof_flush(r->h);
-      r->stp.post();
+    pending.push_back(r);
+  };
+  // admission in arrival order; an admitted solve launches its first
+  // iteration at once
+  auto admit_queued = [&]() {
+    while (!s->queue.empty() && int(s->active.size()) < s->opt.max_active &&
+           s->in_use + s->queue.front()->footprint <= s->opt.mem_budget_bytes) {
+      Request* r = s->queue.front();
+      s->queue.erase(s->queue.begin());
+      int rc = admit(s, r);
+      if (rc) {
+        r->status = rc;
+        r->done = true;
+        r->t_done = std::chrono::steady_clock::now();
+        if (r->h) eig_destroy(r->h);
+        if (r->st) cudaStreamDestroy(r->st);
+        r->h = nullptr;
+        r->st = nullptr;
+        s->finished.push_back(r);
+        continue;
+      }
+      s->active.push_back(r);
+      launch_one(r);
     }
-    if (r->stp.finished) {
-      retire(s, r);
-      s->finished.push_back(r);
-    } else {
-      still.push_back(r);
+  };
+  for (auto* r : s->active) launch_one(r);
+  admit_queued();
+  // every active solve advances by one iteration; the host part of each
+  // (strategy decision, small eigenproblems launched, bookkeeping) runs as
+  // soon as its own stream has drained, in completion order, so that a
+  // short iteration does not wait behind a long one; a finished solve frees
+  // its slot and memory at once and the queue is admitted into it
+  while (!pending.empty()) {
+    bool progressed = false;
+    for (size_t i = 0; i < pending.size();) {
+      Request* r = pending[i];
+      if (!r->stp.finished) {
+        const cudaError_t q = cudaStreamQuery(r->st);
+        if (q == cudaErrorNotReady) {
+          ++i;
+          continue;
+        }
+        if (q != cudaSuccess) {
+          cudaGetLastError();
+          r->stp.finished = true;
+          r->stp.status = EIG_ECUDA;
+        } else {
+          prof_flush(r->h);
+          r->stp.post();
+        }
+      }
+      progressed = true;
+      pending.erase(pending.begin() + i);
+      if (r->stp.finished) {
+        retire(s, r);
+        s->finished.push_back(r);
+        s->active.erase(std::find(s->active.begin(), s->active.end(), r));
+        admit_queued();
+      }
     }
+    if (!progressed) std::this_thread::yield();
   }
-  s->active.swap(still);
   if (n_active) *n_active = int(s->active.size());
   if (n_queued) *n_queued = int(s->queue.size());
   return EIG_OK;

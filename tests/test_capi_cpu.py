@@ -85,7 +85,7 @@ def test_options_default_values(libpath):
     assert lib.eig_options_default(ctypes.byref(o)) == 0
     assert (o.tol, o.max_iter, o.je, o.js, o.jp, o.j_warm) == (1e-10, 1000, 12, 2, 10, 5)
     assert (o.mu, o.r_warm, o.cheb_degree) == (1.1, 1e-4, 12)
-    assert (o.expand_powered, o.gram_tc, o.warm_first) == (0, 1, 0)
+    assert (o.expand_powered, o.gram_tc, o.warm_first, o.expand_random, o.seed) == (0, 1, 0, 0, 0)
 
 
 def test_struct_layouts_match_header(tmp_path):

@@ -471,6 +471,54 @@ def test_lobpcg_graph_laplacian_jacobi_deflation():
     s.close()
 
 
+def hub_graph_laplacian(n=4000, hubs=(1500, 900, 700, 530), seed=9):
+    """A ring plus hub vertices joined to many random vertices: rows longer
+    than the SpMM's split threshold (512 nonzeros) next to short ones."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    rows = list(range(n))
+    cols = [(i + 1) % n for i in range(n)]
+    vals = list(rng.uniform(0.5, 1.5, n))
+    for h, deg in enumerate(hubs):
+        nb = rng.choice(np.arange(len(hubs), n), deg, replace=False)
+        rows += [h] * deg
+        cols += list(nb)
+        vals += list(rng.uniform(0.5, 1.5, deg))
+    Wm = sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
+    Wm = Wm + Wm.T
+    Lm = (sp.diags(np.asarray(Wm.sum(axis=1)).ravel()) - Wm).tocsr()
+    Lm.sort_indices()
+    return W.CSR(n, Lm.indptr.astype(np.int32), Lm.indices.astype(np.int32), Lm.data.astype(np.float64))
+
+
+@pytest.mark.parametrize("form", ["f64", "df64", "mixed"])
+def test_split_rows_of_power_law_graphs(form):
+    """Rows with more than 512 nonzeros go through the split SpMM path (one
+    CTA per row, partial rows summed in a fixed order); the whole solve
+    matches the dense eigenvalues and the oracle, and runs bitwise the same
+    twice."""
+    A = hub_graph_laplacian()
+    deg = np.diff(A.indptr)
+    assert (deg > 512).sum() == 4 and deg.max() > 1000
+    M = A.to_scipy()
+    ev = np.linalg.eigvalsh(M.toarray())
+    X0 = W.gaussian_block(A.n, 24, 4)
+    normA = float(ev[-1])
+    kw = dict(nev=12, k_max=24, strategy="fix", X0=X0, normA=normA, tol=1e-9, precond=1, deflate_ones=1,
+              max_iter=800, form=form)
+    s = L.Solver(A, **kw)
+    out = s.solve()
+    again = s.solve()
+    s.close()
+    ref = o_lobpcg(A, X0, 12, 17, "fix", tol=1e-9, normA=normA, precond=1.0 / M.diagonal(),
+                   u0=np.ones(A.n) / math.sqrt(A.n), max_iter=800)
+    assert out["status"] == 0 and ref.converged
+    tol = 1e-8 if form == "mixed" else 1e-9
+    assert np.max(np.abs(out["lam"] - ev[1:13]) / ev[1:13]) <= tol
+    assert np.max(np.abs(out["lam"] - ref.lam) / ref.lam) <= tol
+    assert np.array_equal(out["lam"], again["lam"])
+
+
 @pytest.mark.parametrize("form", ["df64", "f64", "mixed"])
 @pytest.mark.parametrize("strategy", ["none", "fix", "slopek"])
 def test_chebsi_anderson_parity(form, strategy):
@@ -609,6 +657,73 @@ def test_sd_parity(form, strategy):
     if strategy == "fix":
         assert out["n_expand"] >= 1
     s.close()
+
+
+@pytest.mark.parametrize("form", ["f64", "df64"])
+def test_lobpcg_random_expansion_parity(c1, form):
+    """The 'Random' variant of Sec. 6.4: the expansion appends counter-based
+    Gaussian columns (the same definition on both sides), so the histories
+    agree after the expansions too."""
+    A, normA, X0, ex = c1
+    s = L.Solver(A, nev=10, k_max=20, strategy="fix", X0=X0, normA=normA, tol=1e-10, form=form,
+                 expand_random=1, seed=2024)
+    out = s.solve()
+    s.close()
+    ref = o_lobpcg(A, X0, 10, 15, "fix", tol=1e-10, normA=normA, expand="random", seed=2024)
+    assert out["status"] == 0 and ref.converged
+    assert out["n_expand"] >= 1
+    assert np.max(np.abs(out["lam"] - ref.lam) / ref.lam) <= 1e-10
+    assert np.max(np.abs(out["lam"] - ex[:10]) / ex[:10]) <= 1e-10
+    first_exp = min(j for j, e in ref.events if e == "expand")
+    m = min(len(ref.history), len(out["history"]), first_exp + 8)
+    assert m > first_exp + 1
+    assert np.allclose(out["history"][:m], ref.history[:m], rtol=1e-6)
+
+
+def test_chebsi_random_expansion_parity():
+    A = W.anderson_3d(12, seed=2)
+    ev = np.linalg.eigvalsh(A.to_scipy().toarray())
+    X0 = W.gaussian_block(A.n, 32, 2)
+    ub = W.gershgorin_bound(A)
+    normA = float(np.abs(ev).max())
+    kw = dict(j_warm=2, r_warm=1e-2, je=4, js=1)
+    s = L.Solver(A, nev=16, k_max=32, strategy="fix", X0=X0, normA=normA, tol=1e-11, algo="chebsi",
+                 cheb_degree=10, cheb_upper=ub, max_iter=400, expand_random=1, seed=77, **kw)
+    out = s.solve()
+    s.close()
+    ref = o_chebsi(A, X0, 16, 21, "fix", tol=1e-11, normA=normA, degree=10, upper=ub, max_iter=400,
+                   expand="random", seed=77, **kw)
+    assert out["status"] == 0 and ref.converged and out["n_expand"] >= 1
+    assert np.max(np.abs(out["lam"] - ev[:16]) / np.abs(ev[:16])) <= 1e-10
+    first_exp = min(j for j, e in ref.events if e == "expand")
+    m = min(len(ref.history), len(out["history"]), first_exp + 6)
+    assert np.allclose(out["history"][:m], ref.history[:m], rtol=1e-6)
+
+
+@pytest.mark.parametrize("strategy", ["fix", "slopek"])
+def test_lobpcg_aggressive_warmup_parity(c1, strategy):
+    """The first-pair warm-up gate of the paper's closing remarks
+    (warm_first, r_warm = 1e-1): same decisions and results as the oracle's
+    strategy with the same gate, and the first shrink comes earlier than with
+    the default gate."""
+    A, normA, X0, ex = c1
+    kw = dict(warm_first=1, r_warm=1e-1)
+    s = L.Solver(A, nev=10, k_max=20, strategy=strategy, X0=X0, normA=normA, tol=1e-10, **kw)
+    out = s.solve()
+    s.close()
+    ref = o_lobpcg(A, X0, 10, 15, strategy, tol=1e-10, normA=normA, warm_first=True, r_warm=1e-1)
+    base = o_lobpcg(A, X0, 10, 15, strategy, tol=1e-10, normA=normA)
+    assert out["status"] == 0 and ref.converged
+    assert np.max(np.abs(out["lam"] - ref.lam) / ref.lam) <= 1e-10
+    assert np.max(np.abs(out["lam"] - ex[:10]) / ex[:10]) <= 1e-10
+    m = min(12, len(ref.history), len(out["history"]))
+    assert np.allclose(out["history"][:m], ref.history[:m], rtol=1e-6)
+    # the active widths are the oracle's while the histories agree
+    mw = min(m, len(ref.widths), len(out["widths"]))
+    assert list(out["widths"][:mw]) == list(ref.widths[:mw])
+    first = min(j for j, e in ref.events if e == "shrink")
+    first_base = min(j for j, e in base.events if e == "shrink")
+    assert first < first_base
 
 
 def test_chebsi_powered_drop_parity():

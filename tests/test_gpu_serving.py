@@ -78,3 +78,39 @@ def test_request_larger_than_budget_is_rejected():
         srv.submit(A, X0, r.nev, r.k_max, "fix", normA=normA, **OPTS)
     assert e.value.code == 8   # EIG_EREJECT
     srv.close()
+
+
+@pytest.mark.parametrize("form", ["mixed", "f64"])
+def test_arrivals_while_others_are_mid_solve(form):
+    """Requests submitted while earlier ones are part-way through their
+    iterations: the newcomers are admitted at the next step and, like the
+    running solves, give bitwise the results of a solve alone; a request
+    that arrives after a slot was freed by a finished solve takes it."""
+    stream = small_stream(5)
+    opts = dict(OPTS, form=form)
+    srv = L.Server(64 << 30, 3)
+    tickets = {}
+    r, A, normA, X0 = stream[0]
+    tickets[0] = srv.submit(A, X0, r.nev, r.k_max, "fix", normA=normA, **opts)
+    seen_active = []
+    nxt = 1
+    for step in range(20000):
+        if nxt < len(stream) and step in (3, 7, 11, 40):
+            r, A, normA, X0 = stream[nxt]
+            tickets[nxt] = srv.submit(A, X0, r.nev, r.k_max, "fix", normA=normA, **opts)
+            nxt += 1
+        a, q = srv.step()
+        seen_active.append(a)
+        if nxt >= len(stream) and a == 0 and q == 0:
+            break
+    assert nxt == len(stream) and max(seen_active) >= 2
+    for i, (r, A, normA, X0) in enumerate(stream):
+        got = srv.poll(tickets[i], n=A.n)
+        assert got is not None and got["status"] == 0
+        s = L.Solver(A, nev=r.nev, k_max=r.k_max, strategy="fix", X0=X0, normA=normA, **opts)
+        ref = s.solve()
+        s.close()
+        assert got["iters"] == ref["iters"]
+        assert np.array_equal(got["lam"], ref["lam"])
+        srv.release(tickets[i])
+    srv.close()

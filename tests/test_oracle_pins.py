@@ -539,3 +539,34 @@ def test_chebsi_powered_drop_matches_and_expands():
     r = chebsi(A, X0, 8, 11, "fix", expand="powered", **kw)
     assert r.converged and np.allclose(r.lam, ev[:8], rtol=1e-10, atol=1e-12)
     assert any(e == "expand" for _, e in r.events)
+
+
+# ---------------------------------------------------------------------------
+# The 'Random' expansion of Sec. 6.4: the counter-based Gaussian columns
+# ---------------------------------------------------------------------------
+def test_philox_known_answers(golden_dir):
+    from oracle.philox import philox4x32_10
+    rows = [l.split()[1:] for l in open(os.path.join(golden_dir, "philox4x32_10_kat.txt"))
+            if l.startswith("kat ")]
+    assert len(rows) == 3
+    for r in rows:
+        c0, c1, c2, c3, k0, k1, *want = (int(x, 16) for x in r)
+        got = philox4x32_10([c0], [c1], [c2], [c3], k0, k1)
+        assert [int(g[0]) for g in got] == want
+
+
+def test_gaussian_columns_are_standard_normal_and_counter_addressed():
+    from scipy import stats
+    from oracle.philox import gaussian_columns
+    Z = gaussian_columns(20000, 6, seed=12345, e=3)
+    # marginal: mean 0, variance 1, normal shape (Kolmogorov-Smirnov)
+    assert abs(Z.mean()) < 0.01 and abs(Z.var() - 1.0) < 0.02
+    assert stats.kstest(Z.ravel(), "norm").pvalue > 1e-3
+    # the sine and cosine halves of one Box-Muller pair are uncorrelated
+    assert abs(np.corrcoef(Z[:, 0], Z[:, 1])[0, 1]) < 0.03
+    # counter addressing: a sub-block is the block of its own size, and the
+    # expansion index and the seed give other draws
+    assert np.array_equal(gaussian_columns(300, 4, 12345, 3), Z[:300, :4])
+    assert not np.allclose(gaussian_columns(300, 4, 12345, 4), Z[:300, :4])
+    assert not np.allclose(gaussian_columns(300, 4, 12346, 3), Z[:300, :4])
+    assert np.all(np.isfinite(Z))
