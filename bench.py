@@ -619,7 +619,14 @@ def main():
     if sp and sp["launches"]:
         a = sp["bytes"] / (sp["ms"] / 1e3) / 1e9
         f = sp["flops"] / (sp["ms"] / 1e3) / 1e12
-        line["spmm"] = {"hbm_gbs": a, "hbm_frac": a / hbm,
+        # bytes of one row of V read per nonzero (element size of the class's
+        # dominant format): the traffic of a gather without reuse, the bound
+        # that applies when V is far larger than L2 and the column indices
+        # are scattered (the power-law graph); the Laplacian reuses V rows
+        # through L2 and reads V about once
+        esz = 4 if args.form == "mixed" else 8
+        g = sp["flops"] / 2 * esz / (sp["ms"] / 1e3) / 1e9
+        line["spmm"] = {"hbm_gbs": a, "hbm_frac": a / hbm, "gather_gbs": g, "gather_frac": g / hbm,
                         "fp64_tflops": f if args.form == "f64" else None,
                         "fp64_pipe_frac": f / FP64_PEAK_TFLOPS if args.form == "f64" else None}
 
@@ -658,7 +665,9 @@ def main():
         for name in ("drop", "powered", "random"):
             if name in var or (name == "powered" and algo != "chebsi"):
                 continue
-            ex2 = dict(extra, expand_powered=0, expand_random=0, **EXPAND_OPTS[name])
+            ex2 = dict(extra)
+            ex2.update(expand_powered=0, expand_random=0)
+            ex2.update(EXPAND_OPTS[name])
             other = L.Solver((rp, ci, va), nev=nev, k_max=k, strategy=args.strategy, X0=X0d, normA=normA,
                              tol=0.5 * tol, form=args.form, stream=stream, max_iter=args.max_iter, algo=algo,
                              **ex2)

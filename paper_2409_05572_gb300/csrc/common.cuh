@@ -34,11 +34,29 @@ struct Blk {
     start[nseg + 1] = width;
     ++nseg;
   }
+  // segment of logical column c (c < width): its pointer, leading dimension
+  // and first logical column, by unrolled selects, so that a kernel reading a
+  // Blk parameter never indexes it dynamically (which would copy the
+  // parameter to local memory)
+  __host__ __device__ __forceinline__ void seg(int c, T*& p, int64_t& l, int& s0) const {
+    p = ptr[0];
+    l = ld[0];
+    s0 = start[0];
+#pragma unroll
+    for (int t = 1; t < MAX_SEG; ++t)
+      if (t < nseg && c >= start[t]) {
+        p = ptr[t];
+        l = ld[t];
+        s0 = start[t];
+      }
+  }
   // address of element (row, logical column c); c < width
   __host__ __device__ T* at(int64_t row, int c) const {
-    int t = 0;
-    while (t + 1 < nseg && c >= start[t + 1]) ++t;
-    return ptr[t] + row * ld[t] + (c - start[t]);
+    T* p;
+    int64_t l;
+    int s0;
+    seg(c, p, l, s0);
+    return p + row * l + (c - s0);
   }
 };
 

@@ -436,16 +436,16 @@ __global__ void __launch_bounds__(256) gram_kernel(int64_t n, Blk<typename Pol<A
   const T* vp = nullptr;
   int64_t vld = 0;
   if (m0 + lc < a) {
-    up = U.at(0, m0 + lc);
-    int s = 0;
-    while (s + 1 < U.nseg && m0 + lc >= U.start[s + 1]) ++s;
-    uld = U.ld[s];
+    T* p;
+    int s0;
+    U.seg(m0 + lc, p, uld, s0);
+    up = p + (m0 + lc - s0);
   }
   if (n0 + lc < b) {
-    vp = V.at(0, n0 + lc);
-    int s = 0;
-    while (s + 1 < V.nseg && n0 + lc >= V.start[s + 1]) ++s;
-    vld = V.ld[s];
+    T* p;
+    int s0;
+    V.seg(n0 + lc, p, vld, s0);
+    vp = p + (n0 + lc - s0);
   }
   typename P::Acc acc[4][4];
 #pragma unroll
@@ -612,10 +612,10 @@ __global__ void __launch_bounds__(256) update_kernel(int64_t n, Blk<typename Pol
     const T* up = nullptr;
     int64_t uld = 0;
     if (kk < s_dim) {
-      int sg = 0;
-      while (sg + 1 < U.nseg && kk >= U.start[sg + 1]) ++sg;
-      up = U.ptr[sg] + (kk - U.start[sg]);
-      uld = U.ld[sg];
+      T* p;
+      int s0;
+      U.seg(kk, p, uld, s0);
+      up = p + (kk - s0);
     }
 #pragma unroll
     for (int i = 0; i < GT / 8; ++i) {

@@ -163,10 +163,10 @@ __device__ __forceinline__ void store16(__nv_bfloat16* blk, int64_t r, const flo
 
 template <typename T>
 __device__ __forceinline__ void col_lookup(const Blk<T>& U, int c, const T*& p, int64_t& ld) {
-  int s = 0;
-  while (s + 1 < U.nseg && c >= U.start[s + 1]) ++s;
-  p = U.ptr[s] + (c - U.start[s]);
-  ld = U.ld[s];
+  T* base;
+  int s0;
+  U.seg(c, base, ld, s0);
+  p = base + (c - s0);
 }
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem, int nbytes) {

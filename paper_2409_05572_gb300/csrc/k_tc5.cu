@@ -278,6 +278,55 @@ __device__ __forceinline__ void flush_one(tf& m, const float* a, float sc) {
 __device__ __forceinline__ double acc_value(const dd& m) { return double(m.hi) + double(m.lo); }
 __device__ __forceinline__ double acc_value(const tf& m) { return (double(m.m0) + double(m.m1)) + double(m.m2); }
 
+// (m0 + m1 + m2) 2^e rounded once to float64, with integer operations only:
+// GB300 runs float64 arithmetic at 1/64 of its float32 rate, and the five
+// float64 operations per element of acc_value + ldexp made the epilogue of
+// a 128 x 32 update tile (three 128-index chunks) slower than its MMAs.
+// The three floats become 64-bit fixed-point integers in units of
+// 2^(E0 - 187), E0 the biased exponent of m0 (m0's 24-bit mantissa shifted
+// left by 37 bits, the others aligned to it; bits below 2^-61 |m0| are
+// dropped), their sum is rounded to 53 bits (nearest even) and the float64
+// fields are assembled.  Zero, tiny or non-finite heads, a tail above the
+// head and results outside the normal float64 range take the float64 path.
+__device__ __forceinline__ long long tf_fixed(uint32_t b, int E0) {
+  const int E = int((b >> 23) & 255u);
+  if (E == 0) return 0;  // zero, or a subnormal below 2^-61 |m0|
+  const long long M = (long long)((b & 0x7FFFFFu) | 0x800000u);
+  const int sh = E - E0 + 37;
+  const long long v = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> -sh) : 0ll);
+  return (b >> 31) ? -v : v;
+}
+__device__ __forceinline__ double tf_value_scaled(const tf& m, int e) {
+  const uint32_t b0 = __float_as_uint(m.m0), b1 = __float_as_uint(m.m1), b2 = __float_as_uint(m.m2);
+  const int E0 = int((b0 >> 23) & 255u), E1 = int((b1 >> 23) & 255u), E2 = int((b2 >> 23) & 255u);
+  if (E0 < 64 || E0 == 255 || E1 > E0 + 1 || E2 > E0 + 1 || E1 == 255 || E2 == 255)
+    return ldexp(acc_value(m), e);
+  // |terms| < 2^61, 2^62, 2^62: the sum cannot overflow
+  const long long S = tf_fixed(b0, E0) + tf_fixed(b1, E0) + tf_fixed(b2, E0);
+  if (S == 0) return 0.0;
+  const unsigned long long a = S < 0 ? 0ull - (unsigned long long)S : (unsigned long long)S;
+  const int nb = 64 - __clzll((long long)a);
+  unsigned long long mant;
+  int sh = nb - 53;
+  if (sh > 0) {
+    mant = a >> sh;
+    const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) ++mant;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++sh;
+    }
+  } else {
+    mant = a << (-sh);
+  }
+  // value = mant 2^(sh + E0 - 187 + e), mant in [2^52, 2^53)
+  const int biased = sh + E0 - 187 + e + 52 + 1023;
+  if (biased < 1 || biased > 2046) return ldexp(acc_value(m), e);
+  const unsigned long long bits =
+      (S < 0 ? (1ull << 63) : 0ull) | ((unsigned long long)biased << 52) | (mant & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
+
 template <int NS>
 using AccT = std::conditional_t<NS == 6, dd, tf>;
 
@@ -473,10 +522,13 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(const __grid_constant__
       if (MODE == 0) {
 #pragma unroll
         for (int j = 0; j < CT; ++j) {
-          double v = acc_value(master[j]);
           // float64 operands: times 2^(r_a + r_b(column) - 14); every lane
           // takes part in the shuffle
-          if constexpr (NS == 7) v = ldexp(v, ra - 14 + __shfl_sync(0xffffffffu, rb, j));
+          double v;
+          if constexpr (NS == 7)
+            v = tf_value_scaled(master[j], ra - 14 + __shfl_sync(0xffffffffu, rb, j));
+          else
+            v = acc_value(master[j]);
           const int64_t col = c0 + j;
           if (live && col < B.M) go.part[int64_t(blockIdx.z) * A.M * B.M + r * B.M + col] = v;
         }
@@ -486,10 +538,18 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(const __grid_constant__
         bool fast = false;
         T* yrow = nullptr;
         if (live && c0 + CT <= B.M) {
-          int sg = 0;
-          while (sg + 1 < uo.Y.nseg && c0 >= uo.Y.start[sg + 1]) ++sg;
-          yrow = uo.Y.ptr[sg] + r * uo.Y.ld[sg] + (c0 - uo.Y.start[sg]);
-          fast = c0 + CT <= uo.Y.start[sg + 1] && (reinterpret_cast<uintptr_t>(yrow) & 15) == 0;
+          T* yp;
+          int64_t yld;
+          int ys0;
+          uo.Y.seg(int(c0), yp, yld, ys0);
+          yrow = yp + r * yld + (c0 - ys0);
+          // the run stays inside the segment when the column after it
+          // belongs to the same one (or it ends the block)
+          T* yq;
+          int64_t qld;
+          int qs0;
+          uo.Y.seg(int(c0 + CT - 1), yq, qld, qs0);
+          fast = qs0 == ys0 && (reinterpret_cast<uintptr_t>(yrow) & 15) == 0;
         }
         if constexpr (NS == 6) {
           if (live) {
@@ -529,8 +589,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc5_kernel(const __grid_constant__
             // every lane takes part in the shuffles of the column exponents
             const int s0 = ra - 14 + __shfl_sync(0xffffffffu, rb, j);
             const int s1 = ra - 14 + __shfl_sync(0xffffffffu, rb, j + 1);
-            double v0 = ldexp(acc_value(master[j]), s0);
-            double v1 = ldexp(acc_value(master[j + 1]), s1);
+            double v0 = tf_value_scaled(master[j], s0);
+            double v1 = tf_value_scaled(master[j + 1], s1);
             if (fast) {
               double2* y2 = reinterpret_cast<double2*>(yrow) + j / 2;
               if (uo.has_beta) {
