@@ -50,10 +50,15 @@ METRIC = "converged eigenpairs/s at 1e-8 residual vs fixed-block FP64; p50/p99 l
 UNIT = "eigenpairs/s"
 
 # DRAM traffic / algorithmic bytes of the tensor-core classes of the float64
-# form (slicing + product kernels), from an ncu capture of the current
-# kernels at n = 262,144; empty (traffic reported as null) until the
-# kernels that changed have been captured again.
-TC_TRAFFIC_RATIO = {}
+# form (slicing + product kernels), from one ncu capture of the current
+# kernels at n = 262,144 (`bench.py --kernel gram --n 262144 --a 384 --sym
+# --arith f64_tc` and `--kernel update ... --a 384 --b 256`; 384-column
+# operands; the Gram class reads U once, 0.805 GB; the update class reads U
+# and writes Y, 1.342 GB): column slicer 0.805 GB read + 1.356 GB written,
+# Gram product 1.417 + 0.003 GB; row slicer 0.805 + 1.357 GB, update product
+# 1.414 + 0.511 GB.  Traffic grows with n.
+TC_TRAFFIC_RATIO = {"gram": (0.805 + 1.356 + 1.417 + 0.003) / 0.805,
+                    "update": (0.805 + 1.357 + 1.414 + 0.511) / 1.342}
 
 
 def peaks():
