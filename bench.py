@@ -161,7 +161,7 @@ def make_workload(name):
     if name == "c4":
         A = W.graph_laplacian(4_000_000, seed=3)
         return dict(A=A, nev=200, k_max=400, normA=W.norm_estimate(A), seed=3, tol=1e-8, algo="lobpcg",
-                    extra=dict(precond=1, deflate_ones=1, gram_tc=0),
+                    extra=dict(precond=1, deflate_ones=1, tc_chunk_rows=1048576),
                     desc=f"graph Laplacian, power-law degrees (exponent 2.5, mean 10), n={A.n}, nnz={A.nnz}, "
                          "nev=200 above the null vector, LOBPCG k_max=400 + Jacobi, residual 1e-8",
                     exact=None)
@@ -456,8 +456,12 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=200.0, help="c5: device memory for active solves")
     ap.add_argument("--max-active", type=int, default=64, help="c5: solves advanced per step")
     ap.add_argument("--gram-tc", type=int, default=None, choices=[0, 1],
-                    help="1: Gram and update on the tensor cores (exact slices); 0: on the CUDA cores "
-                         "(default 1, and 0 for c4, whose slice buffers would not fit in HBM)")
+                    help="1 (default): Gram and update on the tensor cores (exact slices); 0: on the CUDA "
+                         "cores")
+    ap.add_argument("--tc-chunk-rows", type=int, default=None,
+                    help="rows of the tensor-core slice buffers (a multiple of 128; products run over "
+                         "row chunks; default: all rows, and 2^20 for c4, whose full slice buffers would "
+                         "not fit in HBM)")
     ap.add_argument("--expand", default="drop", choices=["drop", "powered", "random"],
                     help="vectors appended at an expansion (Sec. 6.4): the saved ones, the saved ones "
                          "filtered every iteration (Chebyshev SI only), fresh Gaussian ones")
@@ -517,6 +521,8 @@ def main():
     extra = dict(wl.get("extra", {}))
     if args.gram_tc is not None:
         extra["gram_tc"] = args.gram_tc
+    if args.tc_chunk_rows is not None:
+        extra["tc_chunk_rows"] = args.tc_chunk_rows
     if args.aggressive_warmup:
         extra.update(warm_first=1, r_warm=1e-1)
     extra.update(EXPAND_OPTS[args.expand])
@@ -569,7 +575,8 @@ def main():
                                     + ("7 slices, 28 pairs per float64 multiply-add)" if args.form == "f64"
                                        else "6 slices, 21 pairs per double-float multiply-add)"))
                        if tc_on else "CUDA cores",
-                       "l2": "inputs larger than L2 (each n x k block is 4.3 GB); no flush",
+                       "tc_chunk_rows": extra.get("tc_chunk_rows", 0),
+                       "l2": f"inputs larger than L2 (each n x k_max block is {8 * A.n * k / 1e9:.1f} GB); no flush",
                        "warmup_rule": "first pair, r_warm 1e-1" if args.aggressive_warmup else "r^(j), r_warm 1e-4",
                        "expand": args.expand},
             "converged": bool(ok), "iters": last["iters"], "n_shrink": last["n_shrink"],

@@ -290,6 +290,15 @@ typedef struct {
                           (w0 2^21 + w1 / 2^11 + 1/2) 2^-53 and
                           (w2 2^21 + w3 / 2^11) 2^-53 of its four words    */
   uint64_t seed;       /* key of the 'Random' draws                          */
+  int tc_chunk_rows;   /* 0 (default): the slice buffers of the tensor-core
+                          products hold all n rows; > 0, a multiple of 128:
+                          they hold this many rows and every Gram product and
+                          block update runs over row chunks of that size (the
+                          Gram's chunks summed in order), so that matrices
+                          whose full slice buffers would not fit in HBM (the
+                          4M-row graph with k_max = 400) keep the tensor-core
+                          products; the slices of [X, P] are then not cached
+                          across an orthogonalisation                        */
 } eig_options;
 
 /* kernel classes of the per-class statistics (eig_result.kstats) */

@@ -52,7 +52,7 @@ class eig_options(C.Structure):
                 ("normA", C.c_double), ("mixed_switch", C.c_double), ("X0", C.c_void_p),
                 ("x0_on_device", C.c_int), ("stream", C.c_void_p), ("profile", C.c_int),
                 ("expand_powered", C.c_int), ("gram_tc", C.c_int), ("warm_first", C.c_int),
-                ("expand_random", C.c_int), ("seed", C.c_uint64)]
+                ("expand_random", C.c_int), ("seed", C.c_uint64), ("tc_chunk_rows", C.c_int)]
 
 
 class eig_server_opts(C.Structure):

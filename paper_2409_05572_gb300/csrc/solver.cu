@@ -167,6 +167,8 @@ struct eig_handle {
   void* tcQr = nullptr;
   int qcmax = 0;
   int tcns = 0;  // slices per value (6 double-float, 7 float64)
+  int64_t tcrows = 0;     // rows held by tcU / tcV (n, or the chunk of tc_chunk_rows)
+  double* Gt = nullptr;   // Gram of one row chunk (chunked tensor-core products)
   // small float64 work
   int smax = 0;
   double *Gp = nullptr, *Rinv = nullptr, *cholw = nullptr, *Z = nullptr, *lamd = nullptr, *CP = nullptr;
@@ -289,6 +291,16 @@ bool same_blk(const Blk<T>& a, const Blk<T>& b) {
 // on the tensor cores (slice buffers); slices per value of the form's blocks
 bool uses_gram_tc(const eig_options& o) { return o.gram_tc != 0; }
 int tc_slices(int form) { return form == EIG_FORM_F64 ? tc::NS_F64 : tc::NS_DF; }
+// rows held by the slice buffers: all n, or the chunk of tc_chunk_rows
+int64_t tc_rows_of(int64_t n, int chunk) { return (chunk > 0 && chunk < n) ? int64_t(chunk) : n; }
+
+// the view of rows r0 .. of a block
+template <typename T>
+Blk<T> rows_from(const Blk<T>& b, int64_t r0) {
+  Blk<T> r = b;
+  for (int t = 0; t < b.nseg; ++t) r.ptr[t] = b.ptr[t] + r0 * b.ld[t];
+  return r;
+}
 
 // one slice buffer: a Gram operand (K = n, up to w columns) or an update's
 // left operand (K = up to w columns, n rows)
@@ -353,6 +365,22 @@ struct Ops {
     if constexpr (AG == Arith::DF64 || AG == Arith::F64) {
       if (h->tcU) {  // tensor-core product on exact bf16 slices
         const bool one = same_blk(U, V);
+        if (h->tcrows < h->n) {
+          // row chunks: G = sum over chunks of U_c^T V_c, added in chunk order
+          for (int64_t r0 = 0; r0 < h->n; r0 += h->tcrows) {
+            const int64_t rr = std::min(h->tcrows, h->n - r0);
+            const Blk<T> Uc = rows_from(U, r0);
+            CK(tc_slice_cols(rr, Uc, h->tcU, st(), gate));
+            if (!one) CK(tc_slice_cols(rr, rows_from(V, r0), h->tcV, st(), gate));
+            double* dst = r0 == 0 ? h->Gp : h->Gt;
+            CK(gram_tc_product(h->tcns, rr, U.width, V.width, h->tcU, one ? h->tcU : h->tcV, sym, dst, V.width,
+                               h->gscr, st(), gate));
+            if (r0 > 0)
+              CK(eig::axpby<Arith::F64>(U.width, V.width, h->Gp, V.width, 1.0, h->Gt, V.width, 1.0, h->Gp,
+                                        V.width, st()));
+          }
+          return EIG_OK;
+        }
         const bool ucached = q_cached(U);
         void* su = ucached ? h->tcQc : h->tcU;
         if (!ucached) CK(tc_slice_cols(h->n, U, h->tcU, st(), gate));
@@ -376,6 +404,14 @@ struct Ops {
         }
         const double nn = double(h->n);
         Prof p(h, EIG_K_UPDATE, 2.0 * nn * U.width * c, E * nn * (U.width + c * (beta != 0.0 ? 2.0 : 1.0)));
+        if (h->tcrows < h->n) {  // row chunks: each output row needs only its own U row
+          for (int64_t r0 = 0; r0 < h->n; r0 += h->tcrows) {
+            const int64_t rr = std::min(h->tcrows, h->n - r0);
+            CK(tc_slice_rows(rr, rows_from(U, r0), h->tcU, st(), gate));
+            CK(update_tc_product(rr, U.width, c, h->tcU, h->tcC, rows_from(Y, r0), beta, st(), gate));
+          }
+          return EIG_OK;
+        }
         const bool ucached = q_cached(U);
         if (!ucached) CK(tc_slice_rows(h->n, U, h->tcU, st(), gate));
         CK(update_tc_product(h->n, U.width, c, ucached ? h->tcQr : h->tcU, h->tcC, Y, beta, st(), gate));
@@ -1330,6 +1366,7 @@ void free_all(eig_handle* h) {
   F(h->tcC);
   F(h->tcQc);
   F(h->tcQr);
+  F(h->Gt);
   F(h->Gp);
   F(h->Rinv);
   F(h->cholw);
@@ -1367,7 +1404,7 @@ __global__ void fill_kernel(int64_t n, double v, double* x) {
 
 // Device bytes eig_create allocates (same formulas as its allocations).
 size_t footprint_bytes(int64_t n, int64_t nnz, int nev, int k_max, int nes, int form, int precond,
-                       int deflate, int on_device, int gram_tc) {
+                       int deflate, int on_device, int gram_tc, int tc_chunk_rows) {
   const size_t LDS = size_t((3 * k_max + 3) / 4 * 4);
   const size_t hd = size_t(k_max - nes);
   const size_t wtw = std::max(size_t(k_max), 2 * hd);
@@ -1389,8 +1426,12 @@ size_t footprint_bytes(int64_t n, int64_t nnz, int nev, int k_max, int nes, int 
        8 * smax * smax;
   if (gram_tc) {
     const int ns = tc_slices(form);
-    b += 2 * tc_operand_bytes(ns, n, int(smax)) + tc_slice_bytes(ns, int64_t(smax), 2 * k_max + 1) +
-         2 * tc_operand_bytes(ns, n, 2 * k_max + 1);
+    const int64_t rows = tc_rows_of(n, tc_chunk_rows);
+    b += 2 * tc_operand_bytes(ns, rows, int(smax)) + tc_slice_bytes(ns, int64_t(smax), 2 * k_max + 1);
+    if (rows == n)
+      b += 2 * tc_operand_bytes(ns, n, 2 * k_max + 1);   // slices of [u0, X, P], both layouts
+    else
+      b += 8 * smax * smax;                              // Gram of one row chunk
   }
   return b + b / 16 + (size_t(32) << 20);        // allocator rounding and slack
 }
@@ -1501,6 +1542,7 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
   if (opt->je < 1 || opt->js < 0 || opt->jp < 1) return EIG_EINVAL;
   if (opt->expand_random != 0 && opt->expand_random != 1) return EIG_EINVAL;
   if (opt->expand_random && opt->expand_powered) return EIG_EINVAL;
+  if (opt->tc_chunk_rows < 0 || opt->tc_chunk_rows % 128 != 0) return EIG_EINVAL;
   if (k_max > 1400) return EIG_EINVAL;
   eig_handle* h = new eig_handle();
   h->n = A->n;
@@ -1614,12 +1656,17 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
   AL(h->Sd, sizeof(double) * size_t(n) * std::max(h->wtw, nev));
   if (uses_gram_tc(h->opt)) {
     const int ns = h->tcns = tc_slices(opt->form);
-    AL(h->tcU, tc_operand_bytes(ns, n, 3 * k_max + 1));
-    AL(h->tcV, tc_operand_bytes(ns, n, 3 * k_max + 1));
+    h->tcrows = tc_rows_of(n, opt->tc_chunk_rows);
+    AL(h->tcU, tc_operand_bytes(ns, h->tcrows, 3 * k_max + 1));
+    AL(h->tcV, tc_operand_bytes(ns, h->tcrows, 3 * k_max + 1));
     AL(h->tcC, tc_slice_bytes(ns, 3 * k_max + 1, 2 * k_max + 1));
-    h->qcmax = 2 * k_max + 1;  // [u0, X, P]
-    AL(h->tcQc, tc_operand_bytes(ns, n, h->qcmax));
-    AL(h->tcQr, tc_operand_bytes(ns, n, h->qcmax));
+    if (h->tcrows == n) {
+      h->qcmax = 2 * k_max + 1;  // [u0, X, P]
+      AL(h->tcQc, tc_operand_bytes(ns, n, h->qcmax));
+      AL(h->tcQr, tc_operand_bytes(ns, n, h->qcmax));
+    } else {
+      AL(h->Gt, sizeof(double) * size_t(3 * k_max + 1) * (3 * k_max + 1));
+    }
   }
   // small
   const int smax = 3 * k_max + 1;
@@ -1817,7 +1864,8 @@ size_t eig_footprint(int64_t n, int64_t nnz, int nev, int k_max, const eig_optio
   eig_options_default(&d);
   const eig_options* o = opt ? opt : &d;
   const int nes = o->nes > 0 ? o->nes : nev + 5;
-  return footprint_bytes(n, nnz, nev, k_max, nes, o->form, o->precond, o->deflate_ones, 0, o->gram_tc);
+  return footprint_bytes(n, nnz, nev, k_max, nes, o->form, o->precond, o->deflate_ones, 0, o->gram_tc,
+                         o->tc_chunk_rows);
 }
 
 int eig_server_create(const eig_server_opts* opts, eig_server** out) {
@@ -1853,7 +1901,7 @@ int eig_submit(eig_server* s, const eig_csr* A, int nev, int k_max, int strategy
   r->strategy = strategy;
   r->opt = *opt;
   r->footprint = footprint_bytes(A->n, A->nnz, nev, k_max, nes, opt->form, opt->precond, opt->deflate_ones, 0,
-                                 opt->gram_tc);
+                                 opt->gram_tc, opt->tc_chunk_rows);
   r->t_submit = std::chrono::steady_clock::now();
   if (r->footprint > s->opt.mem_budget_bytes) {
     delete r;

@@ -86,6 +86,7 @@ def test_options_default_values(libpath):
     assert (o.tol, o.max_iter, o.je, o.js, o.jp, o.j_warm) == (1e-10, 1000, 12, 2, 10, 5)
     assert (o.mu, o.r_warm, o.cheb_degree) == (1.1, 1e-4, 12)
     assert (o.expand_powered, o.gram_tc, o.warm_first, o.expand_random, o.seed) == (0, 1, 0, 0, 0)
+    assert o.tc_chunk_rows == 0
 
 
 def test_struct_layouts_match_header(tmp_path):
@@ -132,6 +133,9 @@ def test_footprint_orders_the_configurations(libpath):
     assert f(2_097_152, 14_581_760, 64, 128, gram_tc=0) < c2
     c4 = dict(precond=1, deflate_ones=1)
     assert f(4_000_000, 44_000_000, 200, 400, **c4) > 280e9 > f(4_000_000, 44_000_000, 200, 400, gram_tc=0, **c4)
+    # row-chunked slice buffers bring the tensor-core products back under HBM
+    chunked = [f(4_000_000, 44_000_000, 200, 400, tc_chunk_rows=r, **c4) for r in (262_144, 1_048_576)]
+    assert f(4_000_000, 44_000_000, 200, 400, gram_tc=0, **c4) < chunked[0] < chunked[1] < 280e9
     sizes = [f(n, 7 * n, 32, k) for n in (10_000, 100_000, 1_000_000) for k in (64, 96, 128)]
     assert sizes == sorted(sizes[:3]) + sorted(sizes[3:6]) + sorted(sizes[6:])
     for k in range(3):

@@ -577,6 +577,28 @@ def test_c3_shape_chebsi_parity(c3_40, form):
         assert abs(out["iters"] - ref.iters) <= 1 and out["n_shrink"] == n_sh
 
 
+@pytest.mark.parametrize("form", ["f64", "df64"])
+def test_row_chunked_tensor_core_products(form):
+    """tc_chunk_rows: the slice buffers hold 2048 rows and every Gram and
+    update runs over row chunks (the last one ragged); the solve matches the
+    unchunked one and the closed form."""
+    A = W.laplacian_3d(20, 22, 24)   # n = 10560 = 5 x 2048 + 320
+    ex = dirichlet_spectrum((20, 22, 24))
+    normA = W.dirichlet_norm((20, 22, 24))
+    X0 = W.gaussian_block(A.n, 40, 1)
+    kw = dict(nev=24, k_max=40, strategy="fix", X0=X0, normA=normA, tol=1e-10, form=form)
+    s = L.Solver(A, tc_chunk_rows=2048, **kw)
+    out = s.solve()
+    s.close()
+    s = L.Solver(A, **kw)
+    ref = s.solve()
+    s.close()
+    assert out["status"] == 0 and ref["status"] == 0
+    assert np.max(np.abs(out["lam"] - ex[:24]) / ex[:24]) <= 1e-10
+    assert np.max(np.abs(out["lam"] - ref["lam"]) / ref["lam"]) <= 1e-11
+    assert out["resid"].max() <= 2e-10
+
+
 def test_solver_reuse_gives_identical_results(c1):
     A, normA, X0, _ = c1
     s = L.Solver(A, nev=10, k_max=20, strategy="fix", X0=X0, normA=normA, tol=1e-10)
