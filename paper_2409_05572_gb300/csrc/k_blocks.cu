@@ -370,11 +370,13 @@ static void spmm_dispatch_g(const Csr<A>& M, int w, const typename Pol<A>::T* V,
     launch_spmm<A, VEC, 16, 1>(M, w, V, ldv, Y, ldy, alpha, beta, U, ldu, gamma, st);
   else if (wv <= 32)
     launch_spmm<A, VEC, 32, 1>(M, w, V, ldv, Y, ldy, alpha, beta, U, ldu, gamma, st);
-  else if (wv <= 64)
-    launch_spmm<A, VEC, 32, 2>(M, w, V, ldv, Y, ldy, alpha, beta, U, ldu, gamma, st);
   // 3 and 6 vectors per lane for the widths between the powers of two (a
   // shrunk block of nes = k_max / 2 + 5 columns): a lane slot past the last
   // column still issues its loads and multiply-adds, predicated off
+  else if (wv <= 48)
+    launch_spmm<A, VEC, 16, 3>(M, w, V, ldv, Y, ldy, alpha, beta, U, ldu, gamma, st);
+  else if (wv <= 64)
+    launch_spmm<A, VEC, 32, 2>(M, w, V, ldv, Y, ldy, alpha, beta, U, ldu, gamma, st);
   else if (wv <= 96)
     launch_spmm<A, VEC, 32, 3>(M, w, V, ldv, Y, ldy, alpha, beta, U, ldu, gamma, st);
   else if (wv <= 128)

@@ -284,13 +284,13 @@ __device__ __forceinline__ double acc_value(const tf& m) { return (double(m.m0) 
 // a 128 x 32 update tile (three 128-index chunks) slower than its MMAs.
 // The three floats become 64-bit fixed-point integers in units of
 // 2^(E0 - 187), E0 the biased exponent of m0 (m0's 24-bit mantissa shifted
-// left by 37 bits, the others aligned to it; bits below 2^-61 |m0| are
-// dropped), their sum is rounded to 53 bits (nearest even) and the float64
-// fields are assembled.  Zero, tiny or non-finite heads, a tail above the
+// left by 37 bits, the others aligned to it; each tail loses less than one
+// unit, at most 2^-60 |m0|), their sum is rounded to 53 bits (nearest even)
+// and the float64 fields are assembled.  Zero, tiny or non-finite heads, a tail above the
 // head and results outside the normal float64 range take the float64 path.
 __device__ __forceinline__ long long tf_fixed(uint32_t b, int E0) {
   const int E = int((b >> 23) & 255u);
-  if (E == 0) return 0;  // zero, or a subnormal below 2^-61 |m0|
+  if (E == 0) return 0;  // zero, or a subnormal below 2^-60 |m0| (E0 >= 64)
   const long long M = (long long)((b & 0x7FFFFFu) | 0x800000u);
   const int sh = E - E0 + 37;
   const long long v = sh >= 0 ? (M << sh) : (sh > -64 ? (M >> -sh) : 0ll);

@@ -66,7 +66,7 @@ def rounded(x_np, arith):
 # a7: SpMM
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("arith", ["f64", "df64", "f32"])
-@pytest.mark.parametrize("w", [1, 3, 8, 20, 64, 130, 133, 300])
+@pytest.mark.parametrize("w", [1, 3, 8, 20, 64, 69, 130, 133, 300])
 def test_spmm_parity(arith, w):
     A = W.anderson_3d(9, seed=2)   # n = 729, 7 nnz/row, random values
     n = A.n

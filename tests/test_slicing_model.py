@@ -28,6 +28,7 @@ Float64 blocks (seven slices, second half of this module):
 Everything here is exact rational arithmetic (Python integers / fractions)
 except the float32 steps, which numpy performs with IEEE rounding.
 """
+import math
 from fractions import Fraction
 
 import numpy as np
@@ -306,3 +307,82 @@ def test_f64_triple_float_accumulation_is_float64_class():
         total += abs(c)
     got = Fraction(float(m0)) + Fraction(float(m1)) + Fraction(float(m2))
     assert abs(got - exact_sum) <= Fraction(1, 2 ** 53) * total
+
+
+def f32_fixed(x, E0):
+    """One float32 of the accumulator as an integer in units of
+    2^(E0 - 187) (E0 the head's biased exponent): the mantissa shifted by
+    E - E0 + 37, right shifts truncating toward zero on the magnitude."""
+    b = int(np.float32(x).view(np.uint32))
+    E = (b >> 23) & 255
+    if E == 0:
+        return 0
+    M = (b & 0x7FFFFF) | 0x800000
+    sh = E - E0 + 37
+    v = M << sh if sh >= 0 else (M >> -sh if sh > -64 else 0)
+    return -v if b >> 31 else v
+
+
+def fixed_to_double(m0, m1, m2, e):
+    """The epilogue's float64 of (m0 + m1 + m2) 2^e: the three floats as
+    64-bit fixed-point integers aligned to the head, summed, rounded once to
+    53 bits (nearest even), float64 fields assembled; None where the kernel
+    takes its float64 path instead."""
+    E0 = (int(np.float32(m0).view(np.uint32)) >> 23) & 255
+    E1 = (int(np.float32(m1).view(np.uint32)) >> 23) & 255
+    E2 = (int(np.float32(m2).view(np.uint32)) >> 23) & 255
+    if E0 < 64 or E0 == 255 or E1 > E0 + 1 or E2 > E0 + 1 or E1 == 255 or E2 == 255:
+        return None
+    S = f32_fixed(m0, E0) + f32_fixed(m1, E0) + f32_fixed(m2, E0)
+    assert -2 ** 63 < S < 2 ** 63
+    if S == 0:
+        return 0.0
+    a = abs(S)
+    sh = a.bit_length() - 53
+    if sh > 0:
+        mant = a >> sh
+        rem, half = a & ((1 << sh) - 1), 1 << (sh - 1)
+        if rem > half or (rem == half and mant & 1):
+            mant += 1
+        if mant >> 53:
+            mant >>= 1
+            sh += 1
+    else:
+        mant = a << -sh
+    biased = sh + E0 - 187 + e + 52 + 1023
+    if biased < 1 or biased > 2046:
+        return None
+    bits = (1 << 63 if S < 0 else 0) | (biased << 52) | (mant & ((1 << 52) - 1))
+    return float(np.array(bits, dtype=np.uint64).view(np.float64))
+
+
+def test_integer_float64_assembly_rounds_the_triple_float_once():
+    """The product epilogue's conversion of the triple-float accumulator:
+    on random accumulators (head, a tail up to 2^-20 below it and a smaller
+    one, both signs, scales up to 2^+-900) the float64 it assembles is the
+    exact sum m0 + m1 + m2 rounded to nearest, plus the bits that the fixed
+    point drops (below one unit 2^(E0 - 187) <= 2^-60 |m0| for each of the
+    two tails); special cases take the float64 path."""
+    rng = np.random.default_rng(41)
+    checked = 0
+    for _ in range(3000):
+        m0 = np.float32(rng.uniform(1, 2) * 2.0 ** int(rng.integers(-60, 60)) * rng.choice([-1, 1]))
+        m1 = np.float32(float(m0) * rng.uniform(-1, 1) * 2.0 ** -int(rng.integers(0, 21)))
+        m2 = np.float32(float(m1) * rng.uniform(-1, 1) * 2.0 ** -int(rng.integers(0, 30)))
+        e = int(rng.integers(-900, 900))
+        got = fixed_to_double(m0, m1, m2, e)
+        if got is None:
+            continue
+        checked += 1
+        exact = (Fraction(float(m0)) + Fraction(float(m1)) + Fraction(float(m2))) * Fraction(2) ** e
+        ulp = Fraction(2) ** (math.frexp(float(exact))[1] - 53) if exact else Fraction(0)
+        err = abs(Fraction(got) - exact)
+        assert err <= ulp / 2 + Fraction(2) ** -59 * abs(Fraction(float(m0))) * Fraction(2) ** e, (m0, m1, m2, e)
+    assert checked > 2500
+    # the fall-back cases
+    assert fixed_to_double(np.float32(0), np.float32(1), np.float32(0), 0) is None        # zero head
+    assert fixed_to_double(np.float32(1), np.float32(8), np.float32(0), 0) is None        # tail above the head
+    assert fixed_to_double(np.float32(np.inf), np.float32(0), np.float32(0), 0) is None   # non-finite
+    assert fixed_to_double(np.float32(1), np.float32(0), np.float32(0), 1100) is None     # outside float64
+    # exact cancellation to zero
+    assert fixed_to_double(np.float32(1), np.float32(-1), np.float32(0), 0) == 0.0
