@@ -570,3 +570,29 @@ def test_gaussian_columns_are_standard_normal_and_counter_addressed():
     assert not np.allclose(gaussian_columns(300, 4, 12345, 4), Z[:300, :4])
     assert not np.allclose(gaussian_columns(300, 4, 12346, 3), Z[:300, :4])
     assert np.all(np.isfinite(Z))
+
+
+def test_expansion_variants_order_as_in_sec_6_4():
+    """The appended vectors of Sec. 6.4: on a small Anderson Hamiltonian
+    (Chebyshev SI) and on c1 (LOBPCG) every variant converges to the dense
+    eigenvalues, and the iteration counts order as the paper reports --
+    powered X_drop <= X_drop < Random."""
+    A = W.anderson_3d(12, seed=2)
+    ev = np.linalg.eigvalsh(A.to_scipy().toarray())
+    X0 = W.gaussian_block(A.n, 32, 2)
+    kw = dict(tol=1e-10, normA=float(np.abs(ev).max()), degree=8, upper=W.gershgorin_bound(A), j_warm=2,
+              r_warm=1e-2, je=4, js=1, max_iter=400, seed=5)
+    its = {}
+    for ex in ("drop", "powered", "random"):
+        r = chebsi(A, X0, 16, 21, "fix", expand=ex, **kw)
+        assert r.converged and np.allclose(r.lam, ev[:16], rtol=1e-10, atol=1e-12)
+        its[ex] = r.iters
+    assert its["powered"] <= its["drop"] < its["random"], its
+    A = W.laplacian_2d(32)
+    X0 = W.gaussian_block(A.n, 20, 0)
+    normA = W.dirichlet_norm((32, 32))
+    drop = lobpcg(A, X0, 10, 15, "fix", tol=1e-10, normA=normA)
+    rand = lobpcg(A, X0, 10, 15, "fix", tol=1e-10, normA=normA, expand="random", seed=5)
+    assert drop.converged and rand.converged
+    assert np.allclose(rand.lam, drop.lam, rtol=1e-10)
+    assert drop.iters < rand.iters
