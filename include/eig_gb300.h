@@ -91,7 +91,9 @@ int eig_convert(int64_t count, const void *src, int src_dtype, void *dst, int ds
  * format dtype (U may be NULL when gamma == 0); val is float64 when dtype is
  * EIG_F64, float32 for EIG_F32 and double-float for EIG_DF64.  Y must not
  * overlap V or U.  The three-term form is one step of the Chebyshev
- * recurrence.  w <= 1024. */
+ * recurrence.  w <= 1024.  Each row is one lane group's work here; inside
+ * eig_solve, rows with more than 512 nonzeros (power-law graphs) are split
+ * over the warps of a CTA from a list built once at eig_create. */
 int eig_spmm(int64_t n, const int32_t *rowptr, const int32_t *colind, const void *val,
              int dtype, int w, const void *V, int64_t ldv, void *Y, int64_t ldy, double alpha,
              double beta, const void *U, int64_t ldu, double gamma, void *stream);
