@@ -383,7 +383,11 @@ int eig_strategy_trace(int strategy, int nes, int nex, const eig_options *opt, c
  * footprint fits mem_budget_bytes and fewer than max_active solves run, then
  * advances every active solve by one iteration (Algorithm 3 / 1 each, with
  * their own shrink / expand decisions); each solve runs on its own CUDA
- * stream so their kernels overlap.  A finished solve's results (eigenvalues,
+ * stream so their kernels overlap, and the host part of each iteration runs
+ * as soon as that solve's stream has drained (completion order, streams
+ * polled).  A solve that finishes inside the step frees its slot and memory
+ * at once, and queued requests are admitted into them (their first iteration
+ * runs in the same step).  A finished solve's results (eigenvalues,
  * residuals, history, eigenvectors copied to host memory) are kept until
  * eig_release; its device memory and slot are freed at once.  eig_poll sets
  * *ready and fills *out (V is then a HOST pointer, n x nev row-major;
