@@ -260,7 +260,10 @@ typedef struct {
   double cheb_upper;   /* upper bound of the spectrum (0 = normA)             */
   int precond;         /* 0 none, 1 Jacobi T = diag(A)^{-1}                   */
   int deflate_ones;    /* 1: keep every block orthogonal to 1/sqrt(n)         */
-  double normA;        /* ||A||_2 used by Eq. conv; must be > 0               */
+  double normA;        /* ||A||_2 used by Eq. conv; 0 (default): eig_create
+                          takes the Gershgorin bound of eig_norm_bound, an
+                          upper bound (the test is then at most that much
+                          stricter)                                          */
   double mixed_switch; /* 1e-5: residual at which MIXED promotes to DF64      */
   const double *X0;    /* n x k_max float64 row-major initial block (required)*/
   int x0_on_device;    /* 1: X0 is a device pointer                           */
@@ -337,11 +340,19 @@ typedef struct {
 typedef struct eig_handle eig_handle;
 
 /* Fill *opt with the defaults listed above (X0 NULL, normA 0). */
+
+/* Gershgorin bound max_i sum_j |a_ij| >= ||A||_2 of a symmetric CSR matrix
+ * (host arrays only: A->on_device must be 0), into *out.  eig_create and
+ * eig_submit use it when opt->normA is 0.  EIG_EINVAL for a device CSR or a
+ * malformed one (n <= 0, rowptr not starting at 0 or not ascending). */
+int eig_norm_bound(const eig_csr *A, double *out);
 int eig_options_default(eig_options *opt);
 
 /* Validate and allocate a solver for the nev smallest eigenpairs with
  * initial/expanded width k_max (nex).  Requires 1 <= nev <= nes < k_max <= n,
- * opt->X0 != NULL and opt->normA > 0.  Device memory: eig_footprint() bytes
+ * opt->X0 != NULL and opt->normA >= 0 (0: the Gershgorin bound, read from
+ * the host CSR or, for a device CSR, from one copy of its values).  Device
+ * memory: eig_footprint() bytes
  * (for the 128^3 Laplacian with k_max = 128, about 90 GB in the float64 form
  * with the tensor-core products); EIG_ENOMEM if it does not fit. */
 int eig_create(const eig_csr *A, int nev, int k_max, int strategy, const eig_options *opt,

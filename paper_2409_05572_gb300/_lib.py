@@ -30,7 +30,7 @@ EXPORTS = ("eig_convert", "eig_spmm", "eig_gram", "eig_gram_noalloc", "eig_block
            "eig_cholqr2", "eig_syev", "eig_hl_trick", "eig_options_default", "eig_create", "eig_solve",
            "eig_query", "eig_destroy", "eig_strerror", "eig_footprint", "eig_server_create", "eig_submit",
            "eig_server_step", "eig_poll", "eig_release", "eig_server_destroy", "eig_device_status",
-           "eig_strategy_trace", "eig_tc_wait_selftest")
+           "eig_strategy_trace", "eig_tc_wait_selftest", "eig_norm_bound")
 
 
 class EigError(RuntimeError):
@@ -108,6 +108,7 @@ def load(path: str = LIB_PATH):
         "eig_server_destroy": [p],
         "eig_footprint": [i64, i64, i32, i32, C.POINTER(eig_options)],
         "eig_strategy_trace": [i32, i32, i32, C.POINTER(eig_options), p, p, i32, p, p, i32, C.POINTER(C.c_int)],
+        "eig_norm_bound": [C.POINTER(eig_csr), C.POINTER(C.c_double)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -320,9 +321,8 @@ class Solver:
             if not hasattr(opt, k):
                 raise TypeError(f"unknown option {k}")
             setattr(opt, k, v)
-        if normA is None:
-            raise ValueError("normA is required (the matrix 2-norm of Eq. conv)")
-        opt.normA = float(normA)
+        # None: eig_create takes the Gershgorin bound of ||A||_2
+        opt.normA = 0.0 if normA is None else float(normA)
         if X0 is None:
             raise ValueError("X0 (n x k_max float64) is required")
         if hasattr(X0, "data_ptr"):
@@ -358,7 +358,7 @@ class Solver:
             "history": np.ctypeslib.as_array(r.history, (it,)).copy() if r.history and it else np.zeros(0),
             "widths": (np.ctypeslib.as_array(r.widths, (max(it - (1 if r.status == EIG_OK else 0), 0),)).copy()
                        if r.widths else np.zeros(0, dtype=np.int32)),
-            "time_ms": r.time_ms, "V_ptr": r.V, "launches": int(r.launches),
+            "time_ms": r.time_ms, "V_ptr": r.V, "launches": int(r.launches), "normA": r.normA,
         }
         if r.kstats:
             ks = np.ctypeslib.as_array(r.kstats, (len(KCLASSES), 4)).copy()
@@ -418,6 +418,19 @@ def make_options(algo="lobpcg", form="f64", tol=1e-10, max_iter=1000, nes=0, nor
     if normA is not None:
         opt.normA = float(normA)
     return opt
+
+
+def norm_bound(A):
+    """eig_norm_bound: the Gershgorin bound of ||A||_2 of a host CSR matrix."""
+    rp = np.ascontiguousarray(A.indptr, dtype=np.int32)
+    ci = np.ascontiguousarray(A.indices, dtype=np.int32)
+    vdt = np.float32 if np.asarray(A.data).dtype == np.float32 else np.float64
+    va = np.ascontiguousarray(A.data, dtype=vdt)
+    csr = eig_csr(A.n, ci.size, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0,
+                  EIG_F32 if vdt == np.float32 else EIG_F64)
+    out = C.c_double()
+    _check("eig_norm_bound", load().eig_norm_bound(C.byref(csr), C.byref(out)))
+    return out.value
 
 
 def footprint(n, nnz, nev, k_max, **opts):

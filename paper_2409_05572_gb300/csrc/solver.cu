@@ -130,6 +130,20 @@ struct SEStrategy {
 // SpMM rows longer than this are split over the warps of a CTA
 constexpr int HEAVY_MIN = 512;
 
+// max_i sum_j |a_ij| of host CSR arrays (an upper bound of ||A||_2 for a
+// symmetric A, and of the spectrum's magnitude)
+double gershgorin_bound(int64_t n, const int32_t* rp, const void* val, int val_dtype) {
+  double best = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double r = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+      r += val_dtype == EIG_F32 ? std::fabs(double(static_cast<const float*>(val)[k]))
+                                : std::fabs(static_cast<const double*>(val)[k]);
+    best = std::max(best, r);
+  }
+  return best;
+}
+
 struct eig_handle {
   int64_t n = 0, nnz = 0;
   int nev = 0, kmax = 0, nes = 0, strategy = 0;
@@ -1535,7 +1549,7 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
   if (A->val_dtype != EIG_F64 && A->val_dtype != EIG_F32) return EIG_EINVAL;
   if (nev < 1 || nes < nev || nes >= k_max || k_max > A->n) return EIG_EINVAL;
   if (strategy < EIG_NONE || strategy > EIG_SLOPEK) return EIG_EINVAL;
-  if (!opt->X0 || !(opt->normA > 0.0) || opt->max_iter < 1 || !(opt->tol > 0.0)) return EIG_EINVAL;
+  if (!opt->X0 || !(opt->normA >= 0.0) || opt->max_iter < 1 || !(opt->tol > 0.0)) return EIG_EINVAL;
   if (opt->algo != EIG_LOBPCG && opt->algo != EIG_CHEB_SI && opt->algo != EIG_SD) return EIG_EINVAL;
   if (opt->form < EIG_FORM_DF64 || opt->form > EIG_FORM_MIXED) return EIG_EINVAL;
   if (opt->algo == EIG_CHEB_SI && opt->cheb_degree < 2) return EIG_EINVAL;
@@ -1610,6 +1624,20 @@ int eig_create(const eig_csr* A, int nev, int k_max, int strategy, const eig_opt
     std::vector<int32_t> hv;
     for (int64_t i = 0; i < n; ++i)
       if (hrp[i + 1] - hrp[i] > HEAVY_MIN) hv.push_back(int32_t(i));
+    if (opt->normA == 0.0) {  // ||A||_2 of Eq. conv not given: the Gershgorin bound
+      const void* hval = A->val;
+      std::vector<double> vbuf;
+      if (A->on_device) {
+        const size_t vb = (A->val_dtype == EIG_F32 ? sizeof(float) : sizeof(double)) * size_t(nnz);
+        vbuf.resize((vb + sizeof(double) - 1) / sizeof(double));
+        if (cudaMemcpyAsync(vbuf.data(), A->val, vb, cudaMemcpyDeviceToHost, h->st) ||
+            cudaStreamSynchronize(h->st))
+          return fail(EIG_ECUDA);
+        hval = vbuf.data();
+      }
+      h->opt.normA = gershgorin_bound(n, hrp, hval, A->val_dtype);
+      if (!(h->opt.normA > 0.0)) return fail(EIG_EINVAL);  // the zero matrix
+    }
     if (!hv.empty()) {
       AL(h->heavy, sizeof(int32_t) * hv.size());
       if (cudaMemcpyAsync(h->heavy, hv.data(), sizeof(int32_t) * hv.size(), cudaMemcpyHostToDevice, h->st) ||
@@ -1838,6 +1866,7 @@ void retire(eig_server* s, Request* r) {
   r->resid = h->resid;
   r->history = h->history;
   r->widths = h->widths;
+  r->opt.normA = h->opt.normA;  // the Gershgorin bound when the request left it 0
   r->V.resize(size_t(r->n) * r->nev);
   if (r->status == EIG_OK || r->status == EIG_ENOTCONV)
     cudaMemcpyAsync(r->V.data(), h->V, sizeof(double) * r->V.size(), cudaMemcpyDeviceToHost, r->st);
@@ -1858,6 +1887,16 @@ void retire(eig_server* s, Request* r) {
 }  // namespace
 
 extern "C" {
+
+int eig_norm_bound(const eig_csr* A, double* out) {
+  if (!A || !out || A->on_device || A->n <= 0 || !A->rowptr || !A->val) return EIG_EINVAL;
+  if (A->val_dtype != EIG_F64 && A->val_dtype != EIG_F32) return EIG_EINVAL;
+  if (A->rowptr[0] != 0) return EIG_EINVAL;
+  for (int64_t i = 0; i < A->n; ++i)
+    if (A->rowptr[i + 1] < A->rowptr[i]) return EIG_EINVAL;
+  *out = gershgorin_bound(A->n, A->rowptr, A->val, A->val_dtype);
+  return EIG_OK;
+}
 
 size_t eig_footprint(int64_t n, int64_t nnz, int nev, int k_max, const eig_options* opt) {
   eig_options d;
@@ -1881,7 +1920,7 @@ int eig_submit(eig_server* s, const eig_csr* A, int nev, int k_max, int strategy
   if (!s || !A || !opt || !ticket || A->on_device || !opt->X0 || opt->x0_on_device) return EIG_EINVAL;
   if (A->val_dtype != EIG_F64 && A->val_dtype != EIG_F32) return EIG_EINVAL;
   const int nes = opt->nes > 0 ? opt->nes : nev + 5;
-  if (A->n <= 0 || nev < 1 || nes < nev || nes >= k_max || k_max > A->n || !(opt->normA > 0.0)) return EIG_EINVAL;
+  if (A->n <= 0 || nev < 1 || nes < nev || nes >= k_max || k_max > A->n || !(opt->normA >= 0.0)) return EIG_EINVAL;
   Request* r = new Request();
   r->ticket = s->next_ticket++;
   r->n = A->n;

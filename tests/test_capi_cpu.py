@@ -140,3 +140,28 @@ def test_footprint_orders_the_configurations(libpath):
     assert sizes == sorted(sizes[:3]) + sorted(sizes[3:6]) + sorted(sizes[6:])
     for k in range(3):
         assert sizes[k] < sizes[3 + k] < sizes[6 + k]
+
+
+def test_norm_bound_is_the_gershgorin_bound(libpath):
+    """eig_norm_bound (host only): max_i sum_j |a_ij|, an upper bound of
+    ||A||_2 -- exact for the 2D Dirichlet Laplacian's interior rows (8), close
+    for the Anderson Hamiltonian, within 2x for a graph Laplacian; float32
+    values give the same bound; device or malformed CSR is rejected."""
+    import numpy as np
+    from paper_2409_05572_gb300 import _lib
+    from paper_2409_05572_gb300 import workloads as W
+    _lib.load()
+    for A in (W.laplacian_2d(16), W.anderson_3d(6, seed=2), W.graph_laplacian(2000, seed=3)):
+        M = A.to_scipy()
+        want = float(np.max(np.asarray(abs(M).sum(axis=1)).ravel()))
+        got = _lib.norm_bound(A)
+        assert abs(got - want) <= 1e-14 * want   # the same sums, in row order
+        norm2 = float(np.max(np.abs(np.linalg.eigvalsh(M.toarray()))))
+        assert norm2 <= got * (1 + 1e-12) and got <= 2.0 * norm2 + 1e-12
+        A32 = W.CSR(A.n, A.indptr, A.indices, A.data.astype(np.float32))
+        assert abs(_lib.norm_bound(A32) - want) <= 1e-6 * want
+    assert _lib.norm_bound(W.laplacian_2d(16)) == 8.0
+    bad = W.laplacian_2d(4)
+    bad = W.CSR(bad.n, np.concatenate([[1], bad.indptr[1:]]).astype(np.int32), bad.indices, bad.data)
+    with pytest.raises(_lib.EigError):
+        _lib.norm_bound(bad)

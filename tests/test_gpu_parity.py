@@ -599,6 +599,20 @@ def test_row_chunked_tensor_core_products(form):
     assert out["resid"].max() <= 2e-10
 
 
+def test_norm_estimated_when_not_given(c1):
+    """normA = 0 (None in the binding): eig_create takes the Gershgorin bound
+    of ||A||_2 (8 for the 2D Laplacian, against the exact 7.98...), so the
+    stopping test is that much stricter and the solve still reaches the
+    closed form."""
+    A, normA, X0, ex = c1
+    s = L.Solver(A, nev=10, k_max=20, strategy="fix", X0=X0, tol=1e-10)
+    out = s.solve()
+    s.close()
+    assert out["status"] == 0
+    assert out["normA"] == 8.0 and normA < 8.0
+    assert np.max(np.abs(out["lam"] - ex[:10]) / ex[:10]) <= 1e-10
+
+
 def test_solver_reuse_gives_identical_results(c1):
     A, normA, X0, _ = c1
     s = L.Solver(A, nev=10, k_max=20, strategy="fix", X0=X0, normA=normA, tol=1e-10)
